@@ -1,0 +1,156 @@
+"""Closed-form flip rates of the paper's noise channels (Methods
+"Simulation"), sampled with the oracle and compared within 5 sigma.
+
+* X_ERROR(p) before M: the record flips with probability p.
+* DEPOLARIZE1(p): X, Y, Z each with p/3; read out (x, z) through two copy
+  CNOTs, the joint distribution is (1-p, p/3, p/3, p/3).
+* DEPOLARIZE2(p): the 15 non-identity two-qubit Paulis each with p/15; the
+  4-bit (x1, z1, x2, z2) readout is uniform over the 15 non-zero values.
+* Bell pair + DEPOLARIZE2(p_ebit) + ZZ parity: 8 p_ebit / 15.
+* XOR of N independent X_ERROR(p) sites: (1 - (1 - 2p)^N) / 2.
+* Per-site rates and independence over many targets (several 64-unit
+  segments with a ragged last one); p = 0 never fires, p = 1 always does.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_05611_gb300.circuits import Circuit
+
+
+def bits(c, shots, seed=11):
+    det, obs = oracle.sample(c, shots, seed, threads=4)
+    return oracle.unpack_bits(det, shots)
+
+
+def close(k, n, p, sig=5.0):
+    sd = math.sqrt(max(p * (1 - p), 1e-12) / n)
+    return abs(k / n - p) <= sig * sd + 1e-12
+
+
+@pytest.mark.parametrize("p", [1e-3, 0.05, 0.3])
+def test_x_error_before_measure(p):
+    c = Circuit()
+    c.append("R", [0])
+    c.append("X_ERROR", [0], p=p)
+    c.append("M", [0])
+    c.append("DETECTOR", [0])
+    n = 400_000
+    assert close(bits(c, n).sum(), n, p)
+
+
+def readout_xz(c, q, a, b):
+    """Copy x_q onto ancilla a (CX q->a, M a) and z_q onto b (RX b, CX b->q, MX b)."""
+    c.append("CX", [q, a])
+    c.append("CX", [b, q])
+
+
+def test_depolarize1_pauli_distribution():
+    p = 0.3
+    c = Circuit()
+    c.append("R", [0, 1])
+    c.append("RX", [2])
+    c.append("DEPOLARIZE1", [0], p=p)
+    readout_xz(c, 0, 1, 2)
+    c.append("M", [1])
+    c.append("MX", [2])
+    c.append("DETECTOR", [0])
+    c.append("DETECTOR", [1])
+    n = 300_000
+    b = bits(c, n)
+    code = b[0] + 2 * b[1]
+    h = np.bincount(code, minlength=4)
+    assert close(h[0], n, 1 - p)
+    for k in (1, 2, 3):
+        assert close(h[k], n, p / 3)
+
+
+def test_depolarize2_pauli_distribution():
+    p = 0.45
+    c = Circuit()
+    c.append("R", [0, 1, 2, 4])
+    c.append("RX", [3, 5])
+    c.append("DEPOLARIZE2", [0, 1], p=p)
+    readout_xz(c, 0, 2, 3)
+    readout_xz(c, 1, 4, 5)
+    c.append("M", [2, 4])
+    c.append("MX", [3, 5])
+    for r in range(4):
+        c.append("DETECTOR", [r])
+    n = 300_000
+    b = bits(c, n)
+    x1, x2, z1, z2 = b[0], b[1], b[2], b[3]
+    code = x1 + 2 * z1 + 4 * x2 + 8 * z2
+    h = np.bincount(code, minlength=16)
+    assert close(h[0], n, 1 - p)
+    e = n * p / 15
+    chi2 = ((h[1:] - e) ** 2 / e).sum()
+    assert chi2 < 14 + 6 * math.sqrt(28)
+    # marginal x1 flip: 8 of 15 Paulis carry X or Y on the first qubit
+    assert close(x1.sum(), n, 8 * p / 15)
+
+
+def test_bell_pair_zz_parity():
+    pe = 0.2
+    c = Circuit()
+    c.append("R", [0, 1])
+    c.append("H", [0])
+    c.append("CX", [0, 1])
+    c.append("DEPOLARIZE2", [0, 1], p=pe)
+    c.append("M", [0, 1])
+    c.append("DETECTOR", [0, 1])
+    n = 300_000
+    assert close(bits(c, n).sum(), n, 8 * pe / 15)
+
+
+@pytest.mark.parametrize("N,p", [(7, 0.02), (130, 0.003)])
+def test_xor_of_independent_sites(N, p):
+    c = Circuit()
+    c.append("R", list(range(N + 1)))
+    c.append("X_ERROR", list(range(N)), p=p)
+    c.append("CX", [v for q in range(N) for v in (q, N)])
+    c.append("M", [N])
+    c.append("DETECTOR", [0])
+    n = 300_000
+    assert close(bits(c, n).sum(), n, (1 - (1 - 2 * p) ** N) / 2)
+
+
+def test_many_targets_rates_and_independence():
+    """200 targets = segments of 64, 64, 64 and 8 units."""
+    T, p = 200, 0.02
+    c = Circuit()
+    c.append("R", list(range(T)))
+    c.append("X_ERROR", list(range(T)), p=p)
+    c.append("M", list(range(T)))
+    for q in range(T):
+        c.append("DETECTOR", [q])
+    n = 64 * 1500
+    b = bits(c, n).astype(np.float64)
+    rates = b.mean(axis=1)
+    sd = math.sqrt(p * (1 - p) / n)
+    assert np.all(np.abs(rates - p) < 5.5 * sd)
+    z = (b.sum() / (T * n) - p) / math.sqrt(p * (1 - p) / (T * n))
+    assert abs(z) < 5
+    # neighbouring targets and neighbouring shots are independent
+    cov_t = np.mean(b[:-1] * b[1:]) - p * p
+    assert abs(cov_t) < 6 * p / math.sqrt((T - 1) * n)
+    cov_s = np.mean(b[:, :-1] * b[:, 1:]) - p * p
+    assert abs(cov_s) < 6 * p / math.sqrt(T * (n - 1))
+    # per (segment, chunk) event counts are Binomial(64 * units, p)
+    counts = b[:64].reshape(64, n // 64, 64).sum(axis=(0, 2))
+    assert abs(counts.mean() - 4096 * p) < 5 * math.sqrt(4096 * p * (1 - p) / counts.size)
+    assert abs(counts.var() / (4096 * p * (1 - p)) - 1) < 0.2
+
+
+def test_probability_zero_and_one():
+    c = Circuit()
+    c.append("R", [0, 1])
+    c.append("X_ERROR", [0], p=0.0)
+    c.append("X_ERROR", [1], p=1.0)
+    c.append("M", [0, 1])
+    c.append("DETECTOR", [0])
+    c.append("DETECTOR", [1])
+    b = bits(c, 1000)
+    assert not b[0].any() and b[1].all()

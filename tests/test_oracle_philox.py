@@ -1,0 +1,88 @@
+"""Pins of the oracle's Philox4x32-10 and gap tables.
+
+Philox4x32-10 (Salmon et al., SC'11) is a bijection of the 128-bit counter
+for a fixed key: this test inverts the published round structure (the
+multipliers are odd, so each low product is invertible mod 2^32) and checks
+that the inverse of the oracle's output returns the counter; a wrong
+multiplier, key schedule or output wiring in the oracle breaks the round
+trip. Output statistics are checked too. (An independent implementation on
+the GPU, cuRAND's Philox4_32_10, is compared in tests/test_gpu_rng.py.)
+
+The gap tables are pinned by the distribution they induce: P(A >= a) and
+P(B >= b) read off the tables must equal the geometric tails to within the
+2^-32 quantisation.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+M0, M1 = 0xD2511F53, 0xCD9E8D57
+W0, W1 = 0x9E3779B9, 0xBB67AE85
+MASK = 0xFFFFFFFF
+
+
+def philox_inverse(out, key):
+    inv0, inv1 = pow(M0, -1, 1 << 32), pow(M1, -1, 1 << 32)
+    keys = [((key[0] + r * W0) & MASK, (key[1] + r * W1) & MASK) for r in range(10)]
+    n0, n1, n2, n3 = out
+    for r in reversed(range(10)):
+        k0, k1 = keys[r]
+        c2 = (n1 * inv1) & MASK
+        c0 = (n3 * inv0) & MASK
+        hi1 = (M1 * c2) >> 32
+        hi0 = (M0 * c0) >> 32
+        c1 = n0 ^ hi1 ^ k0
+        c3 = n2 ^ hi0 ^ k1
+        n0, n1, n2, n3 = c0, c1, c2, c3
+    return (n0, n1, n2, n3)
+
+
+def test_philox_is_the_published_bijection():
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        ctr = tuple(int(v) for v in rng.integers(0, 1 << 32, 4, dtype=np.uint64))
+        key = tuple(int(v) for v in rng.integers(0, 1 << 32, 2, dtype=np.uint64))
+        out = oracle.philox4x32_10(ctr, key)
+        assert philox_inverse(out, key) == ctr
+    assert oracle.philox4x32_10((0, 0, 0, 0), (0, 0)) != (0, 0, 0, 0)
+
+
+def test_philox_output_statistics():
+    outs = np.array([oracle.philox4x32_10((j, 7, 3, 1), (12345, 0)) for j in range(20000)],
+                    dtype=np.uint64)
+    bits = ((outs[:, :, None] >> np.arange(32, dtype=np.uint64)) & np.uint64(1)).astype(np.float64)
+    frac = bits.mean(axis=0)
+    # every output bit is balanced: |mean - 1/2| < 5 sigma
+    assert np.all(np.abs(frac - 0.5) < 5 * 0.5 / math.sqrt(outs.shape[0]))
+    # byte histogram of all words is uniform (chi-square, 255 dof)
+    b = outs.astype(np.uint32).view(np.uint8).ravel()
+    h = np.bincount(b, minlength=256)
+    e = b.size / 256
+    chi2 = ((h - e) ** 2 / e).sum()
+    assert chi2 < 255 + 6 * math.sqrt(2 * 255)
+    # consecutive counters are uncorrelated in word 0
+    w = outs[:, 0].astype(np.float64)
+    r = np.corrcoef(w[:-1], w[1:])[0, 1]
+    assert abs(r) < 5 / math.sqrt(w.size)
+
+
+@pytest.mark.parametrize("p", [1e-4, 1e-3, 1e-2, 0.1, 0.5, 0.9])
+def test_gap_tables_induce_geometric_tails(p):
+    ta, tb = oracle.gap_tables(p)
+    q = (1 - p) ** 256
+    for a in range(1, 17):
+        assert abs(int(ta[a - 1]) / 2 ** 32 - q ** a) <= 2.0 ** -31
+    for b in range(1, 256):
+        want = ((1 - p) ** b - q) / (1 - q)
+        assert abs(int(tb[b - 1]) / 2 ** 32 - want) <= 2.0 ** -31 + 1e-12
+    assert np.all(np.diff(ta.astype(np.int64)) <= 0) and np.all(np.diff(tb.astype(np.int64)) <= 0)
+
+
+def test_gap_tables_edge_probabilities():
+    ta, tb = oracle.gap_tables(1.0)
+    assert not ta.any() and not tb.any()   # p = 1: every trial is an event
+    ta, tb = oracle.gap_tables(1e-12)      # tiny p: A almost surely >= 16
+    assert ta[-1] > 0xFFFF0000
