@@ -1,0 +1,185 @@
+/*
+ * tmcs.h -- C ABI of libtmcs.so, a GB300 (sm_103a) Pauli-frame Monte Carlo
+ * sampler for noisy Clifford circuits: detection events and logical-observable
+ * flips of syndrome-extraction circuits for distributed transversal
+ * operations (arXiv 2504.05611: Methods "Simulation", "Non-local CNOT
+ * circuit", "State teleportation circuit", "Decoding").
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns a tmcs_status; on failure a thread-local message
+ *     is available from tmcs_last_error().
+ *   - Device buffers are allocated and owned by the caller; the library never
+ *     frees them. Host buffers are caller-owned too.
+ *   - Sampling calls are asynchronous on the given CUDA stream (cudaStream_t
+ *     passed as void*; NULL = legacy default stream). The caller synchronises
+ *     the stream before reading results.
+ *   - Output layout (detector-major, bit-packed): for n_det detectors and S
+ *     shots, C = ceil(S/64) uint64 words per detector; word c of detector j
+ *     holds shots 64c .. 64c+63, bit i (LSB first) = shot 64c+i; the value is
+ *     the flip of the detector parity relative to the noiseless circuit.
+ *     Pad bits of the last word are 0. Observables use the same layout.
+ *   - Results depend only on (circuit, seed, global 64-shot chunk index):
+ *     not on tile shape, batch composition, stream or GPU.
+ */
+#ifndef TMCS_ABI_H_
+#define TMCS_ABI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TMCS_OK = 0,
+    TMCS_E_INVALID = 1,          /* bad op, target, probability, record index or argument */
+    TMCS_E_NONDETERMINISTIC = 2, /* a detector/observable is random in the noiseless circuit */
+    TMCS_E_OOM = 3,              /* host or device allocation failed */
+    TMCS_E_CUDA = 4,             /* a CUDA runtime call failed */
+    TMCS_E_TIMEOUT = 5,          /* a bounded device wait expired */
+    TMCS_E_BUFFER = 6            /* output buffer too small / misaligned */
+} tmcs_status;
+
+/*
+ * Opcodes (Methods "Simulation" for the noise channels; Supplementary Note 1
+ * for the symplectic Pauli encoding the frames use):
+ *   R, RX          reset to |0> / |+> (frame cleared)
+ *   H, S           single-qubit Cliffords (frame: swap x,z / z ^= x)
+ *   CX             pairs (control, target): x_t ^= x_c, z_c ^= z_t
+ *   M, MX          Z / X measurement; each target appends one record
+ *   X_ERROR, Z_ERROR(p)          X / Z with probability p per target
+ *   DEPOLARIZE1(p)               X, Y, Z each with p/3
+ *   DEPOLARIZE2(p) on pairs      each of the 15 non-identity Paulis with p/15
+ *   XFEED, ZFEED   pairs (record, qubit): X / Z on qubit if the record reads 1
+ *                  (classically conditioned Paulis, Methods "Simulation")
+ *   DETECTOR       XOR of the listed absolute record indices
+ *   OBSERVABLE     XOR of the listed records into observable `arg`
+ *   TICK           layer hint, no effect
+ */
+typedef enum {
+    TMCS_R = 0, TMCS_RX, TMCS_H, TMCS_S, TMCS_CX, TMCS_M, TMCS_MX,
+    TMCS_X_ERROR, TMCS_Z_ERROR, TMCS_DEPOLARIZE1, TMCS_DEPOLARIZE2,
+    TMCS_XFEED, TMCS_ZFEED, TMCS_DETECTOR, TMCS_OBSERVABLE, TMCS_TICK
+} tmcs_opcode;
+
+/* One instruction. `targets` points at n_targets uint32 (host memory, read
+ * during tmcs_circuit_build only). `p` is used by the four noise opcodes,
+ * `arg` by OBSERVABLE (observable id). 32 bytes on LP64. */
+typedef struct {
+    uint32_t code;
+    uint32_t n_targets;
+    double p;
+    uint32_t arg;
+    uint32_t reserved; /* must be 0 */
+    const uint32_t *targets;
+} tmcs_op;
+
+typedef struct tmcs_circuit tmcs_circuit; /* opaque; owned by the library */
+
+/* tmcs_circuit_build flags */
+#define TMCS_FLAG_NO_AUDIT 0x1u   /* skip the determinism audit */
+#define TMCS_FLAG_NO_PRUNE 0x2u   /* keep frame components that cannot reach an output */
+
+/*
+ * Validate and compile an op list (host only; no CUDA call).
+ * Compiles to a straight-line program over frame-component slots: liveness
+ * pruning drops every x/z component that cannot reach a detector or
+ * observable, components get shared-memory slots by interval allocation, and
+ * independent updates are grouped into layers. Unless TMCS_FLAG_NO_AUDIT is
+ * set, a 64-lane gauge-randomised noiseless run checks that every detector and
+ * observable is deterministic (TMCS_E_NONDETERMINISTIC otherwise).
+ * On success *out owns the compiled circuit; free it with tmcs_circuit_free.
+ * Errors: TMCS_E_INVALID (bad opcode, odd pair list, qubit/record index out of
+ * range, p outside [0,1] or in (0, 1e-12), reserved != 0), TMCS_E_OOM.
+ */
+int tmcs_circuit_build(const tmcs_op *ops, size_t n_ops, uint32_t flags, tmcs_circuit **out);
+
+/* Release a circuit and its device copies (all devices it was uploaded to).
+ * The caller must ensure no sampling call using it is still in flight. */
+int tmcs_circuit_free(tmcs_circuit *c);
+
+/* Sizes of a compiled circuit; any pointer may be NULL. device_bytes is the
+ * size of the compiled program one device copy occupies. */
+int tmcs_circuit_info(const tmcs_circuit *c, uint64_t *n_qubits, uint64_t *n_meas,
+                      uint64_t *n_det, uint64_t *n_obs, uint64_t *device_bytes);
+
+/* Compiler statistics of a circuit (for tuning and reports). */
+typedef struct {
+    uint64_t n_layers;        /* synchronised layers of the device program */
+    uint64_t n_slots;         /* frame-component slots (64 shots x 8 bytes each per chunk) */
+    uint64_t n_xor;           /* slot XOR updates (gates, feeds) after pruning */
+    uint64_t n_zero;          /* slot clears */
+    uint64_t n_copy;          /* slot copies */
+    uint64_t n_noise_ops;     /* noise ops with at least one live component */
+    uint64_t n_noise_units;   /* noise targets (pairs) of those ops */
+    uint64_t n_noise_segments;/* 64-unit segments of those ops */
+    uint64_t n_parity_terms;  /* record reads of detectors and observables */
+    uint64_t live_components; /* x/z components kept by pruning (of 2 * updates) */
+    uint64_t pruned_updates;  /* slot updates removed by pruning */
+} tmcs_stats;
+int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out);
+
+/*
+ * Noiseless reference measurement record on the host (CHP stabilizer
+ * tableau, Aaronson & Gottesman 2004); a random outcome resolves to 0.
+ * meas_bits: host, ceil(n_meas/8) bytes, bit i of byte b = record 8b+i.
+ * O(n_qubits^2) memory and time per measurement; not on the sampling path.
+ */
+int tmcs_reference_sample(const tmcs_circuit *c, uint8_t *meas_bits);
+
+/*
+ * Sample `shots` shots with global 64-shot chunks 0 .. ceil(shots/64)-1.
+ * detector_bits:   device, n_det * ceil(shots/64) uint64, 8-byte aligned
+ * observable_bits: device, n_obs * ceil(shots/64) uint64 (may be NULL if n_obs == 0)
+ * Asynchronous on `stream`; the first call on a device uploads the compiled
+ * program to it (synchronously, before the launch).
+ * Errors: TMCS_E_INVALID (NULL circuit/buffer, shots == 0), TMCS_E_CUDA,
+ * TMCS_E_OOM (program upload).
+ */
+int tmcs_sample(const tmcs_circuit *c, uint64_t shots, uint64_t seed,
+                uint64_t *detector_bits, uint64_t *observable_bits, void *stream);
+
+/*
+ * Resumable / shardable form: shots 64*first_chunk .. 64*first_chunk+shots-1
+ * of the stream defined by `seed`. Outputs have ceil(shots/64) words per
+ * detector; word j is global chunk first_chunk + j. Concatenating the outputs
+ * of disjoint ranges reproduces one tmcs_sample call bit for bit.
+ * first_chunk + ceil(shots/64) must not exceed 2^32.
+ */
+int tmcs_sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
+                      uint64_t *detector_bits, uint64_t *observable_bits, void *stream);
+
+/* One job of a batched launch: circuit, shots (from chunk 0), seed, outputs. */
+typedef struct {
+    const tmcs_circuit *c;
+    uint64_t shots;
+    uint64_t seed;
+    uint64_t *det;
+    uint64_t *obs;
+} tmcs_job;
+
+/*
+ * Sample many circuits of uneven size in one persistent launch on `stream`:
+ * resident CTAs pull (job, tile) work items from a device queue. Each job's
+ * output equals its own tmcs_sample call bit for bit.
+ * Errors: as tmcs_sample; TMCS_E_INVALID if any job is invalid.
+ */
+int tmcs_batch_sample(const tmcs_job *jobs, size_t n_jobs, void *stream);
+
+/* Thread-local description of the last error of this thread ("" if none). */
+const char *tmcs_last_error(void);
+
+/*
+ * Gap tables of the sampling specification for probability p in (0, 1]:
+ * ta[0..15] = TA[1..16] = floor(2^32 exp(256 a ln(1-p))),
+ * tb[0..254] = TB[1..255] = floor(2^32 exp(b ln(1-p)) expm1((256-b) ln(1-p))
+ *                                  / expm1(256 ln(1-p))).
+ * Exported so tests can compare them with an independent computation.
+ */
+int tmcs_debug_gap_tables(double p, uint32_t *ta, uint32_t *tb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TMCS_ABI_H_ */

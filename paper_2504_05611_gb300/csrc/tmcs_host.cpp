@@ -1,0 +1,859 @@
+// Host side of libtmcs: op-list validation, the slot compiler, the gap
+// tables of the sampling specification, the determinism audit and the
+// reference-sample tableau. No CUDA calls in this file.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "tmcs_internal.h"
+
+namespace tmcs {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+static bool is_noise(uint32_t code) {
+    return code == TMCS_X_ERROR || code == TMCS_Z_ERROR || code == TMCS_DEPOLARIZE1 ||
+           code == TMCS_DEPOLARIZE2;
+}
+
+static bool is_pair(uint32_t code) {
+    return code == TMCS_CX || code == TMCS_DEPOLARIZE2 || code == TMCS_XFEED || code == TMCS_ZFEED;
+}
+
+// ------------------------------------------------------------ gap tables
+//
+// Sampling specification: for noise probability p, gaps between events are
+// G = 256 A + B with A = #{a in 1..16 : w0 < TA[a]}, B = #{b in 1..255 :
+// w1 < TB[b]}; the tables below make G geometric with success probability p
+// on every position a 4096-trial segment can reach.
+
+static uint32_t frac_to_u32(double x) {
+    double v = std::floor(std::ldexp(x, 32));
+    if (!(v > 0.0)) return 0u;
+    if (v >= 4294967295.0) return 0xFFFFFFFFu;
+    return static_cast<uint32_t>(v);
+}
+
+int gap_tables(double p, uint32_t *ta, uint32_t *tb) {
+    if (!(p > 0.0 && p <= 1.0)) return fail(TMCS_E_INVALID, "gap tables need p in (0, 1]");
+    const double lq = std::log1p(-p);
+    const double den = std::expm1(256.0 * lq);
+    for (uint32_t a = 1; a <= kTA; a++) ta[a - 1] = frac_to_u32(std::exp(256.0 * double(a) * lq));
+    for (uint32_t b = 1; b <= kTB; b++) {
+        if (p >= 1.0) {
+            tb[b - 1] = 0u;
+            continue;
+        }
+        const double num = std::exp(double(b) * lq) * std::expm1(double(256 - b) * lq);
+        tb[b - 1] = frac_to_u32(num / den);
+    }
+    // The kernel finds A and B by binary search, which equals the count only
+    // for non-increasing tables.
+    for (uint32_t a = 1; a < kTA; a++)
+        if (ta[a] > ta[a - 1]) return fail(TMCS_E_INVALID, "gap table TA not monotone (p too small)");
+    for (uint32_t b = 1; b < kTB; b++)
+        if (tb[b] > tb[b - 1]) return fail(TMCS_E_INVALID, "gap table TB not monotone (p too small)");
+    return TMCS_OK;
+}
+
+size_t program_bytes(const Program &p) {
+    auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+    return al(p.layers.size() * sizeof(Layer)) + al(p.args.size() * 4) +
+           al(p.noise.size() * sizeof(NoiseDesc)) + al(p.tables.size() * 4);
+}
+
+// -------------------------------------------------------------- compiler
+
+namespace {
+
+enum IRKind : uint8_t { I_ZERO, I_XOR, I_COPY, I_NOISE, I_DET, I_OBS };
+
+struct IRInst {
+    uint8_t kind;
+    uint32_t a, b;  // ZERO a | XOR a ^= b | COPY a = b | NOISE a = index | DET/OBS a = index
+};
+
+struct IRNoise {
+    uint32_t op;
+    uint32_t kind;
+    double p;
+    std::vector<uint32_t> comp;  // (xv, zv) per target qubit
+    std::vector<uint8_t> live;   // per comp entry
+};
+
+struct IRParity {
+    uint32_t acc;  // accumulator vreg (OBS) or detector id (DET)
+    std::vector<uint32_t> recs;
+};
+
+}  // namespace
+
+int compile(tmcs_circuit *c, uint32_t flags) {
+    const bool prune = !(flags & TMCS_FLAG_NO_PRUNE);
+    const uint64_t Q = c->n_qubits;
+    uint32_t V = 0;
+    std::vector<IRInst> ir;
+    std::vector<IRNoise> noise;
+    std::vector<IRParity> pars;
+    std::vector<uint32_t> X(Q), Z(Q), rec(c->n_meas), acc(c->n_obs);
+    ir.reserve(c->ops.size() * 4 + 2 * Q);
+
+    auto newv = [&]() -> uint32_t { return V++; };
+    for (uint64_t q = 0; q < Q; q++) {
+        X[q] = newv();
+        ir.push_back({I_ZERO, X[q], 0});
+        Z[q] = newv();
+        ir.push_back({I_ZERO, Z[q], 0});
+    }
+    for (uint64_t o = 0; o < c->n_obs; o++) {
+        acc[o] = newv();
+        ir.push_back({I_ZERO, acc[o], 0});
+    }
+    uint64_t m = 0, d = 0;
+    for (size_t i = 0; i < c->ops.size(); i++) {
+        const HostOp &op = c->ops[i];
+        const uint32_t *t = c->targets.data() + op.toff;
+        switch (op.code) {
+        case TMCS_R:
+        case TMCS_RX:
+            for (uint32_t a = 0; a < op.nt; a++) {
+                X[t[a]] = newv();
+                ir.push_back({I_ZERO, X[t[a]], 0});
+                Z[t[a]] = newv();
+                ir.push_back({I_ZERO, Z[t[a]], 0});
+            }
+            break;
+        case TMCS_H:
+            for (uint32_t a = 0; a < op.nt; a++) std::swap(X[t[a]], Z[t[a]]);
+            break;
+        case TMCS_S:
+            for (uint32_t a = 0; a < op.nt; a++) ir.push_back({I_XOR, Z[t[a]], X[t[a]]});
+            break;
+        case TMCS_CX:
+            for (uint32_t a = 0; a + 1 < op.nt; a += 2) {
+                ir.push_back({I_XOR, X[t[a + 1]], X[t[a]]});
+                ir.push_back({I_XOR, Z[t[a]], Z[t[a + 1]]});
+            }
+            break;
+        case TMCS_M:
+        case TMCS_MX:
+            for (uint32_t a = 0; a < op.nt; a++) {
+                std::vector<uint32_t> &P = (op.code == TMCS_M) ? X : Z;
+                rec[m++] = P[t[a]];
+                uint32_t nv = newv();
+                ir.push_back({I_COPY, nv, P[t[a]]});
+                P[t[a]] = nv;
+            }
+            break;
+        case TMCS_X_ERROR:
+        case TMCS_Z_ERROR:
+        case TMCS_DEPOLARIZE1:
+        case TMCS_DEPOLARIZE2: {
+            if (!(op.p > 0.0) || op.nt == 0) break;
+            IRNoise nz;
+            nz.op = uint32_t(i);
+            nz.kind = op.code == TMCS_X_ERROR ? N_XERR : op.code == TMCS_Z_ERROR ? N_ZERR
+                      : op.code == TMCS_DEPOLARIZE1 ? N_DEP1 : N_DEP2;
+            nz.p = op.p;
+            nz.comp.reserve(2 * op.nt);
+            for (uint32_t a = 0; a < op.nt; a++) {
+                nz.comp.push_back(X[t[a]]);
+                nz.comp.push_back(Z[t[a]]);
+            }
+            nz.live.assign(nz.comp.size(), 0);
+            ir.push_back({I_NOISE, uint32_t(noise.size()), 0});
+            noise.push_back(std::move(nz));
+            break;
+        }
+        case TMCS_XFEED:
+            for (uint32_t a = 0; a + 1 < op.nt; a += 2) ir.push_back({I_XOR, X[t[a + 1]], rec[t[a]]});
+            break;
+        case TMCS_ZFEED:
+            for (uint32_t a = 0; a + 1 < op.nt; a += 2) ir.push_back({I_XOR, Z[t[a + 1]], rec[t[a]]});
+            break;
+        case TMCS_DETECTOR: {
+            IRParity p;
+            p.acc = uint32_t(d++);
+            for (uint32_t a = 0; a < op.nt; a++) p.recs.push_back(rec[t[a]]);
+            ir.push_back({I_DET, uint32_t(pars.size()), 0});
+            pars.push_back(std::move(p));
+            break;
+        }
+        case TMCS_OBSERVABLE: {
+            IRParity p;
+            p.acc = acc[op.arg];
+            for (uint32_t a = 0; a < op.nt; a++) p.recs.push_back(rec[t[a]]);
+            ir.push_back({I_OBS, uint32_t(pars.size()), 0});
+            pars.push_back(std::move(p));
+            break;
+        }
+        default:
+            break;
+        }
+    }
+
+    // ---- backward liveness: keep only updates that can reach an output
+    std::vector<uint8_t> live(V, 0), keep(ir.size(), 0);
+    for (uint64_t o = 0; o < c->n_obs; o++) live[acc[o]] = 1;
+    uint64_t pruned = 0;
+    for (size_t k = ir.size(); k-- > 0;) {
+        const IRInst &in = ir[k];
+        switch (in.kind) {
+        case I_ZERO:
+            if (live[in.a] || !prune) keep[k] = 1;
+            live[in.a] = 0;
+            break;
+        case I_COPY:
+            if (live[in.a] || !prune) {
+                keep[k] = 1;
+                live[in.b] = 1;
+            } else {
+                pruned++;
+            }
+            live[in.a] = 0;
+            break;
+        case I_XOR:
+            if (live[in.a] || !prune) {
+                keep[k] = 1;
+                live[in.a] = 1;
+                live[in.b] = 1;
+            } else {
+                pruned++;
+            }
+            break;
+        case I_NOISE: {
+            IRNoise &nz = noise[in.a];
+            bool any = false;
+            for (size_t e = 0; e < nz.comp.size(); e++) {
+                const bool is_x = (e & 1) == 0;
+                // X_ERROR touches only x components, Z_ERROR only z components
+                if (nz.kind == N_XERR && !is_x) continue;
+                if (nz.kind == N_ZERR && is_x) continue;
+                if (live[nz.comp[e]] || !prune) {
+                    nz.live[e] = 1;
+                    live[nz.comp[e]] = 1;
+                    any = true;
+                }
+            }
+            if (any) keep[k] = 1;
+            break;
+        }
+        case I_DET:
+        case I_OBS:
+            keep[k] = 1;
+            for (uint32_t r : pars[in.a].recs) live[r] = 1;
+            if (in.kind == I_OBS) live[pars[in.a].acc] = 1;
+            break;
+        }
+    }
+
+    // ---- layering: maximal runs of independent same-kind instructions
+    std::vector<uint32_t> layer_of(ir.size(), 0xFFFFFFFFu);
+    std::vector<uint32_t> wstamp(V, 0xFFFFFFFFu), rstamp(V, 0xFFFFFFFFu);
+    std::vector<uint8_t> layer_kind;
+    std::vector<std::vector<uint32_t>> layer_insts;
+    int cur_kind = -1;
+    uint32_t L = 0xFFFFFFFFu;
+    auto open = [&](int kind) {
+        layer_kind.push_back(uint8_t(kind));
+        layer_insts.emplace_back();
+        L = uint32_t(layer_kind.size() - 1);
+        cur_kind = kind;
+    };
+    for (size_t k = 0; k < ir.size(); k++) {
+        if (!keep[k]) continue;
+        const IRInst &in = ir[k];
+        bool ok = (cur_kind == int(in.kind)) && in.kind != I_NOISE;
+        if (ok) {
+            switch (in.kind) {
+            case I_ZERO:
+                ok = wstamp[in.a] != L && rstamp[in.a] != L;
+                break;
+            case I_XOR:
+            case I_COPY:
+                ok = wstamp[in.a] != L && rstamp[in.a] != L && wstamp[in.b] != L;
+                break;
+            case I_DET:
+                for (uint32_t r : pars[in.a].recs) ok = ok && wstamp[r] != L;
+                break;
+            case I_OBS:
+                ok = wstamp[pars[in.a].acc] != L && rstamp[pars[in.a].acc] != L;
+                for (uint32_t r : pars[in.a].recs) ok = ok && wstamp[r] != L;
+                break;
+            }
+        }
+        if (!ok) open(in.kind);
+        layer_of[k] = L;
+        layer_insts[L].push_back(uint32_t(k));
+        switch (in.kind) {
+        case I_ZERO:
+            wstamp[in.a] = L;
+            break;
+        case I_XOR:
+        case I_COPY:
+            wstamp[in.a] = L;
+            rstamp[in.b] = L;
+            break;
+        case I_DET:
+            for (uint32_t r : pars[in.a].recs) rstamp[r] = L;
+            break;
+        case I_OBS:
+            wstamp[pars[in.a].acc] = L;
+            for (uint32_t r : pars[in.a].recs) rstamp[r] = L;
+            break;
+        case I_NOISE:
+            cur_kind = -1;  // noise layers hold one op
+            break;
+        }
+    }
+    const uint32_t n_layers_body = uint32_t(layer_kind.size());
+    const uint32_t obsout_layer = n_layers_body;  // final layer writes observables
+
+    // ---- live ranges in layers and interval slot allocation
+    std::vector<uint32_t> def_layer(V, 0xFFFFFFFFu), last_layer(V, 0);
+    std::vector<uint8_t> used(V, 0);
+    auto touch = [&](uint32_t v, uint32_t l) {
+        used[v] = 1;
+        last_layer[v] = std::max(last_layer[v], l);
+    };
+    for (size_t k = 0; k < ir.size(); k++) {
+        if (!keep[k]) continue;
+        const IRInst &in = ir[k];
+        const uint32_t l = layer_of[k];
+        switch (in.kind) {
+        case I_ZERO:
+            def_layer[in.a] = l;
+            touch(in.a, l);
+            break;
+        case I_COPY:
+            def_layer[in.a] = l;
+            touch(in.a, l);
+            touch(in.b, l);
+            break;
+        case I_XOR:
+            touch(in.a, l);
+            touch(in.b, l);
+            break;
+        case I_NOISE: {
+            const IRNoise &nz = noise[in.a];
+            for (size_t e = 0; e < nz.comp.size(); e++)
+                if (nz.live[e]) touch(nz.comp[e], l);
+            break;
+        }
+        case I_DET:
+        case I_OBS:
+            for (uint32_t r : pars[in.a].recs) touch(r, l);
+            if (in.kind == I_OBS) touch(pars[in.a].acc, l);
+            break;
+        }
+    }
+    for (uint64_t o = 0; o < c->n_obs; o++) touch(acc[o], obsout_layer);
+    for (uint32_t v = 0; v < V; v++) {
+        if (used[v] && def_layer[v] == 0xFFFFFFFFu)
+            return fail(TMCS_E_INVALID, "internal: frame value used without definition");
+    }
+    std::vector<std::vector<uint32_t>> defs_at(n_layers_body + 1), frees_at(n_layers_body + 1);
+    for (uint32_t v = 0; v < V; v++) {
+        if (!used[v]) continue;
+        defs_at[def_layer[v]].push_back(v);
+        frees_at[last_layer[v]].push_back(v);
+    }
+    std::vector<uint32_t> slot(V, kDeadSlot), free_list;
+    uint32_t n_slots = 0;
+    for (uint32_t l = 0; l <= n_layers_body; l++) {
+        for (uint32_t v : defs_at[l]) {
+            if (!free_list.empty()) {
+                slot[v] = free_list.back();
+                free_list.pop_back();
+            } else {
+                slot[v] = n_slots++;
+            }
+        }
+        for (uint32_t v : frees_at[l]) free_list.push_back(slot[v]);
+    }
+    if (n_slots > kMaxSlots)
+        return fail(TMCS_E_INVALID, "circuit needs " + std::to_string(n_slots) +
+                                        " frame slots; at most 65534 are supported");
+
+    // ---- gap tables
+    Program &P = c->prog;
+    P = Program();
+    std::unordered_map<uint64_t, uint32_t> table_id;
+    auto table_for = [&](double p, uint32_t *out) -> int {
+        uint64_t key;
+        std::memcpy(&key, &p, 8);
+        auto it = table_id.find(key);
+        if (it != table_id.end()) {
+            *out = it->second;
+            return TMCS_OK;
+        }
+        uint32_t id = uint32_t(P.table_p.size());
+        P.table_p.push_back(p);
+        P.tables.resize(P.tables.size() + kTableWords, 0u);
+        int rc = gap_tables(p, &P.tables[size_t(id) * kTableWords], &P.tables[size_t(id) * kTableWords + kTBOff]);
+        if (rc) return rc;
+        table_id[key] = id;
+        *out = id;
+        return TMCS_OK;
+    };
+
+    // ---- emission
+    tmcs_stats &S = c->stats;
+    S = tmcs_stats{};
+    for (uint32_t l = 0; l < n_layers_body; l++) {
+        const std::vector<uint32_t> &ins = layer_insts[l];
+        Layer ly{};
+        ly.count = uint32_t(ins.size());
+        ly.off = uint32_t(P.args.size());
+        switch (layer_kind[l]) {
+        case I_ZERO:
+            ly.kind = L_ZERO;
+            for (uint32_t k : ins) P.args.push_back(slot[ir[k].a]);
+            S.n_zero += ins.size();
+            break;
+        case I_XOR:
+        case I_COPY:
+            ly.kind = layer_kind[l] == I_XOR ? L_XOR : L_COPY;
+            for (uint32_t k : ins) P.args.push_back(slot[ir[k].a] | (slot[ir[k].b] << 16));
+            (layer_kind[l] == I_XOR ? S.n_xor : S.n_copy) += ins.size();
+            break;
+        case I_NOISE: {
+            const IRNoise &nz = noise[ir[ins[0]].a];
+            NoiseDesc nd{};
+            nd.op_index = nz.op;
+            nd.kind = nz.kind;
+            int rc = table_for(nz.p, &nd.table);
+            if (rc) return rc;
+            const uint32_t nq = uint32_t(nz.comp.size() / 2);
+            nd.n_units = nz.kind == N_DEP2 ? nq / 2 : nq;
+            nd.n_seg = (nd.n_units + kSegUnits - 1) / kSegUnits;
+            nd.tgt_off = uint32_t(P.args.size());
+            for (uint32_t q = 0; q < nq; q++) {
+                uint32_t xs = nz.live[2 * q] ? slot[nz.comp[2 * q]] : kDeadSlot;
+                uint32_t zs = nz.live[2 * q + 1] ? slot[nz.comp[2 * q + 1]] : kDeadSlot;
+                P.args.push_back(xs | (zs << 16));
+                S.live_components += (xs != kDeadSlot) + (zs != kDeadSlot);
+            }
+            ly.kind = L_NOISE;
+            ly.count = nd.n_seg;
+            ly.off = nd.tgt_off;
+            ly.aux = uint32_t(P.noise.size());
+            P.noise.push_back(nd);
+            S.n_noise_ops++;
+            S.n_noise_units += nd.n_units;
+            S.n_noise_segments += nd.n_seg;
+            break;
+        }
+        case I_DET:
+        case I_OBS: {
+            ly.kind = layer_kind[l] == I_DET ? L_DET : L_OBS;
+            ly.aux = layer_kind[l] == I_DET ? pars[ir[ins[0]].a].acc : 0;
+            const size_t bounds = P.args.size();
+            P.args.resize(bounds + ins.size() + 1);
+            for (size_t e = 0; e < ins.size(); e++) {
+                const IRParity &pp = pars[ir[ins[e]].a];
+                P.args[bounds + e] = uint32_t(P.args.size());
+                if (ly.kind == L_OBS) P.args.push_back(slot[pp.acc]);
+                for (uint32_t r : pp.recs) P.args.push_back(slot[r]);
+                S.n_parity_terms += pp.recs.size();
+            }
+            P.args[bounds + ins.size()] = uint32_t(P.args.size());
+            break;
+        }
+        }
+        P.layers.push_back(ly);
+    }
+    if (c->n_obs) {
+        Layer ly{};
+        ly.kind = L_OBSOUT;
+        ly.count = uint32_t(c->n_obs);
+        ly.off = uint32_t(P.args.size());
+        for (uint64_t o = 0; o < c->n_obs; o++) P.args.push_back(slot[acc[o]]);
+        P.layers.push_back(ly);
+    }
+    P.n_slots = n_slots;
+    P.n_det = c->n_det;
+    P.n_obs = c->n_obs;
+    S.n_layers = P.layers.size();
+    S.n_slots = n_slots;
+    S.pruned_updates = pruned;
+    return TMCS_OK;
+}
+
+// ------------------------------------------------------------- audit
+//
+// 64-lane noiseless frame run with random gauge Paulis after every reset and
+// measurement (random Z after R/M, random X after RX/MX): these leave the
+// state unchanged, so every deterministic parity stays 0 in every lane while
+// a random one is 1 in about half of them.
+
+static uint64_t mix64(uint64_t &s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int audit(const tmcs_circuit *c) {
+    std::vector<uint64_t> x(c->n_qubits), z(c->n_qubits), rec(c->n_meas), obs(c->n_obs);
+    for (int pass = 0; pass < 2; pass++) {
+        uint64_t s = 0x5EEDull + 1000003ull * uint64_t(pass);
+        std::fill(x.begin(), x.end(), 0);
+        std::fill(z.begin(), z.end(), 0);
+        std::fill(obs.begin(), obs.end(), 0);
+        uint64_t m = 0, d = 0;
+        for (const HostOp &op : c->ops) {
+            const uint32_t *t = c->targets.data() + op.toff;
+            switch (op.code) {
+            case TMCS_R:
+                for (uint32_t a = 0; a < op.nt; a++) { x[t[a]] = 0; z[t[a]] = mix64(s); }
+                break;
+            case TMCS_RX:
+                for (uint32_t a = 0; a < op.nt; a++) { z[t[a]] = 0; x[t[a]] = mix64(s); }
+                break;
+            case TMCS_H:
+                for (uint32_t a = 0; a < op.nt; a++) std::swap(x[t[a]], z[t[a]]);
+                break;
+            case TMCS_S:
+                for (uint32_t a = 0; a < op.nt; a++) z[t[a]] ^= x[t[a]];
+                break;
+            case TMCS_CX:
+                for (uint32_t a = 0; a + 1 < op.nt; a += 2) {
+                    x[t[a + 1]] ^= x[t[a]];
+                    z[t[a]] ^= z[t[a + 1]];
+                }
+                break;
+            case TMCS_M:
+                for (uint32_t a = 0; a < op.nt; a++) { rec[m++] = x[t[a]]; z[t[a]] ^= mix64(s); }
+                break;
+            case TMCS_MX:
+                for (uint32_t a = 0; a < op.nt; a++) { rec[m++] = z[t[a]]; x[t[a]] ^= mix64(s); }
+                break;
+            case TMCS_XFEED:
+                for (uint32_t a = 0; a + 1 < op.nt; a += 2) x[t[a + 1]] ^= rec[t[a]];
+                break;
+            case TMCS_ZFEED:
+                for (uint32_t a = 0; a + 1 < op.nt; a += 2) z[t[a + 1]] ^= rec[t[a]];
+                break;
+            case TMCS_DETECTOR: {
+                uint64_t v = 0;
+                for (uint32_t a = 0; a < op.nt; a++) v ^= rec[t[a]];
+                if (v)
+                    return fail(TMCS_E_NONDETERMINISTIC,
+                                "detector " + std::to_string(d) + " is not deterministic");
+                d++;
+                break;
+            }
+            case TMCS_OBSERVABLE:
+                for (uint32_t a = 0; a < op.nt; a++) obs[op.arg] ^= rec[t[a]];
+                break;
+            default:
+                break;
+            }
+        }
+        for (uint64_t o = 0; o < c->n_obs; o++)
+            if (obs[o])
+                return fail(TMCS_E_NONDETERMINISTIC,
+                            "observable " + std::to_string(o) + " is not deterministic");
+    }
+    return TMCS_OK;
+}
+
+// ------------------------------------------------------ reference sample
+//
+// CHP tableau (Aaronson & Gottesman, PRA 70, 052328, 2004): rows 0..n-1 are
+// destabilizers, n..2n-1 stabilizers, row 2n is scratch; each row is packed
+// x bits, z bits and a sign. Random outcomes resolve to 0.
+
+namespace {
+
+struct Tableau {
+    size_t n, W;
+    std::vector<uint64_t> x, z;
+    std::vector<uint8_t> r;
+    explicit Tableau(size_t n_) : n(n_), W((n_ + 63) / 64), x((2 * n_ + 1) * W), z((2 * n_ + 1) * W), r(2 * n_ + 1) {
+        for (size_t i = 0; i < n; i++) {
+            x[i * W + i / 64] |= 1ull << (i % 64);
+            z[(n + i) * W + i / 64] |= 1ull << (i % 64);
+        }
+    }
+    uint64_t *xr(size_t i) { return &x[i * W]; }
+    uint64_t *zr(size_t i) { return &z[i * W]; }
+    bool xb(size_t i, size_t a) const { return (x[i * W + a / 64] >> (a % 64)) & 1; }
+
+    void h(size_t a) {
+        const size_t w = a / 64;
+        const uint64_t bit = 1ull << (a % 64);
+        for (size_t i = 0; i < 2 * n; i++) {
+            uint64_t &xw = x[i * W + w], &zw = z[i * W + w];
+            const bool xi = xw & bit, zi = zw & bit;
+            r[i] ^= uint8_t(xi && zi);
+            if (xi != zi) { xw ^= bit; zw ^= bit; }
+        }
+    }
+    void s(size_t a) {
+        const size_t w = a / 64;
+        const uint64_t bit = 1ull << (a % 64);
+        for (size_t i = 0; i < 2 * n; i++) {
+            uint64_t &xw = x[i * W + w], &zw = z[i * W + w];
+            const bool xi = xw & bit, zi = zw & bit;
+            r[i] ^= uint8_t(xi && zi);
+            if (xi) zw ^= bit;
+        }
+    }
+    void cx(size_t a, size_t b) {
+        const size_t wa = a / 64, wb = b / 64;
+        const uint64_t ba = 1ull << (a % 64), bb = 1ull << (b % 64);
+        for (size_t i = 0; i < 2 * n; i++) {
+            uint64_t *xw = &x[i * W], *zw = &z[i * W];
+            const bool xa = xw[wa] & ba, za = zw[wa] & ba, xb_ = xw[wb] & bb, zb = zw[wb] & bb;
+            r[i] ^= uint8_t(xa && zb && (xb_ == za));
+            if (xa) xw[wb] ^= bb;
+            if (zb) zw[wa] ^= ba;
+        }
+    }
+    void pauli_x(size_t a) {
+        for (size_t i = 0; i < 2 * n; i++) r[i] ^= uint8_t((z[i * W + a / 64] >> (a % 64)) & 1);
+    }
+    void pauli_z(size_t a) {
+        for (size_t i = 0; i < 2 * n; i++) r[i] ^= uint8_t((x[i * W + a / 64] >> (a % 64)) & 1);
+    }
+    // row h <- row i * row h, with the sign rule of the tableau algorithm
+    void rowsum(size_t h, size_t i) {
+        int64_t sum = 2 * int64_t(r[h]) + 2 * int64_t(r[i]);
+        uint64_t *x1 = xr(i), *z1 = zr(i), *x2 = xr(h), *z2 = zr(h);
+        for (size_t w = 0; w < W; w++) {
+            const uint64_t a = x1[w], b = z1[w], cx_ = x2[w], dz = z2[w];
+            // g = +1 / -1 cases of the phase exponent of P1 * P2
+            const uint64_t plus = (a & b & ~cx_ & dz) | (a & ~b & cx_ & dz) | (~a & b & cx_ & ~dz);
+            const uint64_t minus = (a & b & cx_ & ~dz) | (a & ~b & ~cx_ & dz) | (~a & b & cx_ & dz);
+            sum += int64_t(__builtin_popcountll(plus)) - int64_t(__builtin_popcountll(minus));
+            x2[w] ^= a;
+            z2[w] ^= b;
+        }
+        sum %= 4;
+        if (sum < 0) sum += 4;
+        r[h] = uint8_t(sum == 2);
+    }
+    int measure(size_t a) {
+        size_t p = SIZE_MAX;
+        for (size_t i = n; i < 2 * n; i++)
+            if (xb(i, a)) { p = i; break; }
+        if (p != SIZE_MAX) {
+            for (size_t i = 0; i < 2 * n; i++)
+                if (i != p && xb(i, a)) rowsum(i, p);
+            std::memcpy(xr(p - n), xr(p), W * 8);
+            std::memcpy(zr(p - n), zr(p), W * 8);
+            r[p - n] = r[p];
+            std::memset(xr(p), 0, W * 8);
+            std::memset(zr(p), 0, W * 8);
+            zr(p)[a / 64] |= 1ull << (a % 64);
+            r[p] = 0;
+            return 0;
+        }
+        const size_t sc = 2 * n;
+        std::memset(xr(sc), 0, W * 8);
+        std::memset(zr(sc), 0, W * 8);
+        r[sc] = 0;
+        for (size_t i = 0; i < n; i++)
+            if (xb(i, a)) rowsum(sc, i + n);
+        return r[sc];
+    }
+};
+
+}  // namespace
+
+}  // namespace tmcs
+
+using namespace tmcs;
+
+extern "C" {
+
+const char *tmcs_last_error(void) { return g_last_error.c_str(); }
+
+int tmcs_debug_gap_tables(double p, uint32_t *ta, uint32_t *tb) {
+    if (!ta || !tb) return fail(TMCS_E_INVALID, "null table pointer");
+    return gap_tables(p, ta, tb);
+}
+
+int tmcs_circuit_build(const tmcs_op *ops, size_t n_ops, uint32_t flags, tmcs_circuit **out) {
+    if (!out) return fail(TMCS_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (n_ops && !ops) return fail(TMCS_E_INVALID, "ops is NULL");
+    if (flags & ~uint32_t(TMCS_FLAG_NO_AUDIT | TMCS_FLAG_NO_PRUNE))
+        return fail(TMCS_E_INVALID, "unknown flag bits");
+    tmcs_circuit *c = new (std::nothrow) tmcs_circuit();
+    if (!c) return fail(TMCS_E_OOM, "out of host memory");
+    try {
+        c->ops.reserve(n_ops);
+        uint64_t m = 0, d = 0, q = 0, nobs = 0;
+        for (size_t i = 0; i < n_ops; i++) {
+            const tmcs_op &op = ops[i];
+            const std::string where = "op " + std::to_string(i) + ": ";
+            if (op.code > TMCS_TICK) { delete c; return fail(TMCS_E_INVALID, where + "unknown opcode"); }
+            if (op.reserved) { delete c; return fail(TMCS_E_INVALID, where + "reserved field must be 0"); }
+            if (op.n_targets && !op.targets) { delete c; return fail(TMCS_E_INVALID, where + "targets is NULL"); }
+            if (is_pair(op.code) && (op.n_targets & 1)) { delete c; return fail(TMCS_E_INVALID, where + "odd target count"); }
+            if (is_noise(op.code)) {
+                if (!(op.p >= 0.0 && op.p <= 1.0)) { delete c; return fail(TMCS_E_INVALID, where + "probability outside [0, 1]"); }
+                if (op.p > 0.0 && op.p < 1e-12) { delete c; return fail(TMCS_E_INVALID, where + "probability below 1e-12"); }
+            }
+            if (c->targets.size() + op.n_targets > 0xFFFFFFFFull) { delete c; return fail(TMCS_E_INVALID, "too many targets"); }
+            HostOp h{op.code, op.p, op.arg, uint32_t(c->targets.size()), op.n_targets};
+            const uint32_t *t = op.targets;
+            if (op.code == TMCS_DETECTOR || op.code == TMCS_OBSERVABLE) {
+                for (uint32_t a = 0; a < op.n_targets; a++)
+                    if (t[a] >= m) { delete c; return fail(TMCS_E_INVALID, where + "record index out of range"); }
+                if (op.code == TMCS_DETECTOR) d++;
+                else nobs = std::max<uint64_t>(nobs, uint64_t(op.arg) + 1);
+            } else if (op.code == TMCS_XFEED || op.code == TMCS_ZFEED) {
+                for (uint32_t a = 0; a + 1 < op.n_targets; a += 2) {
+                    if (t[a] >= m) { delete c; return fail(TMCS_E_INVALID, where + "record index out of range"); }
+                    q = std::max<uint64_t>(q, uint64_t(t[a + 1]) + 1);
+                }
+            } else if (op.code != TMCS_TICK) {
+                for (uint32_t a = 0; a < op.n_targets; a++) q = std::max<uint64_t>(q, uint64_t(t[a]) + 1);
+                if (op.code == TMCS_CX || op.code == TMCS_DEPOLARIZE2)
+                    for (uint32_t a = 0; a + 1 < op.n_targets; a += 2)
+                        if (t[a] == t[a + 1]) { delete c; return fail(TMCS_E_INVALID, where + "pair on one qubit"); }
+            }
+            if (op.code == TMCS_M || op.code == TMCS_MX) m += op.n_targets;
+            c->targets.insert(c->targets.end(), t, t + op.n_targets);
+            c->ops.push_back(h);
+        }
+        if (m > 0xFFFFFFFFull || q > 0xFFFFFFFFull || n_ops > 0xFFFFFFFFull) {
+            delete c;
+            return fail(TMCS_E_INVALID, "circuit too large");
+        }
+        // Noise ops must hit distinct qubits: the sampler applies events of
+        // different target units concurrently.
+        {
+            std::vector<uint32_t> seen(q, 0xFFFFFFFFu);
+            for (size_t i = 0; i < c->ops.size(); i++) {
+                const HostOp &op = c->ops[i];
+                if (!is_noise(op.code)) continue;
+                for (uint32_t a = 0; a < op.nt; a++) {
+                    uint32_t v = c->targets[op.toff + a];
+                    if (seen[v] == uint32_t(i)) {
+                        delete c;
+                        return fail(TMCS_E_INVALID, "op " + std::to_string(i) + ": noise op repeats a qubit");
+                    }
+                    seen[v] = uint32_t(i);
+                }
+            }
+        }
+        c->n_qubits = q;
+        c->n_meas = m;
+        c->n_det = d;
+        c->n_obs = nobs;
+        if (!(flags & TMCS_FLAG_NO_AUDIT)) {
+            int rc = audit(c);
+            if (rc) { delete c; return rc; }
+        }
+        int rc = compile(c, flags);
+        if (rc) { delete c; return rc; }
+    } catch (const std::bad_alloc &) {
+        delete c;
+        return fail(TMCS_E_OOM, "out of host memory while compiling");
+    }
+    *out = c;
+    set_error("");
+    return TMCS_OK;
+}
+
+int tmcs_circuit_free(tmcs_circuit *c) {
+    if (!c) return TMCS_OK;
+    free_device_programs(c);
+    delete c;
+    return TMCS_OK;
+}
+
+int tmcs_circuit_info(const tmcs_circuit *c, uint64_t *n_qubits, uint64_t *n_meas, uint64_t *n_det,
+                      uint64_t *n_obs, uint64_t *device_bytes) {
+    if (!c) return fail(TMCS_E_INVALID, "circuit is NULL");
+    if (n_qubits) *n_qubits = c->n_qubits;
+    if (n_meas) *n_meas = c->n_meas;
+    if (n_det) *n_det = c->n_det;
+    if (n_obs) *n_obs = c->n_obs;
+    if (device_bytes) *device_bytes = program_bytes(c->prog);
+    return TMCS_OK;
+}
+
+int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out) {
+    if (!c || !out) return fail(TMCS_E_INVALID, "NULL argument");
+    *out = c->stats;
+    return TMCS_OK;
+}
+
+int tmcs_reference_sample(const tmcs_circuit *c, uint8_t *meas_bits) {
+    if (!c || (!meas_bits && c->n_meas)) return fail(TMCS_E_INVALID, "NULL argument");
+    try {
+        Tableau T(c->n_qubits);
+        std::vector<uint8_t> rec;
+        rec.reserve(c->n_meas);
+        for (const HostOp &op : c->ops) {
+            const uint32_t *t = c->targets.data() + op.toff;
+            switch (op.code) {
+            case TMCS_R:
+                for (uint32_t a = 0; a < op.nt; a++)
+                    if (T.measure(t[a])) T.pauli_x(t[a]);
+                break;
+            case TMCS_RX:
+                for (uint32_t a = 0; a < op.nt; a++) {
+                    if (T.measure(t[a])) T.pauli_x(t[a]);
+                    T.h(t[a]);
+                }
+                break;
+            case TMCS_H:
+                for (uint32_t a = 0; a < op.nt; a++) T.h(t[a]);
+                break;
+            case TMCS_S:
+                for (uint32_t a = 0; a < op.nt; a++) T.s(t[a]);
+                break;
+            case TMCS_CX:
+                for (uint32_t a = 0; a + 1 < op.nt; a += 2) T.cx(t[a], t[a + 1]);
+                break;
+            case TMCS_M:
+                for (uint32_t a = 0; a < op.nt; a++) rec.push_back(uint8_t(T.measure(t[a])));
+                break;
+            case TMCS_MX:
+                for (uint32_t a = 0; a < op.nt; a++) {
+                    T.h(t[a]);
+                    rec.push_back(uint8_t(T.measure(t[a])));
+                    T.h(t[a]);
+                }
+                break;
+            case TMCS_XFEED:
+                for (uint32_t a = 0; a + 1 < op.nt; a += 2)
+                    if (rec[t[a]]) T.pauli_x(t[a + 1]);
+                break;
+            case TMCS_ZFEED:
+                for (uint32_t a = 0; a + 1 < op.nt; a += 2)
+                    if (rec[t[a]]) T.pauli_z(t[a + 1]);
+                break;
+            default:
+                break;
+            }
+        }
+        std::memset(meas_bits, 0, (c->n_meas + 7) / 8);
+        for (size_t i = 0; i < rec.size(); i++)
+            if (rec[i]) meas_bits[i / 8] |= uint8_t(1u << (i % 8));
+    } catch (const std::bad_alloc &) {
+        return fail(TMCS_E_OOM, "out of host memory for the tableau");
+    }
+    return TMCS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// Internal definitions shared by the host compiler (tmcs_host.cpp) and the
+// CUDA sampler (tmcs_sample.cu). Not part of the public ABI.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "tmcs.h"
+
+namespace tmcs {
+
+// ---------------------------------------------------------------- program
+//
+// A compiled circuit is a straight-line program over "slots": shared-memory
+// rows that each hold one frame component (the x or z bit of one qubit over
+// the CTA's shots) or one measurement record. Gates become slot XORs/copies
+// (H is a renaming and costs nothing), resets become clears, noise ops become
+// event streams XORed into slots, detectors/observables become parities of
+// record slots. Layers group independent updates; the kernel runs one layer
+// at a time with a barrier in between.
+
+enum LayerKind : uint32_t {
+    L_ZERO = 0,   // args[off+i] = slot                       -> slot = 0
+    L_XOR = 1,    // args[off+i] = dst | src << 16            -> dst ^= src
+    L_COPY = 2,   // args[off+i] = dst | src << 16            -> dst = src
+    L_NOISE = 3,  // aux = noise descriptor index, count = segments
+    L_DET = 4,    // args[off+i], i <= count: CSR bounds into args (slot lists);
+                  // aux = first detector id
+    L_OBS = 5,    // CSR as L_DET; list[0] = accumulator slot, rest = record slots
+    L_OBSOUT = 6, // args[off+i] = accumulator slot of observable i (count = n_obs)
+};
+
+struct Layer {
+    uint32_t kind;
+    uint32_t count;
+    uint32_t off;
+    uint32_t aux;
+};
+
+enum NoiseKind : uint32_t { N_XERR = 0, N_ZERR = 1, N_DEP1 = 2, N_DEP2 = 3 };
+
+// Targets of a noise op live at args[tgt_off ...]: one word per qubit,
+// x slot in the low 16 bits, z slot in the high 16 bits, 0xFFFF = component
+// pruned (it cannot reach any output). DEPOLARIZE2 has two words per unit.
+struct NoiseDesc {
+    uint32_t op_index;  // index of the op in the user's op list (RNG counter word 2)
+    uint32_t kind;      // NoiseKind
+    uint32_t table;     // gap-table index
+    uint32_t n_units;   // targets (pairs for DEPOLARIZE2)
+    uint32_t n_seg;     // ceil(n_units / 64)
+    uint32_t tgt_off;   // offset into args
+    uint32_t pad0, pad1;
+};
+
+constexpr uint32_t kSegUnits = 64;     // units per noise segment
+constexpr uint32_t kTA = 16;           // TA[1..16]
+constexpr uint32_t kTB = 255;          // TB[1..255]
+// Per probability: words [0,16) = TA[1..16], [16,32) = 0, [32,287) =
+// TB[1..255], [287] = 0. The zero padding lets the kernel find A and B by
+// branch-free binary search with power-of-two steps.
+constexpr uint32_t kTBOff = 32;
+constexpr uint32_t kTableWords = 288;
+constexpr uint32_t kDeadSlot = 0xFFFFu;
+constexpr uint32_t kMaxSlots = 0xFFFEu;
+
+struct Program {
+    std::vector<Layer> layers;
+    std::vector<uint32_t> args;
+    std::vector<NoiseDesc> noise;
+    std::vector<uint32_t> tables;   // kTableWords per distinct p
+    std::vector<double> table_p;
+    uint32_t n_slots = 0;
+    uint64_t n_det = 0, n_obs = 0;
+};
+
+// One device copy of a program.
+struct DeviceProgram {
+    int device = -1;
+    void *base = nullptr;  // single allocation holding everything below
+    size_t bytes = 0;
+    const Layer *layers = nullptr;
+    const uint32_t *args = nullptr;
+    const NoiseDesc *noise = nullptr;
+    const uint32_t *tables = nullptr;
+};
+
+// Host-side copy of one user op.
+struct HostOp {
+    uint32_t code;
+    double p;
+    uint32_t arg;
+    uint32_t toff, nt;
+};
+
+}  // namespace tmcs
+
+struct tmcs_circuit {
+    uint64_t n_qubits = 0, n_meas = 0, n_det = 0, n_obs = 0;
+    std::vector<tmcs::HostOp> ops;
+    std::vector<uint32_t> targets;
+    tmcs::Program prog;
+    tmcs_stats stats{};
+    mutable std::mutex mu;
+    mutable std::map<int, tmcs::DeviceProgram> dev;
+};
+
+namespace tmcs {
+
+// Host side (tmcs_host.cpp)
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int compile(tmcs_circuit *c, uint32_t flags);
+int gap_tables(double p, uint32_t *ta, uint32_t *tb);
+int audit(const tmcs_circuit *c);
+size_t program_bytes(const Program &p);
+
+// Device side (tmcs_sample.cu)
+void free_device_programs(tmcs_circuit *c);
+
+}  // namespace tmcs

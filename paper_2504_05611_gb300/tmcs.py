@@ -1,0 +1,251 @@
+"""ctypes binding of ``libtmcs.so`` (argument marshalling only).
+
+Function names mirror the C ABI in ``include/tmcs.h``; every sampling step
+runs in the library's CUDA kernels. Device buffers are PyTorch CUDA tensors
+(int64 or uint64, contiguous; their bits are the detector words) or raw
+device pointers; streams are ``torch.cuda.Stream`` objects, raw
+``cudaStream_t`` integers, or None for the current PyTorch stream.
+
+The library must be built (``python -m paper_2504_05611_gb300.build`` or
+``__graft_entry__.build()``); importing this module does not build it, and
+every call raises ``RuntimeError`` if it is missing. There is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Iterable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from .circuits import OPCODE_ID, Circuit
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtmcs.so")
+
+TMCS_OK = 0
+STATUS = {0: "TMCS_OK", 1: "TMCS_E_INVALID", 2: "TMCS_E_NONDETERMINISTIC", 3: "TMCS_E_OOM",
+          4: "TMCS_E_CUDA", 5: "TMCS_E_TIMEOUT", 6: "TMCS_E_BUFFER"}
+TMCS_FLAG_NO_AUDIT = 0x1
+TMCS_FLAG_NO_PRUNE = 0x2
+
+OP_DTYPE = np.dtype([("code", "<u4"), ("n_targets", "<u4"), ("p", "<f8"), ("arg", "<u4"),
+                     ("reserved", "<u4"), ("targets", "<u8")])
+assert OP_DTYPE.itemsize == 32
+
+STATS_FIELDS = ("n_layers", "n_slots", "n_xor", "n_zero", "n_copy", "n_noise_ops", "n_noise_units",
+                "n_noise_segments", "n_parity_terms", "live_components", "pruned_updates")
+
+
+class TmcsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_void_p), ("shots", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("det", ctypes.c_void_p), ("obs", ctypes.c_void_p)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in STATS_FIELDS]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libtmcs.so (once); raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2504_05611_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, U64, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+        L.tmcs_circuit_build.argtypes = [P, ctypes.c_size_t, ctypes.c_uint32, ctypes.POINTER(P)]
+        L.tmcs_circuit_free.argtypes = [P]
+        L.tmcs_circuit_info.argtypes = [P, P, P, P, P, P]
+        L.tmcs_circuit_stats.argtypes = [P, P]
+        L.tmcs_reference_sample.argtypes = [P, P]
+        L.tmcs_sample.argtypes = [P, U64, U64, P, P, P]
+        L.tmcs_sample_range.argtypes = [P, U64, U64, U64, P, P, P]
+        L.tmcs_batch_sample.argtypes = [P, ctypes.c_size_t, P]
+        L.tmcs_debug_gap_tables.argtypes = [ctypes.c_double, P, P]
+        L.tmcs_last_error.argtypes = []
+        L.tmcs_last_error.restype = ctypes.c_char_p
+        for f in ("tmcs_circuit_build", "tmcs_circuit_free", "tmcs_circuit_info", "tmcs_circuit_stats",
+                  "tmcs_reference_sample", "tmcs_sample", "tmcs_sample_range", "tmcs_batch_sample",
+                  "tmcs_debug_gap_tables"):
+            getattr(L, f).restype = I
+        _lib = L
+    return _lib
+
+
+def tmcs_last_error() -> str:
+    return lib().tmcs_last_error().decode()
+
+
+def _check(rc: int) -> None:
+    if rc != TMCS_OK:
+        raise TmcsError(rc, tmcs_last_error())
+
+
+def marshal_ops(circuit: Circuit) -> Tuple[np.ndarray, np.ndarray]:
+    """Op list -> (tmcs_op structured array, flat uint32 targets it points into)."""
+    ops = circuit.ops
+    lens = np.fromiter((o.targets.size for o in ops), dtype=np.int64, count=len(ops))
+    flat = (np.concatenate([o.targets for o in ops]).astype(np.uint32)
+            if len(ops) and lens.sum() else np.zeros(1, np.uint32))
+    flat = np.ascontiguousarray(flat)
+    offs = np.zeros(len(ops), dtype=np.int64)
+    if len(ops):
+        np.cumsum(lens[:-1], out=offs[1:])
+    arr = np.zeros(len(ops), dtype=OP_DTYPE)
+    arr["code"] = [OPCODE_ID[o.name] for o in ops]
+    arr["n_targets"] = lens
+    arr["p"] = [o.p for o in ops]
+    arr["arg"] = [o.arg for o in ops]
+    arr["targets"] = flat.ctypes.data + 4 * offs
+    return arr, flat
+
+
+def tmcs_circuit_build(circuit: Circuit, flags: int = 0) -> int:
+    """Compile ``circuit``; returns the opaque handle (int)."""
+    arr, flat = marshal_ops(circuit)
+    out = ctypes.c_void_p()
+    _check(lib().tmcs_circuit_build(arr.ctypes.data if arr.size else None, arr.size, flags,
+                                    ctypes.byref(out)))
+    del flat
+    return int(out.value)
+
+
+def tmcs_circuit_free(handle: int) -> None:
+    _check(lib().tmcs_circuit_free(ctypes.c_void_p(handle)))
+
+
+def tmcs_circuit_info(handle: int) -> Dict[str, int]:
+    v = [ctypes.c_uint64() for _ in range(5)]
+    _check(lib().tmcs_circuit_info(ctypes.c_void_p(handle), *[ctypes.byref(x) for x in v]))
+    return dict(zip(("n_qubits", "n_meas", "n_det", "n_obs", "device_bytes"), (x.value for x in v)))
+
+
+def tmcs_circuit_stats(handle: int) -> Dict[str, int]:
+    s = _Stats()
+    _check(lib().tmcs_circuit_stats(ctypes.c_void_p(handle), ctypes.byref(s)))
+    return {f: getattr(s, f) for f in STATS_FIELDS}
+
+
+def tmcs_reference_sample(handle: int) -> np.ndarray:
+    """Noiseless reference record as a uint8 array of bits (one per record)."""
+    n = tmcs_circuit_info(handle)["n_meas"]
+    buf = np.zeros(max((n + 7) // 8, 1), dtype=np.uint8)
+    _check(lib().tmcs_reference_sample(ctypes.c_void_p(handle), buf.ctypes.data))
+    return np.unpackbits(buf, bitorder="little")[:n]
+
+
+def tmcs_debug_gap_tables(p: float) -> Tuple[np.ndarray, np.ndarray]:
+    ta = np.zeros(16, dtype=np.uint32)
+    tb = np.zeros(255, dtype=np.uint32)
+    _check(lib().tmcs_debug_gap_tables(float(p), ta.ctypes.data, tb.ctypes.data))
+    return ta, tb
+
+
+def _dev_ptr(buf) -> Optional[int]:
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    import torch
+    if not isinstance(buf, torch.Tensor):
+        raise TypeError("device buffers must be torch CUDA tensors or raw pointers")
+    if not buf.is_cuda:
+        raise ValueError("device buffer is not a CUDA tensor")
+    if not buf.is_contiguous() or buf.element_size() != 8:
+        raise ValueError("device buffer must be a contiguous 8-byte-element tensor")
+    return buf.data_ptr()
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _check_size(buf, rows: int, cols: int, what: str) -> None:
+    if buf is None or isinstance(buf, int):
+        return
+    if buf.numel() < rows * cols:
+        raise ValueError(f"{what} buffer has {buf.numel()} words, needs {rows * cols}")
+
+
+def tmcs_sample(handle: int, shots: int, seed: int, det, obs, stream=None) -> None:
+    info = tmcs_circuit_info(handle)
+    cols = (shots + 63) // 64
+    _check_size(det, info["n_det"], cols, "detector")
+    _check_size(obs, info["n_obs"], cols, "observable")
+    _check(lib().tmcs_sample(ctypes.c_void_p(handle), shots, seed & (2 ** 64 - 1), _dev_ptr(det),
+                             _dev_ptr(obs), _stream_ptr(stream)))
+
+
+def tmcs_sample_range(handle: int, first_chunk: int, shots: int, seed: int, det, obs, stream=None) -> None:
+    info = tmcs_circuit_info(handle)
+    cols = (shots + 63) // 64
+    _check_size(det, info["n_det"], cols, "detector")
+    _check_size(obs, info["n_obs"], cols, "observable")
+    _check(lib().tmcs_sample_range(ctypes.c_void_p(handle), first_chunk, shots, seed & (2 ** 64 - 1),
+                                   _dev_ptr(det), _dev_ptr(obs), _stream_ptr(stream)))
+
+
+def tmcs_batch_sample(jobs: Sequence[Tuple[int, int, int, object, object]], stream=None) -> None:
+    """jobs: (handle, shots, seed, det, obs) tuples."""
+    arr = (_Job * max(len(jobs), 1))()
+    for i, (h, shots, seed, det, obs) in enumerate(jobs):
+        info = tmcs_circuit_info(h)
+        cols = (shots + 63) // 64
+        _check_size(det, info["n_det"], cols, "detector")
+        _check_size(obs, info["n_obs"], cols, "observable")
+        arr[i] = _Job(h, shots, seed & (2 ** 64 - 1), _dev_ptr(det), _dev_ptr(obs))
+    _check(lib().tmcs_batch_sample(ctypes.byref(arr), len(jobs), _stream_ptr(stream)))
+
+
+class Sampler:
+    """Owns one compiled circuit; allocates output tensors on demand."""
+
+    def __init__(self, circuit: Circuit, flags: int = 0):
+        self.circuit = circuit
+        self.handle = tmcs_circuit_build(circuit, flags)
+        self.info = tmcs_circuit_info(self.handle)
+
+    def stats(self) -> Dict[str, int]:
+        return tmcs_circuit_stats(self.handle)
+
+    def alloc(self, shots: int, device="cuda"):
+        import torch
+        cols = (shots + 63) // 64
+        det = torch.empty((self.info["n_det"], cols), dtype=torch.int64, device=device)
+        obs = torch.empty((max(self.info["n_obs"], 1), cols), dtype=torch.int64, device=device)
+        return det, obs
+
+    def sample(self, shots: int, seed: int, first_chunk: int = 0, stream=None, out=None):
+        det, obs = out if out is not None else self.alloc(shots)
+        tmcs_sample_range(self.handle, first_chunk, shots, seed, det, obs if self.info["n_obs"] else None,
+                          stream)
+        return det, obs[: self.info["n_obs"]]
+
+    def reference_sample(self) -> np.ndarray:
+        return tmcs_reference_sample(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            tmcs_circuit_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,106 @@
+"""C ABI checks that need no GPU: the library loads and exports every
+function include/tmcs.h declares; host-side calls (compile, info, stats,
+reference sample, gap tables) behave; invalid inputs are rejected with the
+documented status codes."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import tableau
+from paper_2504_05611_gb300 import build as lib_build
+from paper_2504_05611_gb300 import circuits as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tmcs():
+    lib_build.build()
+    from paper_2504_05611_gb300 import tmcs as t
+    return t
+
+
+def declared_functions():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(tmcs_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(tmcs):
+    names = declared_functions()
+    assert "tmcs_sample" in names and "tmcs_batch_sample" in names
+    L = tmcs.lib()
+    for n in names:
+        assert hasattr(L, n), n
+
+
+@pytest.mark.parametrize("p", [1e-4, 1e-3, 1e-2, 0.25, 1.0])
+def test_gap_tables_equal_oracle(tmcs, p):
+    a_ta, a_tb = tmcs.tmcs_debug_gap_tables(p)
+    b_ta, b_tb = oracle.gap_tables(p)
+    assert np.array_equal(a_ta, b_ta) and np.array_equal(a_tb, b_tb)
+
+
+@pytest.mark.parametrize("name", ["sc3", "bb18"])
+@pytest.mark.parametrize("kind", ["nl", "teleport"])
+def test_reference_sample_equals_oracle_tableau(tmcs, name, kind):
+    code = C.code_by_name(name)
+    fn = C.nonlocal_cnot_circuit if kind == "nl" else C.teleport_circuit
+    c = fn(code, 2, 2)
+    h = tmcs.tmcs_circuit_build(c)
+    try:
+        assert np.array_equal(tmcs.tmcs_reference_sample(h), tableau.reference_sample(c)["rec"])
+    finally:
+        tmcs.tmcs_circuit_free(h)
+
+
+def test_info_and_pruning_stats(tmcs):
+    c = C.WORKLOADS["nl_sc3"].circuit()
+    h = tmcs.tmcs_circuit_build(c)
+    info = tmcs.tmcs_circuit_info(h)
+    assert (info["n_qubits"], info["n_meas"], info["n_det"], info["n_obs"]) == (52, 132, 56, 2)
+    st = tmcs.tmcs_circuit_stats(h)
+    # the non-local CNOT with Z detectors needs no z-plane: every z update pruned
+    assert st["pruned_updates"] > 0 and st["n_slots"] > 0
+    tmcs.tmcs_circuit_free(h)
+    h = tmcs.tmcs_circuit_build(c, tmcs.TMCS_FLAG_NO_PRUNE)
+    assert tmcs.tmcs_circuit_stats(h)["pruned_updates"] == 0
+    tmcs.tmcs_circuit_free(h)
+
+
+def test_rejects_nondeterministic_detector(tmcs):
+    c = C.Circuit()
+    c.append("RX", [0])
+    c.append("M", [0])
+    c.append("DETECTOR", [0])
+    with pytest.raises(tmcs.TmcsError) as e:
+        tmcs.tmcs_circuit_build(c)
+    assert e.value.code == 2
+    h = tmcs.tmcs_circuit_build(c, tmcs.TMCS_FLAG_NO_AUDIT)
+    tmcs.tmcs_circuit_free(h)
+
+
+def test_rejects_invalid_ops(tmcs):
+    arr = np.zeros(1, dtype=tmcs.OP_DTYPE)
+    arr["code"] = 99
+    import ctypes
+    out = ctypes.c_void_p()
+    assert tmcs.lib().tmcs_circuit_build(arr.ctypes.data, 1, 0, ctypes.byref(out)) == 1
+    assert "opcode" in tmcs.tmcs_last_error()
+    c = C.Circuit()
+    c.append("X_ERROR", [0, 0], p=0.1)   # noise ops must hit distinct qubits
+    with pytest.raises(tmcs.TmcsError):
+        tmcs.tmcs_circuit_build(c)
+    c = C.Circuit()
+    c.append("X_ERROR", [0], p=1e-13)
+    with pytest.raises(tmcs.TmcsError):
+        tmcs.tmcs_circuit_build(c)
+    with pytest.raises(tmcs.TmcsError):
+        tmcs.tmcs_circuit_build(C.Circuit(), flags=0x80)

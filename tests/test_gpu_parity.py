@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA sampler (through the C ABI) against the CPU oracle.
+
+Every comparison is bit-exact: both sides implement the same sampling
+specification, so detector and observable words must be identical,
+including zero pad bits. Sizes span several CTA tiles and a ragged last
+chunk; the full-size workloads are checked on sampled chunks the oracle
+recomputes one by one (``first_chunk`` keying).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_05611_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2504_05611_gb300 import tmcs  # noqa: E402
+
+
+def gpu_sample(circ, shots, seed, first_chunk=0, flags=0):
+    s = tmcs.Sampler(circ, flags)
+    det, obs = s.sample(shots, seed, first_chunk=first_chunk)
+    torch.cuda.synchronize()
+    out = det.cpu().numpy().view(np.uint64), obs.cpu().numpy().view(np.uint64)
+    s.close()
+    return out
+
+
+def assert_parity(circ, shots, seed, first_chunk=0, flags=0, threads=8):
+    gd, go = gpu_sample(circ, shots, seed, first_chunk, flags)
+    od, oo = oracle.sample(circ, shots, seed, first_chunk=first_chunk, threads=threads)
+    assert gd.shape == od.shape and go.shape == oo.shape
+    bad = np.argwhere(gd != od)
+    assert bad.size == 0, f"{len(bad)} detector words differ, first at {bad[:3].tolist()}"
+    assert np.array_equal(go, oo)
+    return gd, go
+
+
+def test_config_nl_sc3_full():
+    """Distance-3 SC non-local CNOT, 3/3 rounds, p=1e-3, p_ebit=1e-2, 1e4 shots, seed 1."""
+    w = C.WORKLOADS["nl_sc3"]
+    gd, _ = assert_parity(w.circuit(), w.shots, w.seed)
+    assert gd.any()
+
+
+@pytest.mark.parametrize("kind", ["nl", "teleport", "memory"])
+@pytest.mark.parametrize("code", ["sc3", "sc5", "bb18"])
+def test_protocols_high_noise(kind, code):
+    cc = C.code_by_name(code)
+    nz = C.NoiseModel(p=0.02, p_ebit=0.05)
+    if kind == "nl":
+        circ = C.nonlocal_cnot_circuit(cc, 2, 2, nz)
+    elif kind == "teleport":
+        circ = C.teleport_circuit(cc, 2, 2, nz)
+    else:
+        circ = C.memory_circuit(cc, 3, nz)
+    assert_parity(circ, 64 * 37 + 5, seed=7)
+
+
+def test_config_nl_sc11_reduced_shots():
+    w = C.WORKLOADS["nl_sc11"]
+    assert_parity(w.circuit(), 64 * 160 + 29, w.seed)
+
+
+def test_config_tp_bb144_reduced_shots():
+    w = C.WORKLOADS["tp_bb144"]
+    assert_parity(w.circuit(), 64 * 40 + 3, w.seed)
+
+
+def test_idle_and_feed_noise_variants():
+    nz = C.NoiseModel(p=0.01, p_ebit=0.03, idle=True, feed_noise=True)
+    assert_parity(C.teleport_circuit(C.code_by_name("bb18"), 2, 2, nz), 64 * 20 + 1, seed=3)
+
+
+@pytest.mark.parametrize("shots", [1, 63, 64, 65, 127, 1000])
+def test_ragged_shot_counts(shots):
+    assert_parity(C.nonlocal_cnot_circuit(C.code_by_name("sc3"), 1, 1, C.NoiseModel(0.05, 0.1)),
+                  shots, seed=99)
+
+
+def test_first_chunk_sharding_concatenates():
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc5"), 2, 2, C.NoiseModel(0.01, 0.05))
+    full_d, full_o = gpu_sample(circ, 64 * 50, 5)
+    a_d, a_o = gpu_sample(circ, 64 * 20, 5, first_chunk=0)
+    b_d, b_o = gpu_sample(circ, 64 * 30, 5, first_chunk=20)
+    assert np.array_equal(np.concatenate([a_d, b_d], 1), full_d)
+    assert np.array_equal(np.concatenate([a_o, b_o], 1), full_o)
+    assert_parity(circ, 64 * 3 + 7, seed=5, first_chunk=123456)
+
+
+def test_pruning_is_exact():
+    """Liveness pruning only removes work: the unpruned program gives the same bits."""
+    circ = C.teleport_circuit(C.code_by_name("sc3"), 2, 2, C.NoiseModel(0.02, 0.05))
+    a = gpu_sample(circ, 64 * 30, 11)
+    b = gpu_sample(circ, 64 * 30, 11, flags=tmcs.TMCS_FLAG_NO_PRUNE)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_noiseless_is_zero_and_certain_noise():
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc3"), 2, 2, C.NoiseModel(0.0, 0.0))
+    d, o = gpu_sample(circ, 640, 1)
+    assert not d.any() and not o.any()
+    c = C.Circuit()
+    c.append("R", [0, 1])
+    c.append("X_ERROR", [1], p=1.0)
+    c.append("M", [0, 1])
+    c.append("DETECTOR", [0])
+    c.append("DETECTOR", [1])
+    c.append("OBSERVABLE", [1], arg=0)
+    c.append("OBSERVABLE", [0, 1], arg=0)   # accumulates: obs = r1 ^ r0 ^ r1 = r0
+    d, o = assert_parity(c, 100, 1)
+    assert not d[0].any() and (d[1][0] == np.uint64(2 ** 64 - 1)) and not o.any()
+
+
+def random_noisy_circuit(rng, n, depth):
+    """Random Clifford body + inverse on |0>/|+> inputs with noise sprinkled
+    in, a mid-circuit measurement feeding conditioned Paulis, and one detector
+    per (deterministic) final measurement."""
+    c = C.Circuit()
+    xb = [q for q in range(n) if rng.random() < 0.4]
+    zb = [q for q in range(n) if q not in xb]
+    if zb:
+        c.append("R", zb)
+    if xb:
+        c.append("RX", xb)
+    body = []
+    for _ in range(depth):
+        u = rng.integers(3)
+        if u == 0:
+            body.append(("H", [int(rng.integers(n))]))
+        elif u == 1:
+            body.append(("S", [int(rng.integers(n))]))
+        else:
+            a, b = rng.choice(n, 2, replace=False)
+            body.append(("CX", [int(a), int(b)]))
+    inv = []
+    for name, t in reversed(body):
+        inv += [("S", t)] * 3 if name == "S" else [(name, t)]
+    for i, (name, t) in enumerate(body + inv):
+        c.append(name, t)
+        if rng.random() < 0.3:
+            kind = ["X_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2"][int(rng.integers(4))]
+            if kind == "DEPOLARIZE2":
+                a, b = rng.choice(n, 2, replace=False)
+                c.append(kind, [int(a), int(b)], p=float(rng.uniform(0.01, 0.3)))
+            else:
+                qs = sorted(set(int(v) for v in rng.integers(0, n, 2)))
+                c.append(kind, qs, p=float(rng.uniform(0.01, 0.3)))
+    if zb:
+        anc = n
+        c.append("R", [anc])
+        c.append("CX", [zb[0], anc])
+        r = c.append("M", [anc])
+        c.append("XFEED", [int(r[0]), int(rng.integers(n))])
+        c.append("ZFEED", [int(r[0]), int(rng.integers(n))])
+    if zb:
+        c.append("M", zb)
+    if xb:
+        c.append("MX", xb)
+    for r in range(c.n_meas):
+        c.append("DETECTOR", [r])
+    c.append("OBSERVABLE", [c.n_meas - 1], arg=0)
+    return c
+
+
+@pytest.mark.parametrize("trial", range(12))
+def test_random_circuits(trial):
+    rng = np.random.default_rng(900 + trial)
+    circ = random_noisy_circuit(rng, int(rng.integers(2, 9)), int(rng.integers(4, 40)))
+    assert_parity(circ, 64 * 9 + int(rng.integers(1, 64)), seed=int(rng.integers(1, 2 ** 62)))
+
+
+def test_batch_equals_solo():
+    circs = [C.nonlocal_cnot_circuit(C.code_by_name("sc3"), 2, 2, C.NoiseModel(0.01, 0.1)),
+             C.teleport_circuit(C.code_by_name("bb18"), 1, 1, C.NoiseModel(0.003, 0.03)),
+             C.memory_circuit(C.code_by_name("sc5"), 3, C.NoiseModel(0.02, 0.02))]
+    samplers = [tmcs.Sampler(c) for c in circs]
+    shots = [64 * 7 + 3, 1000, 64 * 33]
+    outs = [s.alloc(n) for s, n in zip(samplers, shots)]
+    jobs = [(s.handle, n, 40 + i, d, o) for i, (s, n, (d, o)) in enumerate(zip(samplers, shots, outs))]
+    tmcs.tmcs_batch_sample(jobs)
+    torch.cuda.synchronize()
+    for i, (circ, n) in enumerate(zip(circs, shots)):
+        d, o = outs[i]
+        sd, so = gpu_sample(circ, n, 40 + i)
+        assert np.array_equal(d.cpu().numpy().view(np.uint64), sd)
+        assert np.array_equal(o[: circ.n_obs].cpu().numpy().view(np.uint64), so)
+    for s in samplers:
+        s.close()
+
+
+def test_headline_full_size_sampled_chunks():
+    """Distance-29 SC non-local CNOT, 29/29 rounds, 1e7 shots: sampled chunks
+    (first, middle, last with its ragged tail) against the oracle."""
+    w = C.WORKLOADS["nl_sc29"]
+    circ = w.circuit()
+    shots = w.shots
+    s = tmcs.Sampler(circ)
+    det, obs = s.sample(shots, w.seed)
+    torch.cuda.synchronize()
+    cols = (shots + 63) // 64
+    for col in (0, cols // 2, cols - 1):
+        n = min(64, shots - 64 * col)
+        od, oo = oracle.sample(circ, n, w.seed, first_chunk=col, threads=8)
+        assert np.array_equal(det[:, col].cpu().numpy().view(np.uint64), od[:, 0])
+        assert np.array_equal(obs[:, col].cpu().numpy().view(np.uint64), oo[:, 0])
+    # every detector word has zero pad bits (shots is a multiple of 64 here)
+    assert shots % 64 == 0
+    s.close()
