@@ -171,13 +171,13 @@ int tmcs_batch_sample(const tmcs_job *jobs, size_t n_jobs, void *stream);
 const char *tmcs_last_error(void);
 
 /*
- * Gap tables of the sampling specification for probability p in (0, 1]:
- * ta[0..15] = TA[1..16] = floor(2^32 exp(256 a ln(1-p))),
- * tb[0..254] = TB[1..255] = floor(2^32 exp(b ln(1-p)) expm1((256-b) ln(1-p))
- *                                  / expm1(256 ln(1-p))).
- * Exported so tests can compare them with an independent computation.
+ * Gap table of the sampling specification for probability p in (0, 1]:
+ * table[g-1] = T[g] = floor(2^32 (1-p)^g), g = 1..4096, with (1-p)^g computed
+ * as exp(g * log1p(-p)) in double precision. The gap between noise events is
+ * G = #{g : w < T[g]} for a uniform 32-bit word w. Exported so tests can
+ * compare it with an independent computation.
  */
-int tmcs_debug_gap_tables(double p, uint32_t *ta, uint32_t *tb);
+int tmcs_debug_gap_table(double p, uint32_t *table);
 
 #ifdef __cplusplus
 }

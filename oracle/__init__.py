@@ -9,7 +9,7 @@ generator with no sampling arithmetic).
 Contents:
   * ``frame_oracle.c`` (via this module): one-shot-at-a-time Pauli-frame
     sampler implementing the sampling specification (Philox4x32-10 noise
-    streams, geometric gaps from the TA/TB tables), the gap tables, Philox
+    streams, geometric gaps from the gap table T), the gap table, Philox
     itself, and a 64-lane noiseless propagator for fault injection and
     gauge-randomised determinism audits.
   * ``statevector``: brute-force state-vector simulator for tiny circuits.
@@ -51,8 +51,8 @@ def lib() -> ctypes.CDLL:
         U64 = ctypes.c_uint64
         L.oracle_philox4x32_10.argtypes = [P, P, P]
         L.oracle_philox4x32_10.restype = None
-        L.oracle_gap_tables.argtypes = [ctypes.c_double, P, P]
-        L.oracle_gap_tables.restype = None
+        L.oracle_gap_table.argtypes = [ctypes.c_double, P]
+        L.oracle_gap_table.restype = None
         L.oracle_sample.argtypes = [I64, P, P, P, P, P, I64, I64, I64, I64, U64, U64, U64, P, P, ctypes.c_int]
         L.oracle_sample.restype = ctypes.c_int
         L.oracle_propagate64.argtypes = [I64, P, P, P, P, P, I64, I64, I64, I64, I64, P, P, P, P, U64, P, P]
@@ -99,12 +99,11 @@ def philox4x32_10(ctr: Sequence[int], key: Sequence[int]) -> Tuple[int, int, int
     return tuple(int(v) for v in out)
 
 
-def gap_tables(p: float) -> Tuple[np.ndarray, np.ndarray]:
-    """(TA[1..16], TB[1..255]) for noise probability p in (0, 1]."""
-    ta = np.zeros(16, dtype=np.uint32)
-    tb = np.zeros(255, dtype=np.uint32)
-    lib().oracle_gap_tables(float(p), _ptr(ta), _ptr(tb))
-    return ta, tb
+def gap_table(p: float) -> np.ndarray:
+    """T[1..4096] = floor(2^32 (1-p)^g) for noise probability p in (0, 1]."""
+    t = np.zeros(4096, dtype=np.uint32)
+    lib().oracle_gap_table(float(p), _ptr(t))
+    return t
 
 
 def sample(circuit, shots: int, seed: int, first_chunk: int = 0, threads: int = 1,

@@ -17,18 +17,19 @@
  * The random process (this project's sampling specification; the paper
  * samples with a third-party simulator and fixes no generator):
  *   Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = (seed low 32,
- *   seed high 32), counter = (j, chunk, op index, segment) for draw j of the
- *   noise stream of one segment of one noise op in one 64-shot chunk.
+ *   seed high 32), counter = (j, chunk, op index, segment) for call j of the
+ *   noise stream of one segment of one noise op in one 64-shot chunk. Call j
+ *   yields words (w0, w1, w2, w3) = draws 2j (gap w0, Pauli w1) and 2j+1
+ *   (gap w2, Pauli w3).
  *   A noise op with T units (targets; pairs for DEPOLARIZE2) has segments of
  *   64 units; segment s spans trials t = 64*u_local + lane, u_local < U_s.
- *   Walk: pos = -1; per draw, pos += 1 + 256*A + B, stop when pos >= 64*U_s,
- *   else an event hits unit 64*s + pos/64 in lane pos%64 with Pauli index
- *   k = 1 + ((w2 * K) >> 32), K = 1, 3, 15 for *_ERROR, DEPOLARIZE1, 2.
- *   A = #{a in 1..16 : w0 < TA[a]}, B = #{b in 1..255 : w1 < TB[b]} with
- *   TA[a] = floor(2^32 exp(256 a ln(1-p))),
- *   TB[b] = floor(2^32 exp(b ln(1-p)) expm1((256-b) ln(1-p)) / expm1(256 ln(1-p))),
- *   so 256*A + B is geometric with success probability p on every position
- *   a segment can reach (A is capped at 16 = 4096/256 trials).
+ *   Walk: pos = -1; per draw, pos += 1 + G, stop when pos >= 64*U_s, else an
+ *   event hits unit 64*s + pos/64 in lane pos%64 with Pauli index
+ *   k = 1 + ((w_pauli * K) >> 32), K = 1, 3, 15 for *_ERROR, DEPOLARIZE1, 2.
+ *   G = #{g in 1..4096 : w_gap < T[g]} with T[g] = floor(2^32 (1-p)^g),
+ *   (1-p)^g evaluated as exp(g * log1p(-p)); so G is geometric with success
+ *   probability p on every position a segment can reach (G is capped at
+ *   4096, the trial count of a full segment).
  *   Pauli index bits: x = bit 0, z = bit 1 (X=1, Z=2, Y=3); DEPOLARIZE2 puts
  *   k>>2 on the first target and k&3 on the second.
  *
@@ -49,8 +50,7 @@ enum {
 };
 
 #define SEG_UNITS 64
-#define TA_LEN 16
-#define TB_LEN 255
+#define GAP_LEN 4096
 
 /* ---------------------------------------------------------------- Philox */
 
@@ -91,17 +91,12 @@ static uint32_t to_u32_fraction(double x)
     return (uint32_t)v;
 }
 
-/* TA[0..15] hold TA[1..16]; TB[0..254] hold TB[1..255]. p must be in (0, 1]. */
-void oracle_gap_tables(double p, uint32_t *ta, uint32_t *tb)
+/* t[0..4095] hold T[1..4096] = floor(2^32 (1-p)^g). p must be in (0, 1]. */
+void oracle_gap_table(double p, uint32_t *t)
 {
     double lq = log1p(-p);
-    double den = expm1(256.0 * lq);
-    for (int a = 1; a <= TA_LEN; a++)
-        ta[a - 1] = to_u32_fraction(exp(256.0 * (double)a * lq));
-    for (int b = 1; b <= TB_LEN; b++) {
-        double num = exp((double)b * lq) * expm1((double)(256 - b) * lq);
-        tb[b - 1] = (p >= 1.0) ? 0u : to_u32_fraction(num / den);
-    }
+    for (int g = 1; g <= GAP_LEN; g++)
+        t[g - 1] = to_u32_fraction(exp((double)g * lq));
 }
 
 /* ---------------------------------------------------------- op access */
@@ -117,8 +112,7 @@ typedef struct {
 } oracle_circuit;
 
 typedef struct {
-    uint32_t ta[TA_LEN];
-    uint32_t tb[TB_LEN];
+    uint32_t t[GAP_LEN];
 } gap_table;
 
 static int is_noise(int code)
@@ -126,18 +120,24 @@ static int is_noise(int code)
     return code == OR_X_ERROR || code == OR_Z_ERROR || code == OR_DEP1 || code == OR_DEP2;
 }
 
+/* #{i : w < t[i]} for a non-increasing table (checked when it is built):
+ * the entries with w < t[i] form a prefix, found by bisection. */
 static uint32_t count_below(uint32_t w, const uint32_t *t, int len)
 {
-    uint32_t c = 0;
-    for (int i = 0; i < len; i++) c += (w < t[i]) ? 1u : 0u;
-    return c;
+    int lo = 0, hi = len; /* answer in [lo, hi] */
+    while (lo < hi) {
+        int mid = lo + (hi - lo) / 2;
+        if (w < t[mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    return (uint32_t)lo;
 }
 
 /* ------------------------------------------------- one-shot sampler */
 
 typedef struct {
     const oracle_circuit *c;
-    const gap_table *tables; /* per op (only noise ops filled) */
+    const gap_table *const *tables; /* per op: table of its p (noise ops only) */
     uint64_t seed, first_chunk, shots;
     uint64_t col_begin, col_end; /* output columns (chunks) this worker owns */
     uint64_t n_cols;
@@ -169,17 +169,18 @@ static void noise_op_one_lane(const oracle_circuit *c, const gap_table *tab, int
         if (u_seg > SEG_UNITS) u_seg = SEG_UNITS;
         int64_t n_trials = 64 * u_seg;
         int64_t pos = -1;
-        for (uint32_t j = 0;; j++) {
-            uint32_t ctr[4] = {j, chunk, (uint32_t)i, (uint32_t)s};
+        for (uint32_t d = 0;; d++) {
+            uint32_t ctr[4] = {d / 2, chunk, (uint32_t)i, (uint32_t)s};
             uint32_t w[4];
             oracle_philox4x32_10(ctr, key, w);
-            int64_t A = count_below(w[0], tab->ta, TA_LEN);
-            int64_t B = count_below(w[1], tab->tb, TB_LEN);
-            pos += 1 + 256 * A + B;
+            uint32_t w_gap = (d & 1) ? w[2] : w[0];
+            uint32_t w_pauli = (d & 1) ? w[3] : w[1];
+            int64_t G = count_below(w_gap, tab->t, GAP_LEN);
+            pos += 1 + G;
             if (pos >= n_trials) break;
             if ((uint32_t)(pos & 63) != lane) continue;
             int64_t u = s * SEG_UNITS + (pos >> 6);
-            uint32_t k = 1u + (uint32_t)(((uint64_t)w[2] * (uint64_t)K) >> 32);
+            uint32_t k = 1u + (uint32_t)(((uint64_t)w_pauli * (uint64_t)K) >> 32);
             switch (code) {
             case OR_X_ERROR: apply_pauli(x, z, t[u], 1u); break;
             case OR_Z_ERROR: apply_pauli(x, z, t[u], 2u); break;
@@ -248,7 +249,7 @@ static void *shot_worker(void *arg)
                 case OR_DEP1:
                 case OR_DEP2:
                     if (c->ps[i] > 0.0)
-                        noise_op_one_lane(c, &job->tables[i], i, job->seed, chunk, lane, x, z);
+                        noise_op_one_lane(c, job->tables[i], i, job->seed, chunk, lane, x, z);
                     break;
                 case OR_XFEED:
                     for (int64_t a = 0; a + 1 < nt; a += 2) x[t[a + 1]] ^= rec[t[a]];
@@ -325,15 +326,30 @@ int oracle_sample(int64_t n_ops, const int32_t *codes, const double *ps, const u
     if (validate(&c) != 0) return -1;
     uint64_t n_cols = (shots + 63) / 64;
     if (first_chunk + n_cols > 0x100000000ull) return -1;
-    gap_table *tables = calloc((size_t)n_ops + 1, sizeof(gap_table));
-    if (!tables) return -2;
-    for (int64_t i = 0; i < n_ops; i++)
-        if (is_noise(codes[i]) && ps[i] > 0.0) oracle_gap_tables(ps[i], tables[i].ta, tables[i].tb);
+    /* one table per distinct probability */
+    const gap_table **tables = calloc((size_t)n_ops + 1, sizeof(gap_table *));
+    gap_table *distinct = calloc((size_t)n_ops + 1, sizeof(gap_table));
+    double *distinct_p = calloc((size_t)n_ops + 1, sizeof(double));
+    int64_t n_distinct = 0;
+    if (!tables || !distinct || !distinct_p) { free(tables); free(distinct); free(distinct_p); return -2; }
+    for (int64_t i = 0; i < n_ops; i++) {
+        if (!is_noise(codes[i]) || !(ps[i] > 0.0)) continue;
+        int64_t k = 0;
+        while (k < n_distinct && distinct_p[k] != ps[i]) k++;
+        if (k == n_distinct) {
+            distinct_p[k] = ps[i];
+            oracle_gap_table(ps[i], distinct[k].t);
+            for (int g = 1; g < GAP_LEN; g++)
+                if (distinct[k].t[g] > distinct[k].t[g - 1]) { free(tables); free(distinct); free(distinct_p); return -1; }
+            n_distinct++;
+        }
+        tables[i] = &distinct[k];
+    }
     if (threads < 1) threads = 1;
     if ((uint64_t)threads > n_cols) threads = (int)(n_cols ? n_cols : 1);
     shot_job *jobs = calloc((size_t)threads, sizeof(shot_job));
     pthread_t *tid = calloc((size_t)threads, sizeof(pthread_t));
-    if (!jobs || !tid) { free(tables); free(jobs); free(tid); return -2; }
+    if (!jobs || !tid) { free(tables); free(distinct); free(distinct_p); free(jobs); free(tid); return -2; }
     for (int w = 0; w < threads; w++) {
         jobs[w] = (shot_job){&c, tables, seed, first_chunk, shots,
                              n_cols * (uint64_t)w / (uint64_t)threads,
@@ -349,7 +365,7 @@ int oracle_sample(int64_t n_ops, const int32_t *codes, const double *ps, const u
     }
     for (int w = 0; w < threads; w++)
         if (jobs[w].status) rc = jobs[w].status;
-    free(tables); free(jobs); free(tid);
+    free(tables); free(distinct); free(distinct_p); free(jobs); free(tid);
     return rc;
 }
 

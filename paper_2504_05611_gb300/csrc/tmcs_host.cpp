@@ -32,12 +32,12 @@ static bool is_pair(uint32_t code) {
     return code == TMCS_CX || code == TMCS_DEPOLARIZE2 || code == TMCS_XFEED || code == TMCS_ZFEED;
 }
 
-// ------------------------------------------------------------ gap tables
+// ------------------------------------------------------------ gap table
 //
-// Sampling specification: for noise probability p, gaps between events are
-// G = 256 A + B with A = #{a in 1..16 : w0 < TA[a]}, B = #{b in 1..255 :
-// w1 < TB[b]}; the tables below make G geometric with success probability p
-// on every position a 4096-trial segment can reach.
+// Sampling specification: the gap between consecutive noise events of a
+// segment is G = #{g in 1..4096 : w < T[g]} for a uniform 32-bit word w, with
+// T[g] = floor(2^32 (1-p)^g); P(G >= g) = T[g] / 2^32, so G is geometric with
+// success probability p on every position a 4096-trial segment can reach.
 
 static uint32_t frac_to_u32(double x) {
     double v = std::floor(std::ldexp(x, 32));
@@ -46,25 +46,14 @@ static uint32_t frac_to_u32(double x) {
     return static_cast<uint32_t>(v);
 }
 
-int gap_tables(double p, uint32_t *ta, uint32_t *tb) {
-    if (!(p > 0.0 && p <= 1.0)) return fail(TMCS_E_INVALID, "gap tables need p in (0, 1]");
+int gap_table(double p, uint32_t *t) {
+    if (!(p > 0.0 && p <= 1.0)) return fail(TMCS_E_INVALID, "gap table needs p in (0, 1]");
     const double lq = std::log1p(-p);
-    const double den = std::expm1(256.0 * lq);
-    for (uint32_t a = 1; a <= kTA; a++) ta[a - 1] = frac_to_u32(std::exp(256.0 * double(a) * lq));
-    for (uint32_t b = 1; b <= kTB; b++) {
-        if (p >= 1.0) {
-            tb[b - 1] = 0u;
-            continue;
-        }
-        const double num = std::exp(double(b) * lq) * std::expm1(double(256 - b) * lq);
-        tb[b - 1] = frac_to_u32(num / den);
-    }
-    // The kernel finds A and B by binary search, which equals the count only
-    // for non-increasing tables.
-    for (uint32_t a = 1; a < kTA; a++)
-        if (ta[a] > ta[a - 1]) return fail(TMCS_E_INVALID, "gap table TA not monotone (p too small)");
-    for (uint32_t b = 1; b < kTB; b++)
-        if (tb[b] > tb[b - 1]) return fail(TMCS_E_INVALID, "gap table TB not monotone (p too small)");
+    for (uint32_t g = 1; g <= kGapLen; g++) t[g - 1] = frac_to_u32(std::exp(double(g) * lq));
+    // The kernel locates the count by search, which equals it only for a
+    // non-increasing table.
+    for (uint32_t g = 1; g < kGapLen; g++)
+        if (t[g] > t[g - 1]) return fail(TMCS_E_INVALID, "gap table not monotone (p too small)");
     return TMCS_OK;
 }
 
@@ -402,8 +391,11 @@ int compile(tmcs_circuit *c, uint32_t flags) {
         uint32_t id = uint32_t(P.table_p.size());
         P.table_p.push_back(p);
         P.tables.resize(P.tables.size() + kTableWords, 0u);
-        int rc = gap_tables(p, &P.tables[size_t(id) * kTableWords], &P.tables[size_t(id) * kTableWords + kTBOff]);
+        uint32_t *tab = &P.tables[size_t(id) * kTableWords];
+        int rc = gap_table(p, tab);
         if (rc) return rc;
+        const float inv = p >= 1.0 ? 0.0f : float(1.0 / std::log2(1.0 - p));
+        std::memcpy(tab + kGapLen, &inv, 4);
         table_id[key] = id;
         *out = id;
         return TMCS_OK;
@@ -683,9 +675,9 @@ extern "C" {
 
 const char *tmcs_last_error(void) { return g_last_error.c_str(); }
 
-int tmcs_debug_gap_tables(double p, uint32_t *ta, uint32_t *tb) {
-    if (!ta || !tb) return fail(TMCS_E_INVALID, "null table pointer");
-    return gap_tables(p, ta, tb);
+int tmcs_debug_gap_table(double p, uint32_t *table) {
+    if (!table) return fail(TMCS_E_INVALID, "null table pointer");
+    return gap_table(p, table);
 }
 
 int tmcs_circuit_build(const tmcs_op *ops, size_t n_ops, uint32_t flags, tmcs_circuit **out) {

@@ -24,22 +24,37 @@ namespace tmcs {
 // at a time with a barrier in between.
 
 enum LayerKind : uint32_t {
-    L_ZERO = 0,   // args[off+i] = slot                       -> slot = 0
-    L_XOR = 1,    // args[off+i] = dst | src << 16            -> dst ^= src
-    L_COPY = 2,   // args[off+i] = dst | src << 16            -> dst = src
-    L_NOISE = 3,  // aux = noise descriptor index, count = segments
-    L_DET = 4,    // args[off+i], i <= count: CSR bounds into args (slot lists);
-                  // aux = first detector id
-    L_OBS = 5,    // CSR as L_DET; list[0] = accumulator slot, rest = record slots
-    L_OBSOUT = 6, // args[off+i] = accumulator slot of observable i (count = n_obs)
+    L_ZERO = 0,    // block[i] = slot                          -> slot = 0
+    L_XOR = 1,     // block[i] = dst | src << 16               -> dst ^= src
+    L_COPY = 2,    // block[i] = dst | src << 16               -> dst = src
+    L_NGEN = 3,    // walk the event streams of noise descriptors aux .. aux+count-1
+                   // (a window of aux2 segments in total) into the event buffer
+    L_NAPPLY = 4,  // apply the buffered events of noise descriptor aux, whose
+                   // segments start at window segment aux2
+    L_DET = 5,     // block[0..count] = list bounds relative to the block; lists
+                   // of record slots; detector ids aux .. aux+count-1
+    L_OBS = 6,     // as L_DET; list[0] = accumulator slot, rest = record slots
+    L_OBSOUT = 7,  // block[i] = accumulator slot of observable i (count = n_obs)
 };
 
+// A layer's arguments are one contiguous block args[off, off + nwords) that
+// the kernel stages into shared memory with a bulk asynchronous copy while
+// the previous layer runs: off and nwords are multiples of 4 words (16 bytes)
+// and nwords <= kStageWords. nwords = 0: nothing staged.
 struct Layer {
     uint32_t kind;
     uint32_t count;
     uint32_t off;
+    uint32_t nwords;
     uint32_t aux;
+    uint32_t aux2;
+    uint32_t pad0, pad1;
 };
+
+constexpr uint32_t kStageWords = 2048;  // 8 KB per staging buffer (two buffers)
+constexpr uint32_t kEvCap = 8;          // events buffered per (segment, chunk)
+constexpr uint32_t kWindowSegs = 192;   // noise segments per generation window
+constexpr uint32_t kWindowOps = 16;     // noise ops per generation window
 
 enum NoiseKind : uint32_t { N_XERR = 0, N_ZERR = 1, N_DEP1 = 2, N_DEP2 = 3 };
 
@@ -57,13 +72,11 @@ struct NoiseDesc {
 };
 
 constexpr uint32_t kSegUnits = 64;     // units per noise segment
-constexpr uint32_t kTA = 16;           // TA[1..16]
-constexpr uint32_t kTB = 255;          // TB[1..255]
-// Per probability: words [0,16) = TA[1..16], [16,32) = 0, [32,287) =
-// TB[1..255], [287] = 0. The zero padding lets the kernel find A and B by
-// branch-free binary search with power-of-two steps.
-constexpr uint32_t kTBOff = 32;
-constexpr uint32_t kTableWords = 288;
+constexpr uint32_t kGapLen = 4096;     // T[1..4096]: a full segment has 4096 trials
+// Per probability: words [0, 4096) = T[1..4096] = floor(2^32 (1-p)^g);
+// word 4096 = float bits of 1/log2(1-p) (0 for p = 1), used only to guess the
+// count before the exact table check; words 4097..4099 = 0.
+constexpr uint32_t kTableWords = 4100;
 constexpr uint32_t kDeadSlot = 0xFFFFu;
 constexpr uint32_t kMaxSlots = 0xFFFEu;
 
@@ -71,9 +84,10 @@ struct Program {
     std::vector<Layer> layers;
     std::vector<uint32_t> args;
     std::vector<NoiseDesc> noise;
-    std::vector<uint32_t> tables;   // kTableWords per distinct p
+    std::vector<uint32_t> tables;   // kTableWords per distinct p (gap table + estimate constant)
     std::vector<double> table_p;
     uint32_t n_slots = 0;
+    uint32_t max_window_segs = 0;  // event-buffer size in segments
     uint64_t n_det = 0, n_obs = 0;
 };
 
@@ -87,6 +101,10 @@ struct DeviceProgram {
     const NoiseDesc *noise = nullptr;
     const uint32_t *tables = nullptr;
 };
+
+// Per-device scratch of the library: a status word that kernels set when a
+// bounded wait expires (read and cleared by tmcs_check_device).
+uint32_t *device_status_word(int device);
 
 // Host-side copy of one user op.
 struct HostOp {
@@ -114,7 +132,7 @@ namespace tmcs {
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 int compile(tmcs_circuit *c, uint32_t flags);
-int gap_tables(double p, uint32_t *ta, uint32_t *tb);
+int gap_table(double p, uint32_t *t);
 int audit(const tmcs_circuit *c);
 size_t program_bytes(const Program &p);
 

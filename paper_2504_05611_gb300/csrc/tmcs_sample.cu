@@ -7,9 +7,9 @@
 // layer at a time (barrier in between):
 //   - clear / XOR / copy layers: one thread per (update, chunk word);
 //   - noise layers: one thread per (64-unit segment, chunk); the thread walks
-//     that segment's Philox4x32-10 event stream (geometric gaps from the gap
-//     tables held in shared memory) and XORs each event's Pauli into the
-//     frame words of its target (Methods "Simulation" noise channels);
+//     that segment's Philox4x32-10 event stream (geometric gaps located in
+//     the L1-resident gap table) and XORs each event's Pauli into the frame
+//     words of its target (Methods "Simulation" noise channels);
 //   - detector layers: one thread per (detector, chunk) XORs its record slots
 //     and writes the 64-shot word straight to HBM, detector-major, so
 //     consecutive threads store consecutive words of one detector row;
@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -49,14 +50,18 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
     return make_uint4(c0, c1, c2, c3);
 }
 
-// #{i : w < t[i]} for a non-increasing table padded with zeros to 2^LOG2 words.
-template <int LOG2>
-__device__ __forceinline__ int count_above(const uint32_t *t, uint32_t w) {
-    int b = 0;
-#pragma unroll
-    for (int step = 1 << (LOG2 - 1); step >= 1; step >>= 1)
-        if (w < t[b + step - 1]) b += step;
-    return b;
+// Gap of the sampling specification: G = #{g in 1..4096 : w < T[g]} for the
+// non-increasing table T (T + i holds T[i+1]). A float estimate of
+// log((w+1) 2^-32) / log(1-p) lands within one step of the count; the two
+// loops then move it to the exact count by comparing against the table, so
+// the result never depends on the estimate's rounding.
+__device__ __forceinline__ int gap_count(const uint32_t *__restrict__ T, float inv_log2, uint32_t w) {
+    const float lg = __log2f(__uint2float_rn(w) + 1.0f) - 32.0f;
+    const float est = lg * inv_log2;
+    int g = est >= float(kGapLen) ? int(kGapLen) : (est > 0.0f ? int(est) : 0);
+    while (g < int(kGapLen) && w < __ldg(T + g)) g++;
+    while (g > 0 && w >= __ldg(T + g - 1)) g--;
+    return g;
 }
 
 struct KernelArgs {
@@ -66,7 +71,6 @@ struct KernelArgs {
     const uint32_t *tables;
     uint32_t n_layers;
     uint32_t n_slots;
-    uint32_t n_tables;
     uint32_t key0, key1;
     uint32_t first_chunk;  // global chunk of output column 0
     uint64_t n_cols;       // output columns (chunks) of this call
@@ -75,62 +79,67 @@ struct KernelArgs {
     uint64_t *obs;
 };
 
+__device__ __forceinline__ void xor_bit(uint64_t *F, uint32_t slot, uint32_t K, int k, unsigned long long bit) {
+    if (slot != kDeadSlot) atomicXor(reinterpret_cast<unsigned long long *>(&F[slot * K + k]), bit);
+}
+
+// One event of a noise op: Pauli index from the word, applied to the live
+// frame components of the unit's target(s).
 template <int K>
-__device__ __forceinline__ void noise_layer(uint64_t *F, const uint32_t *T, const NoiseDesc nd,
+__device__ __forceinline__ void apply_event(uint64_t *F, const uint32_t *__restrict__ tg, const NoiseDesc &nd,
+                                            uint32_t npauli, uint32_t s, int pos, uint32_t w_pauli, int k) {
+    const uint32_t unit = s * kSegUnits + uint32_t(pos >> 6);
+    const unsigned long long bit = 1ull << (pos & 63);
+    const uint32_t pk = 1u + __umulhi(w_pauli, npauli);
+    if (nd.kind == N_DEP2) {
+        const uint32_t c0 = __ldg(tg + 2 * unit), c1 = __ldg(tg + 2 * unit + 1);
+        const uint32_t pa = pk >> 2, pb = pk & 3u;
+        if (pa & 1u) xor_bit(F, c0 & 0xFFFFu, K, k, bit);
+        if (pa & 2u) xor_bit(F, c0 >> 16, K, k, bit);
+        if (pb & 1u) xor_bit(F, c1 & 0xFFFFu, K, k, bit);
+        if (pb & 2u) xor_bit(F, c1 >> 16, K, k, bit);
+    } else {
+        const uint32_t c0 = __ldg(tg + unit);
+        const uint32_t pa = nd.kind == N_XERR ? 1u : nd.kind == N_ZERR ? 2u : pk;
+        if (pa & 1u) xor_bit(F, c0 & 0xFFFFu, K, k, bit);
+        if (pa & 2u) xor_bit(F, c0 >> 16, K, k, bit);
+    }
+}
+
+// Noise layer: one thread per (64-unit segment, chunk) walks the segment's
+// event stream; each Philox4x32-10 call yields two draws (gap word, Pauli
+// word).
+template <int K>
+__device__ __forceinline__ void noise_layer(uint64_t *F, const uint32_t *__restrict__ tables, const NoiseDesc nd,
                                             const uint32_t *__restrict__ args, uint32_t key0,
                                             uint32_t key1, uint32_t chunk0, int nvalid) {
-    const uint32_t *TA = T + nd.table * kTableWords;
-    const uint32_t *TB = TA + kTBOff;
+    const uint32_t *T = tables + size_t(nd.table) * kTableWords;
+    const float inv = __uint_as_float(__ldg(T + kGapLen));
     const uint32_t npauli = nd.kind == N_DEP2 ? 15u : nd.kind == N_DEP1 ? 3u : 1u;
+    const uint32_t *tg = args + nd.tgt_off;
     const uint32_t work = nd.n_seg * K;
     for (uint32_t u = threadIdx.x; u < work; u += blockDim.x) {
         const uint32_t s = u / K;
         const int k = int(u % K);
         if (k >= nvalid) continue;
         const uint32_t chunk = chunk0 + uint32_t(k);
-        const int seg_units = int(min(kSegUnits, nd.n_units - s * kSegUnits));
-        const int n_trials = 64 * seg_units;
-        const uint32_t *tg = args + nd.tgt_off;
+        const int n_trials = 64 * int(min(kSegUnits, nd.n_units - s * kSegUnits));
         int pos = -1;
         for (uint32_t j = 0;; j++) {
             const uint4 w = philox4x32_10(j, chunk, nd.op_index, s, key0, key1);
-            const int A = count_above<5>(TA, w.x);
-            const int B = count_above<8>(TB, w.y);
-            pos += 1 + 256 * A + B;
+            pos += 1 + gap_count(T, inv, w.x);
             if (pos >= n_trials) break;
-            const uint32_t unit = s * kSegUnits + uint32_t(pos >> 6);
-            const unsigned long long bit = 1ull << (pos & 63);
-            const uint32_t pk = 1u + __umulhi(w.z, npauli);
-            uint32_t p0, p1 = 0;
-            uint32_t c0, c1 = 0xFFFFFFFFu;
-            if (nd.kind == N_DEP2) {
-                p0 = pk >> 2;
-                p1 = pk & 3u;
-                c0 = __ldg(tg + 2 * unit);
-                c1 = __ldg(tg + 2 * unit + 1);
-            } else {
-                p0 = nd.kind == N_XERR ? 1u : nd.kind == N_ZERR ? 2u : pk;
-                c0 = __ldg(tg + unit);
-            }
-            const uint32_t xs0 = c0 & 0xFFFFu, zs0 = c0 >> 16;
-            if ((p0 & 1u) && xs0 != kDeadSlot)
-                atomicXor(reinterpret_cast<unsigned long long *>(&F[xs0 * K + k]), bit);
-            if ((p0 & 2u) && zs0 != kDeadSlot)
-                atomicXor(reinterpret_cast<unsigned long long *>(&F[zs0 * K + k]), bit);
-            if (p1) {
-                const uint32_t xs1 = c1 & 0xFFFFu, zs1 = c1 >> 16;
-                if ((p1 & 1u) && xs1 != kDeadSlot)
-                    atomicXor(reinterpret_cast<unsigned long long *>(&F[xs1 * K + k]), bit);
-                if ((p1 & 2u) && zs1 != kDeadSlot)
-                    atomicXor(reinterpret_cast<unsigned long long *>(&F[zs1 * K + k]), bit);
-            }
+            apply_event<K>(F, tg, nd, npauli, s, pos, w.y, k);
+            pos += 1 + gap_count(T, inv, w.z);
+            if (pos >= n_trials) break;
+            apply_event<K>(F, tg, nd, npauli, s, pos, w.w, k);
         }
     }
 }
 
 // Runs the whole program for one tile of K chunks starting at output column col0.
 template <int K>
-__device__ __forceinline__ void run_tile(const KernelArgs &P, uint64_t *F, const uint32_t *T, uint64_t col0) {
+__device__ __forceinline__ void run_tile(const KernelArgs &P, uint64_t *F, uint64_t col0) {
     const uint64_t rem = P.n_cols - col0;
     const int nvalid = rem < uint64_t(K) ? int(rem) : K;
     const uint32_t chunk0 = P.first_chunk + uint32_t(col0);
@@ -155,7 +164,7 @@ __device__ __forceinline__ void run_tile(const KernelArgs &P, uint64_t *F, const
             }
             break;
         case L_NOISE:
-            noise_layer<K>(F, T, P.noise[ly.aux], P.args, P.key0, P.key1, chunk0, nvalid);
+            noise_layer<K>(F, P.tables, P.noise[ly.aux], P.args, P.key0, P.key1, chunk0, nvalid);
             break;
         case L_DET:
             for (uint32_t i = threadIdx.x; i < ly.count * K; i += nt) {
@@ -201,11 +210,7 @@ __device__ __forceinline__ void run_tile(const KernelArgs &P, uint64_t *F, const
 template <int K>
 __global__ void __launch_bounds__(1024) frame_kernel(const KernelArgs P) {
     extern __shared__ uint64_t smem[];
-    uint64_t *F = smem;
-    uint32_t *T = reinterpret_cast<uint32_t *>(smem + size_t(P.n_slots) * K);
-    for (uint32_t i = threadIdx.x; i < P.n_tables * kTableWords; i += blockDim.x) T[i] = __ldg(P.tables + i);
-    __syncthreads();
-    run_tile<K>(P, F, T, uint64_t(blockIdx.x) * K);
+    run_tile<K>(P, smem, uint64_t(blockIdx.x) * K);
 }
 
 // ------------------------------------------------------------- host code
@@ -307,10 +312,20 @@ struct LaunchShape {
 
 // Tile shape: as many chunks per CTA as shared memory allows (fewer program
 // re-reads, wider detector stores), but enough tiles to fill every SM.
+static int env_int(const char *name, int dflt) {
+    const char *v = std::getenv(name);
+    return (v && *v) ? std::atoi(v) : dflt;
+}
+
+// Tuning knobs (autotuner / sweeps): TMCS_TILE_K caps the chunks per CTA,
+// TMCS_THREADS fixes the CTA size. Both only change the launch shape, never
+// the output bits.
 static LaunchShape choose_shape(const Program &P, uint64_t n_cols, const DeviceLimits &lim) {
-    const size_t tbytes = P.tables.size() * 4;
+    const size_t tbytes = 0;  // gap tables are read through L1, not staged
     LaunchShape s;
     int K = 16;
+    const int kcap = env_int("TMCS_TILE_K", 16);
+    while (K > 1 && K > kcap) K >>= 1;
     while (K > 1 && size_t(P.n_slots) * 8 * K + tbytes > lim.smem_optin) K >>= 1;
     while (K > 1 && (n_cols + K - 1) / K < uint64_t(2 * lim.sms)) K >>= 1;
     s.K = K;
@@ -319,6 +334,8 @@ static LaunchShape choose_shape(const Program &P, uint64_t n_cols, const DeviceL
     const size_t per_sm = std::max<size_t>(1, lim.smem_per_sm / std::max<size_t>(s.smem + 1024, 1));
     int threads = int(2048 / std::min<size_t>(per_sm, 8));
     threads = std::max(128, std::min(1024, threads));
+    const int tforce = env_int("TMCS_THREADS", 0);
+    if (tforce >= 32 && tforce <= 1024 && tforce % 32 == 0) threads = tforce;
     s.threads = threads;
     return s;
 }
@@ -356,7 +373,7 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
     DeviceLimits lim;
     if ((rc = device_limits(&lim))) return rc;
     const Program &P = c->prog;
-    if (size_t(P.n_slots) * 8 + P.tables.size() * 4 > lim.smem_optin)
+    if (size_t(P.n_slots) * 8 > lim.smem_optin)
         return fail(TMCS_E_INVALID, "circuit needs " + std::to_string(P.n_slots) +
                                         " frame slots; one 64-shot chunk does not fit in shared memory");
     if (P.layers.empty()) return TMCS_OK;
@@ -368,7 +385,6 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
     a.tables = dp->tables;
     a.n_layers = uint32_t(P.layers.size());
     a.n_slots = P.n_slots;
-    a.n_tables = uint32_t(P.table_p.size());
     a.key0 = uint32_t(seed);
     a.key1 = uint32_t(seed >> 32);
     a.first_chunk = uint32_t(first_chunk);

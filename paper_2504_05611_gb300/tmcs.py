@@ -71,12 +71,12 @@ def lib() -> ctypes.CDLL:
         L.tmcs_sample.argtypes = [P, U64, U64, P, P, P]
         L.tmcs_sample_range.argtypes = [P, U64, U64, U64, P, P, P]
         L.tmcs_batch_sample.argtypes = [P, ctypes.c_size_t, P]
-        L.tmcs_debug_gap_tables.argtypes = [ctypes.c_double, P, P]
+        L.tmcs_debug_gap_table.argtypes = [ctypes.c_double, P]
         L.tmcs_last_error.argtypes = []
         L.tmcs_last_error.restype = ctypes.c_char_p
         for f in ("tmcs_circuit_build", "tmcs_circuit_free", "tmcs_circuit_info", "tmcs_circuit_stats",
                   "tmcs_reference_sample", "tmcs_sample", "tmcs_sample_range", "tmcs_batch_sample",
-                  "tmcs_debug_gap_tables"):
+                  "tmcs_debug_gap_table"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -144,11 +144,10 @@ def tmcs_reference_sample(handle: int) -> np.ndarray:
     return np.unpackbits(buf, bitorder="little")[:n]
 
 
-def tmcs_debug_gap_tables(p: float) -> Tuple[np.ndarray, np.ndarray]:
-    ta = np.zeros(16, dtype=np.uint32)
-    tb = np.zeros(255, dtype=np.uint32)
-    _check(lib().tmcs_debug_gap_tables(float(p), ta.ctypes.data, tb.ctypes.data))
-    return ta, tb
+def tmcs_debug_gap_table(p: float) -> np.ndarray:
+    t = np.zeros(4096, dtype=np.uint32)
+    _check(lib().tmcs_debug_gap_table(float(p), t.ctypes.data))
+    return t
 
 
 def _dev_ptr(buf) -> Optional[int]:

@@ -8,9 +8,9 @@ multiplier, key schedule or output wiring in the oracle breaks the round
 trip. Output statistics are checked too. (An independent implementation on
 the GPU, cuRAND's Philox4_32_10, is compared in tests/test_gpu_rng.py.)
 
-The gap tables are pinned by the distribution they induce: P(A >= a) and
-P(B >= b) read off the tables must equal the geometric tails to within the
-2^-32 quantisation.
+The gap table is pinned by the distribution it induces: P(G >= g) read off
+the table must equal the geometric tail (1-p)^g to within the 2^-32
+quantisation.
 """
 import math
 
@@ -70,19 +70,17 @@ def test_philox_output_statistics():
 
 
 @pytest.mark.parametrize("p", [1e-4, 1e-3, 1e-2, 0.1, 0.5, 0.9])
-def test_gap_tables_induce_geometric_tails(p):
-    ta, tb = oracle.gap_tables(p)
-    q = (1 - p) ** 256
-    for a in range(1, 17):
-        assert abs(int(ta[a - 1]) / 2 ** 32 - q ** a) <= 2.0 ** -31
-    for b in range(1, 256):
-        want = ((1 - p) ** b - q) / (1 - q)
-        assert abs(int(tb[b - 1]) / 2 ** 32 - want) <= 2.0 ** -31 + 1e-12
-    assert np.all(np.diff(ta.astype(np.int64)) <= 0) and np.all(np.diff(tb.astype(np.int64)) <= 0)
+def test_gap_table_induces_geometric_tails(p):
+    """P(G >= g) = T[g] / 2^32 must equal (1-p)^g, the geometric tail, to
+    within the 2^-32 quantisation (plus double rounding of the power)."""
+    t = oracle.gap_table(p).astype(np.int64)
+    g = np.arange(1, 4097, dtype=np.float64)
+    want = np.array([(1 - p) ** int(v) for v in g])
+    assert np.all(np.abs(t / 2.0 ** 32 - want) <= 2.0 ** -31 + 1e-12 * want)
+    assert np.all(np.diff(t) <= 0)
 
 
-def test_gap_tables_edge_probabilities():
-    ta, tb = oracle.gap_tables(1.0)
-    assert not ta.any() and not tb.any()   # p = 1: every trial is an event
-    ta, tb = oracle.gap_tables(1e-12)      # tiny p: A almost surely >= 16
-    assert ta[-1] > 0xFFFF0000
+def test_gap_table_edge_probabilities():
+    assert not oracle.gap_table(1.0).any()          # p = 1: every trial is an event
+    t = oracle.gap_table(1e-12)                       # tiny p: G reaches the 4096 cap
+    assert t[-1] > 0xFFFF0000
