@@ -167,6 +167,14 @@ typedef struct {
  */
 int tmcs_batch_sample(const tmcs_job *jobs, size_t n_jobs, void *stream);
 
+/*
+ * Synchronous device-side error check for the current device: returns
+ * TMCS_E_TIMEOUT (and clears the flag) if any sampling kernel since the last
+ * check gave up on a bounded wait (its outputs are then incomplete), else
+ * TMCS_OK. Blocks until prior work on the device's legacy stream is done.
+ */
+int tmcs_check_device(void);
+
 /* Thread-local description of the last error of this thread ("" if none). */
 const char *tmcs_last_error(void);
 

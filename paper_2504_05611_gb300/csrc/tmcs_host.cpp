@@ -89,6 +89,84 @@ struct IRParity {
 
 }  // namespace
 
+// Checks every invariant the kernel relies on for memory safety: staged
+// blocks 16-byte aligned and at most kStageWords words, every slot index
+// below n_slots, list bounds inside their block, detector and observable ids
+// in range, noise windows inside the event buffer. Runs after every compile.
+static int validate_program(const Program &P, uint64_t n_det, uint64_t n_obs) {
+    auto bad = [](const std::string &m) { return fail(TMCS_E_INVALID, "internal: program check failed: " + m); };
+    if (P.args.size() % 4) return bad("args not padded");
+    for (size_t l = 0; l < P.layers.size(); l++) {
+        const Layer &ly = P.layers[l];
+        const std::string at = "layer " + std::to_string(l);
+        if (ly.nwords) {
+            if (ly.off % 4 || ly.nwords % 4 || ly.nwords > kStageWords || size_t(ly.off) + ly.nwords > P.args.size())
+                return bad(at + ": staged block misaligned or out of range");
+        }
+        const uint32_t *b = P.args.data() + ly.off;
+        switch (ly.kind) {
+        case L_ZERO:
+        case L_OBSOUT:
+            if (!ly.nwords || ly.count > ly.nwords) return bad(at + ": block too small");
+            for (uint32_t i = 0; i < ly.count; i++)
+                if (b[i] >= P.n_slots) return bad(at + ": slot out of range");
+            if (ly.kind == L_OBSOUT && ly.count > n_obs) return bad(at + ": observable out of range");
+            break;
+        case L_XOR:
+        case L_COPY:
+            if (!ly.nwords || ly.count > ly.nwords) return bad(at + ": block too small");
+            for (uint32_t i = 0; i < ly.count; i++)
+                if ((b[i] & 0xFFFFu) >= P.n_slots || (b[i] >> 16) >= P.n_slots) return bad(at + ": slot out of range");
+            break;
+        case L_DET:
+        case L_OBS: {
+            if (!ly.nwords || ly.count + 1 > ly.nwords) return bad(at + ": block too small");
+            for (uint32_t d = 0; d < ly.count; d++) {
+                const uint32_t lo = b[d], hi = b[d + 1];
+                if (lo < ly.count + 1 || hi < lo || hi > ly.nwords) return bad(at + ": list bounds");
+                if (ly.kind == L_OBS && hi == lo) return bad(at + ": observable list without accumulator");
+                for (uint32_t t = lo; t < hi; t++)
+                    if (b[t] >= P.n_slots) return bad(at + ": slot out of range");
+            }
+            if (ly.kind == L_DET && uint64_t(ly.aux) + ly.count > n_det) return bad(at + ": detector out of range");
+            break;
+        }
+        case L_NGEN: {
+            if (ly.nwords) return bad(at + ": generation layer with a block");
+            uint64_t segs = 0;
+            for (uint32_t i = 0; i < ly.count; i++) {
+                if (size_t(ly.aux) + i >= P.noise.size()) return bad(at + ": noise descriptor out of range");
+                segs += P.noise[ly.aux + i].n_seg;
+            }
+            if (segs != ly.aux2 || ly.aux2 > P.max_window_segs) return bad(at + ": window size");
+            break;
+        }
+        case L_NAPPLY: {
+            if (ly.nwords || ly.aux >= P.noise.size()) return bad(at + ": apply layer");
+            if (uint64_t(ly.aux2) + P.noise[ly.aux].n_seg > P.max_window_segs) return bad(at + ": window base");
+            break;
+        }
+        default:
+            return bad(at + ": unknown kind");
+        }
+    }
+    for (size_t i = 0; i < P.noise.size(); i++) {
+        const NoiseDesc &nd = P.noise[i];
+        const uint64_t words = uint64_t(nd.kind == N_DEP2 ? 2 : 1) * nd.n_units;
+        if (nd.kind > N_DEP2 || nd.table >= P.table_p.size() || nd.n_seg != (nd.n_units + kSegUnits - 1) / kSegUnits ||
+            uint64_t(nd.tgt_off) + words > P.args.size())
+            return bad("noise descriptor " + std::to_string(i));
+        for (uint64_t w = 0; w < words; w++) {
+            const uint32_t v = P.args[nd.tgt_off + w];
+            if (((v & 0xFFFFu) != kDeadSlot && (v & 0xFFFFu) >= P.n_slots) ||
+                ((v >> 16) != kDeadSlot && (v >> 16) >= P.n_slots))
+                return bad("noise target slot out of range");
+        }
+    }
+    if (P.tables.size() != P.table_p.size() * kTableWords) return bad("table size");
+    return TMCS_OK;
+}
+
 int compile(tmcs_circuit *c, uint32_t flags) {
     const bool prune = !(flags & TMCS_FLAG_NO_PRUNE);
     const uint64_t Q = c->n_qubits;
@@ -402,86 +480,178 @@ int compile(tmcs_circuit *c, uint32_t flags) {
     };
 
     // ---- emission
+    //
+    // Every layer's arguments form one 16-byte-aligned block of at most
+    // kStageWords words (larger layers are split; their items are
+    // independent). Item order inside update layers cycles through the 16
+    // residues of the destination slot, so the lanes of a warp tend to hit
+    // distinct shared-memory banks.
     tmcs_stats &S = c->stats;
     S = tmcs_stats{};
+    auto pad4 = [&]() {
+        while (P.args.size() % 4) P.args.push_back(0u);
+    };
+    // off = start of the layer's block (4-word aligned, written by the caller
+    // after pad4()); staged = false for layers without a block.
+    auto push_layer = [&](uint32_t kind, uint32_t count, size_t off, uint32_t aux, uint32_t aux2,
+                          bool staged) {
+        Layer ly{};
+        ly.kind = kind;
+        ly.count = count;
+        ly.aux = aux;
+        ly.aux2 = aux2;
+        if (staged) {
+            pad4();
+            ly.off = uint32_t(off);
+            ly.nwords = uint32_t(P.args.size() - off);
+        }
+        P.layers.push_back(ly);
+    };
+    auto bank_order = [](std::vector<uint32_t> &w) {
+        std::vector<std::vector<uint32_t>> bucket(16);
+        for (uint32_t v : w) bucket[v & 15u].push_back(v);
+        std::vector<uint32_t> out;
+        out.reserve(w.size());
+        for (size_t r = 0; out.size() < w.size(); r++)
+            for (auto &bk : bucket)
+                if (r < bk.size()) out.push_back(bk[r]);
+        w.swap(out);
+    };
+    auto emit_words = [&](uint32_t kind, std::vector<uint32_t> &w, bool order) {
+        if (order) bank_order(w);
+        for (size_t b = 0; b < w.size(); b += kStageWords) {
+            const size_t e = std::min(w.size(), b + kStageWords);
+            pad4();
+            const size_t off = P.args.size();
+            P.args.insert(P.args.end(), w.begin() + b, w.begin() + e);
+            push_layer(kind, uint32_t(e - b), off, 0, 0, true);
+        }
+    };
+    // noise descriptors (program order) and their generation windows
+    std::vector<uint32_t> noise_layer_desc(n_layers_body, 0xFFFFFFFFu);
+    std::vector<uint32_t> desc_win_first, desc_win_count, desc_win_segs, desc_win_base;
+    for (uint32_t l = 0; l < n_layers_body; l++) {
+        if (layer_kind[l] != I_NOISE) continue;
+        const IRNoise &nz = noise[ir[layer_insts[l][0]].a];
+        NoiseDesc nd{};
+        nd.op_index = nz.op;
+        nd.kind = nz.kind;
+        int rc = table_for(nz.p, &nd.table);
+        if (rc) return rc;
+        const uint32_t nq = uint32_t(nz.comp.size() / 2);
+        nd.n_units = nz.kind == N_DEP2 ? nq / 2 : nq;
+        nd.n_seg = (nd.n_units + kSegUnits - 1) / kSegUnits;
+        nd.tgt_off = uint32_t(P.args.size());
+        for (uint32_t q = 0; q < nq; q++) {
+            uint32_t xs = nz.live[2 * q] ? slot[nz.comp[2 * q]] : kDeadSlot;
+            uint32_t zs = nz.live[2 * q + 1] ? slot[nz.comp[2 * q + 1]] : kDeadSlot;
+            P.args.push_back(xs | (zs << 16));
+            S.live_components += (xs != kDeadSlot) + (zs != kDeadSlot);
+        }
+        noise_layer_desc[l] = uint32_t(P.noise.size());
+        P.noise.push_back(nd);
+        S.n_noise_ops++;
+        S.n_noise_units += nd.n_units;
+        S.n_noise_segments += nd.n_seg;
+    }
+    {
+        const uint32_t nd_count = uint32_t(P.noise.size());
+        desc_win_first.assign(nd_count, 0);
+        desc_win_count.assign(nd_count, 0);
+        desc_win_segs.assign(nd_count, 0);
+        desc_win_base.assign(nd_count, 0);
+        uint32_t i = 0;
+        while (i < nd_count) {
+            uint32_t j = i, segs = 0;
+            while (j < nd_count && (j == i || (segs + P.noise[j].n_seg <= kWindowSegs && j - i < kWindowOps))) {
+                desc_win_base[j] = segs;
+                segs += P.noise[j].n_seg;
+                j++;
+            }
+            for (uint32_t k = i; k < j; k++) {
+                desc_win_first[k] = i;
+                desc_win_count[k] = j - i;
+                desc_win_segs[k] = segs;
+            }
+            P.max_window_segs = std::max(P.max_window_segs, segs);
+            i = j;
+        }
+    }
     for (uint32_t l = 0; l < n_layers_body; l++) {
         const std::vector<uint32_t> &ins = layer_insts[l];
-        Layer ly{};
-        ly.count = uint32_t(ins.size());
-        ly.off = uint32_t(P.args.size());
         switch (layer_kind[l]) {
-        case I_ZERO:
-            ly.kind = L_ZERO;
-            for (uint32_t k : ins) P.args.push_back(slot[ir[k].a]);
+        case I_ZERO: {
+            std::vector<uint32_t> w;
+            w.reserve(ins.size());
+            for (uint32_t k : ins) w.push_back(slot[ir[k].a]);
+            emit_words(L_ZERO, w, true);
             S.n_zero += ins.size();
             break;
+        }
         case I_XOR:
-        case I_COPY:
-            ly.kind = layer_kind[l] == I_XOR ? L_XOR : L_COPY;
-            for (uint32_t k : ins) P.args.push_back(slot[ir[k].a] | (slot[ir[k].b] << 16));
+        case I_COPY: {
+            std::vector<uint32_t> w;
+            w.reserve(ins.size());
+            for (uint32_t k : ins) w.push_back(slot[ir[k].a] | (slot[ir[k].b] << 16));
+            emit_words(layer_kind[l] == I_XOR ? L_XOR : L_COPY, w, true);
             (layer_kind[l] == I_XOR ? S.n_xor : S.n_copy) += ins.size();
             break;
+        }
         case I_NOISE: {
-            const IRNoise &nz = noise[ir[ins[0]].a];
-            NoiseDesc nd{};
-            nd.op_index = nz.op;
-            nd.kind = nz.kind;
-            int rc = table_for(nz.p, &nd.table);
-            if (rc) return rc;
-            const uint32_t nq = uint32_t(nz.comp.size() / 2);
-            nd.n_units = nz.kind == N_DEP2 ? nq / 2 : nq;
-            nd.n_seg = (nd.n_units + kSegUnits - 1) / kSegUnits;
-            nd.tgt_off = uint32_t(P.args.size());
-            for (uint32_t q = 0; q < nq; q++) {
-                uint32_t xs = nz.live[2 * q] ? slot[nz.comp[2 * q]] : kDeadSlot;
-                uint32_t zs = nz.live[2 * q + 1] ? slot[nz.comp[2 * q + 1]] : kDeadSlot;
-                P.args.push_back(xs | (zs << 16));
-                S.live_components += (xs != kDeadSlot) + (zs != kDeadSlot);
-            }
-            ly.kind = L_NOISE;
-            ly.count = nd.n_seg;
-            ly.off = nd.tgt_off;
-            ly.aux = uint32_t(P.noise.size());
-            P.noise.push_back(nd);
-            S.n_noise_ops++;
-            S.n_noise_units += nd.n_units;
-            S.n_noise_segments += nd.n_seg;
+            const uint32_t d = noise_layer_desc[l];
+            if (desc_win_first[d] == d) push_layer(L_NGEN, desc_win_count[d], 0, d, desc_win_segs[d], false);
+            push_layer(L_NAPPLY, 1, 0, d, desc_win_base[d], false);
             break;
         }
         case I_DET:
         case I_OBS: {
-            ly.kind = layer_kind[l] == I_DET ? L_DET : L_OBS;
-            ly.aux = layer_kind[l] == I_DET ? pars[ir[ins[0]].a].acc : 0;
-            const size_t bounds = P.args.size();
-            P.args.resize(bounds + ins.size() + 1);
-            for (size_t e = 0; e < ins.size(); e++) {
-                const IRParity &pp = pars[ir[ins[e]].a];
-                P.args[bounds + e] = uint32_t(P.args.size());
-                if (ly.kind == L_OBS) P.args.push_back(slot[pp.acc]);
-                for (uint32_t r : pp.recs) P.args.push_back(slot[r]);
-                S.n_parity_terms += pp.recs.size();
+            const bool det = layer_kind[l] == I_DET;
+            size_t e = 0;
+            while (e < ins.size()) {
+                // greedily take detectors while bounds + lists fit one stage block
+                size_t f = e, words = 1;
+                while (f < ins.size()) {
+                    const size_t len = pars[ir[ins[f]].a].recs.size() + (det ? 0 : 1);
+                    if (words + 1 + len > kStageWords && f > e) break;
+                    words += 1 + len;
+                    f++;
+                }
+                if (words > kStageWords)
+                    return fail(TMCS_E_INVALID, "a detector or observable lists more than " +
+                                                    std::to_string(kStageWords - 2) + " records");
+                pad4();
+                const size_t off = P.args.size();
+                const size_t nb = f - e + 1;
+                P.args.resize(off + nb);
+                for (size_t i = e; i < f; i++) {
+                    const IRParity &pp = pars[ir[ins[i]].a];
+                    P.args[off + (i - e)] = uint32_t(P.args.size() - off);
+                    if (!det) P.args.push_back(slot[pp.acc]);
+                    for (uint32_t r : pp.recs) P.args.push_back(slot[r]);
+                    S.n_parity_terms += pp.recs.size();
+                }
+                P.args[off + (f - e)] = uint32_t(P.args.size() - off);
+                push_layer(det ? L_DET : L_OBS, uint32_t(f - e), off, det ? pars[ir[ins[e]].a].acc : 0, 0, true);
+                e = f;
             }
-            P.args[bounds + ins.size()] = uint32_t(P.args.size());
             break;
         }
         }
-        P.layers.push_back(ly);
     }
     if (c->n_obs) {
-        Layer ly{};
-        ly.kind = L_OBSOUT;
-        ly.count = uint32_t(c->n_obs);
-        ly.off = uint32_t(P.args.size());
-        for (uint64_t o = 0; o < c->n_obs; o++) P.args.push_back(slot[acc[o]]);
-        P.layers.push_back(ly);
+        std::vector<uint32_t> w;
+        for (uint64_t o = 0; o < c->n_obs; o++) w.push_back(slot[acc[o]]);
+        if (w.size() > kStageWords) return fail(TMCS_E_INVALID, "too many observables");
+        emit_words(L_OBSOUT, w, false);
     }
+    pad4();
     P.n_slots = n_slots;
     P.n_det = c->n_det;
     P.n_obs = c->n_obs;
     S.n_layers = P.layers.size();
     S.n_slots = n_slots;
     S.pruned_updates = pruned;
-    return TMCS_OK;
+    return validate_program(P, c->n_det, c->n_obs);
 }
 
 // ------------------------------------------------------------- audit

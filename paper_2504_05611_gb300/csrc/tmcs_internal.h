@@ -100,6 +100,8 @@ struct DeviceProgram {
     const uint32_t *args = nullptr;
     const NoiseDesc *noise = nullptr;
     const uint32_t *tables = nullptr;
+    int tuned_K = 0;        // launch shape chosen by the autotuner (0: not tuned)
+    int tuned_threads = 0;
 };
 
 // Per-device scratch of the library: a status word that kernels set when a

@@ -18,6 +18,8 @@
 // is identical to the CPU oracle's, so outputs match it bit for bit.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -69,8 +71,10 @@ struct KernelArgs {
     const uint32_t *args;
     const NoiseDesc *noise;
     const uint32_t *tables;
+    uint32_t *status;      // device status word (bit 0: a bounded wait expired)
     uint32_t n_layers;
     uint32_t n_slots;
+    uint32_t max_window_segs;  // event buffer holds max_window_segs * K units
     uint32_t key0, key1;
     uint32_t first_chunk;  // global chunk of output column 0
     uint64_t n_cols;       // output columns (chunks) of this call
@@ -79,19 +83,78 @@ struct KernelArgs {
     uint64_t *obs;
 };
 
+// Buffered events of one (segment, chunk) of a noise op: up to kEvCap events
+// as (position in segment: 12 bits | Pauli index << 12); if the walk had more,
+// it resumes at draw cont_d from position cont_pos when the op is applied.
+struct EvUnit {
+    uint16_t ev[kEvCap];
+    uint16_t n;
+    uint16_t cont_d;  // 0xFFFF: walk complete
+    int16_t cont_pos;
+    uint16_t pad;
+};
+static_assert(sizeof(EvUnit) == 24, "EvUnit layout");
+
+constexpr uint32_t kSpinLimit = 1u << 20;  // bounded mbarrier waits
+
+// ---- PTX wrappers: mbarrier + bulk asynchronous copy (TMA, 1-D)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for phase `parity` of `bar`; gives up after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kSpinLimit; it++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void xor_bit(uint64_t *F, uint32_t slot, uint32_t K, int k, unsigned long long bit) {
     if (slot != kDeadSlot) atomicXor(reinterpret_cast<unsigned long long *>(&F[slot * K + k]), bit);
 }
 
-// One event of a noise op: Pauli index from the word, applied to the live
-// frame components of the unit's target(s).
+// One event of a noise op: Pauli index pk applied to the live frame
+// components of the unit's target(s) in lane pos % 64 of chunk word k.
 template <int K>
-__device__ __forceinline__ void apply_event(uint64_t *F, const uint32_t *__restrict__ tg, const NoiseDesc &nd,
-                                            uint32_t npauli, uint32_t s, int pos, uint32_t w_pauli, int k) {
+__device__ __forceinline__ void apply_event(uint64_t *F, const uint32_t *__restrict__ tg, uint32_t kind,
+                                            uint32_t s, int pos, uint32_t pk, int k) {
     const uint32_t unit = s * kSegUnits + uint32_t(pos >> 6);
     const unsigned long long bit = 1ull << (pos & 63);
-    const uint32_t pk = 1u + __umulhi(w_pauli, npauli);
-    if (nd.kind == N_DEP2) {
+    if (kind == N_DEP2) {
         const uint32_t c0 = __ldg(tg + 2 * unit), c1 = __ldg(tg + 2 * unit + 1);
         const uint32_t pa = pk >> 2, pb = pk & 3u;
         if (pa & 1u) xor_bit(F, c0 & 0xFFFFu, K, k, bit);
@@ -100,117 +163,310 @@ __device__ __forceinline__ void apply_event(uint64_t *F, const uint32_t *__restr
         if (pb & 2u) xor_bit(F, c1 >> 16, K, k, bit);
     } else {
         const uint32_t c0 = __ldg(tg + unit);
-        const uint32_t pa = nd.kind == N_XERR ? 1u : nd.kind == N_ZERR ? 2u : pk;
+        const uint32_t pa = kind == N_XERR ? 1u : kind == N_ZERR ? 2u : pk;
         if (pa & 1u) xor_bit(F, c0 & 0xFFFFu, K, k, bit);
         if (pa & 2u) xor_bit(F, c0 >> 16, K, k, bit);
     }
 }
 
-// Noise layer: one thread per (64-unit segment, chunk) walks the segment's
-// event stream; each Philox4x32-10 call yields two draws (gap word, Pauli
-// word).
+__device__ __forceinline__ uint32_t npauli_of(uint32_t kind) {
+    return kind == N_DEP2 ? 15u : kind == N_DEP1 ? 3u : 1u;
+}
+
+// Walks draws d = d0, d0+1, ... of one (segment, chunk) stream from position
+// pos. With buf != nullptr, events are stored until kEvCap are held (then the
+// resume point is recorded); with buf == nullptr they are applied to F.
 template <int K>
-__device__ __forceinline__ void noise_layer(uint64_t *F, const uint32_t *__restrict__ tables, const NoiseDesc nd,
-                                            const uint32_t *__restrict__ args, uint32_t key0,
-                                            uint32_t key1, uint32_t chunk0, int nvalid) {
-    const uint32_t *T = tables + size_t(nd.table) * kTableWords;
-    const float inv = __uint_as_float(__ldg(T + kGapLen));
-    const uint32_t npauli = nd.kind == N_DEP2 ? 15u : nd.kind == N_DEP1 ? 3u : 1u;
-    const uint32_t *tg = args + nd.tgt_off;
-    const uint32_t work = nd.n_seg * K;
-    for (uint32_t u = threadIdx.x; u < work; u += blockDim.x) {
-        const uint32_t s = u / K;
-        const int k = int(u % K);
-        if (k >= nvalid) continue;
-        const uint32_t chunk = chunk0 + uint32_t(k);
-        const int n_trials = 64 * int(min(kSegUnits, nd.n_units - s * kSegUnits));
-        int pos = -1;
-        for (uint32_t j = 0;; j++) {
-            const uint4 w = philox4x32_10(j, chunk, nd.op_index, s, key0, key1);
-            pos += 1 + gap_count(T, inv, w.x);
-            if (pos >= n_trials) break;
-            apply_event<K>(F, tg, nd, npauli, s, pos, w.y, k);
-            pos += 1 + gap_count(T, inv, w.z);
-            if (pos >= n_trials) break;
-            apply_event<K>(F, tg, nd, npauli, s, pos, w.w, k);
+__device__ __forceinline__ void walk_segment(const NoiseDesc &nd, const uint32_t *__restrict__ T, float inv,
+                                             uint32_t s, uint32_t chunk, uint32_t key0, uint32_t key1,
+                                             uint32_t d0, int pos, EvUnit *buf, uint64_t *F,
+                                             const uint32_t *__restrict__ tg, int k) {
+    const int n_trials = 64 * int(min(kSegUnits, nd.n_units - s * kSegUnits));
+    const uint32_t npauli = npauli_of(nd.kind);
+    uint32_t n = 0;
+    uint4 w = make_uint4(0, 0, 0, 0);
+    for (uint32_t d = d0;; d++) {
+        if (d == d0 || (d & 1u) == 0) w = philox4x32_10(d >> 1, chunk, nd.op_index, s, key0, key1);
+        const uint32_t wg = (d & 1u) ? w.z : w.x;
+        const uint32_t wp = (d & 1u) ? w.w : w.y;
+        const int prev = pos;
+        pos += 1 + gap_count(T, inv, wg);
+        if (pos >= n_trials) break;
+        const uint32_t pk = 1u + __umulhi(wp, npauli);
+        if (buf) {
+            if (n == kEvCap) {
+                buf->cont_d = uint16_t(d);
+                buf->cont_pos = int16_t(prev);
+                buf->n = uint16_t(n);
+                return;
+            }
+            buf->ev[n++] = uint16_t(uint32_t(pos) | (pk << 12));
+            prefetch_l1(tg + (nd.kind == N_DEP2 ? 2u : 1u) * (s * kSegUnits + uint32_t(pos >> 6)));
+        } else {
+            apply_event<K>(F, tg, nd.kind, s, pos, pk, k);
         }
+    }
+    if (buf) {
+        buf->n = uint16_t(n);
+        buf->cont_d = 0xFFFFu;
     }
 }
 
 // Runs the whole program for one tile of K chunks starting at output column col0.
+//
+// Update layers give each thread whole ops: an op's K chunk words of a slot
+// are contiguous, so one item moves KV vectors (128-bit when K >= 2). Ops
+// are unrolled by U so a thread keeps U*KV independent loads in flight.
 template <int K>
-__device__ __forceinline__ void run_tile(const KernelArgs &P, uint64_t *F, uint64_t col0) {
+__device__ __forceinline__ void run_tile(const KernelArgs &P, uint64_t *F, uint32_t *stage0, uint32_t *stage1,
+                                         EvUnit *evbuf, uint64_t *bars, int *abort_flag, uint64_t col0) {
+    constexpr int V = K >= 2 ? 2 : 1;  // 64-bit words per vector
+    constexpr int KV = K / V;          // vectors per slot
+    constexpr int U = KV >= 4 ? 1 : 4 / KV;  // ops per unrolled step
+    using VecT = typename std::conditional<V == 2, ulonglong2, unsigned long long>::type;
+    VecT *Fv = reinterpret_cast<VecT *>(F);
     const uint64_t rem = P.n_cols - col0;
     const int nvalid = rem < uint64_t(K) ? int(rem) : K;
     const uint32_t chunk0 = P.first_chunk + uint32_t(col0);
-    const uint32_t nt = blockDim.x;
+    const uint32_t T_ = blockDim.x, tid = threadIdx.x;
+    uint32_t parity[2] = {0u, 0u};
+
+    auto issue = [&](uint32_t L) {
+        if (tid == 0 && L < P.n_layers) {
+            const Layer ly = P.layers[L];
+            if (ly.nwords) {
+                uint32_t *dst = (L & 1u) ? stage1 : stage0;
+                fence_proxy_async();
+                mbar_arrive_expect_tx(&bars[L & 1u], ly.nwords * 4u);
+                bulk_copy_g2s(dst, P.args + ly.off, ly.nwords * 4u, &bars[L & 1u]);
+            }
+        }
+    };
+    issue(0);
     for (uint32_t L = 0; L < P.n_layers; L++) {
         const Layer ly = P.layers[L];
-        const uint32_t *__restrict__ a = P.args + ly.off;
-        switch (ly.kind) {
-        case L_ZERO:
-            for (uint32_t i = threadIdx.x; i < ly.count * K; i += nt) F[__ldg(a + i / K) * K + i % K] = 0ull;
-            break;
-        case L_XOR:
-            for (uint32_t i = threadIdx.x; i < ly.count * K; i += nt) {
-                const uint32_t w = __ldg(a + i / K);
-                F[(w & 0xFFFFu) * K + i % K] ^= F[(w >> 16) * K + i % K];
+        issue(L + 1);
+        const uint32_t *st = (L & 1u) ? stage1 : stage0;
+        bool ready = true;
+        if (ly.nwords) {
+            ready = mbar_wait_bounded(&bars[L & 1u], parity[L & 1u]);
+            parity[L & 1u] ^= 1u;
+            if (!ready) *abort_flag = 1;
+        }
+        if (ready) {
+            switch (ly.kind) {
+            case L_ZERO: {
+                VecT z;
+                if constexpr (V == 2) z = make_ulonglong2(0ull, 0ull); else z = 0ull;
+                for (uint32_t i = tid; i < ly.count; i += T_) {
+                    VecT *d = Fv + st[i] * KV;
+#pragma unroll
+                    for (int v = 0; v < KV; v++) d[v] = z;
+                }
+                break;
             }
-            break;
-        case L_COPY:
-            for (uint32_t i = threadIdx.x; i < ly.count * K; i += nt) {
-                const uint32_t w = __ldg(a + i / K);
-                F[(w & 0xFFFFu) * K + i % K] = F[(w >> 16) * K + i % K];
+            case L_XOR:
+            case L_COPY: {
+                const uint32_t n = ly.count;
+                const bool is_xor = ly.kind == L_XOR;
+                for (uint32_t i0 = tid; i0 < n; i0 += U * T_) {
+                    uint32_t dsl[U], ssl[U];
+                    bool ok[U];
+#pragma unroll
+                    for (int r = 0; r < U; r++) {
+                        const uint32_t i = i0 + uint32_t(r) * T_;
+                        ok[r] = i < n;
+                        const uint32_t w = ok[r] ? st[i] : 0u;
+                        dsl[r] = (w & 0xFFFFu) * KV;
+                        ssl[r] = (w >> 16) * KV;
+                    }
+                    VecT a[U][KV], b[U][KV];
+#pragma unroll
+                    for (int r = 0; r < U; r++)
+                        if (ok[r]) {
+#pragma unroll
+                            for (int v = 0; v < KV; v++) {
+                                b[r][v] = Fv[ssl[r] + v];
+                                if (is_xor) a[r][v] = Fv[dsl[r] + v];
+                            }
+                        }
+#pragma unroll
+                    for (int r = 0; r < U; r++)
+                        if (ok[r]) {
+#pragma unroll
+                            for (int v = 0; v < KV; v++) {
+                                if constexpr (V == 2) {
+                                    Fv[dsl[r] + v] = is_xor ? make_ulonglong2(a[r][v].x ^ b[r][v].x, a[r][v].y ^ b[r][v].y)
+                                                            : b[r][v];
+                                } else {
+                                    Fv[dsl[r] + v] = is_xor ? (a[r][v] ^ b[r][v]) : b[r][v];
+                                }
+                            }
+                        }
+                }
+                break;
             }
-            break;
-        case L_NOISE:
-            noise_layer<K>(F, P.tables, P.noise[ly.aux], P.args, P.key0, P.key1, chunk0, nvalid);
-            break;
-        case L_DET:
-            for (uint32_t i = threadIdx.x; i < ly.count * K; i += nt) {
-                const uint32_t d = i / K;
-                const int k = int(i % K);
-                if (k >= nvalid) continue;
-                const uint32_t b = __ldg(a + d), e = __ldg(a + d + 1);
-                uint64_t v = 0;
-                for (uint32_t t = b; t < e; t++) v ^= F[__ldg(P.args + t) * K + k];
-                const uint64_t col = col0 + uint64_t(k);
-                if (col == P.n_cols - 1) v &= P.last_mask;
-                P.det[uint64_t(ly.aux + d) * P.n_cols + col] = v;
+            case L_NGEN: {
+                const uint32_t units = ly.aux2 * K;
+                for (uint32_t u = tid; u < units; u += T_) {
+                    const uint32_t ws = u / K;
+                    const int k = int(u % K);
+                    uint32_t di = ly.aux, base = 0;
+                    uint32_t nseg = P.noise[di].n_seg;
+                    while (ws >= base + nseg) {
+                        base += nseg;
+                        nseg = P.noise[++di].n_seg;
+                    }
+                    EvUnit *E = evbuf + u;
+                    if (k >= nvalid) {
+                        E->n = 0;
+                        E->cont_d = 0xFFFFu;
+                        continue;
+                    }
+                    const NoiseDesc nd = P.noise[di];
+                    const uint32_t *Tt = P.tables + size_t(nd.table) * kTableWords;
+                    const float inv = __uint_as_float(__ldg(Tt + kGapLen));
+                    walk_segment<K>(nd, Tt, inv, ws - base, chunk0 + uint32_t(k), P.key0, P.key1, 0u, -1, E,
+                                    nullptr, P.args + nd.tgt_off, k);
+                }
+                break;
             }
-            break;
-        case L_OBS:
-            for (uint32_t i = threadIdx.x; i < ly.count * K; i += nt) {
-                const uint32_t d = i / K;
-                const int k = int(i % K);
-                const uint32_t b = __ldg(a + d), e = __ldg(a + d + 1);
-                uint64_t v = 0;
-                for (uint32_t t = b + 1; t < e; t++) v ^= F[__ldg(P.args + t) * K + k];
-                F[__ldg(P.args + b) * K + k] ^= v;
+            case L_NAPPLY: {
+                const NoiseDesc nd = P.noise[ly.aux];
+                const uint32_t *tg = P.args + nd.tgt_off;
+                const uint32_t items = nd.n_seg * K * kEvCap;
+                for (uint32_t i = tid; i < items; i += T_) {
+                    const uint32_t uu = i / kEvCap, e = i % kEvCap;
+                    const uint32_t s = uu / K;
+                    const int k = int(uu % K);
+                    if (k >= nvalid) continue;
+                    const EvUnit *E = evbuf + (ly.aux2 + s) * K + uint32_t(k);
+                    if (e < E->n) {
+                        const uint32_t v = E->ev[e];
+                        apply_event<K>(F, tg, nd.kind, s, int(v & 0xFFFu), v >> 12, k);
+                    }
+                    if (e == 0 && E->cont_d != 0xFFFFu) {
+                        const uint32_t *Tt = P.tables + size_t(nd.table) * kTableWords;
+                        const float inv = __uint_as_float(__ldg(Tt + kGapLen));
+                        walk_segment<K>(nd, Tt, inv, s, chunk0 + uint32_t(k), P.key0, P.key1, E->cont_d,
+                                        E->cont_pos, nullptr, F, tg, k);
+                    }
+                }
+                break;
             }
-            break;
-        case L_OBSOUT:
-            for (uint32_t i = threadIdx.x; i < ly.count * K; i += nt) {
-                const uint32_t o = i / K;
-                const int k = int(i % K);
-                if (k >= nvalid) continue;
-                uint64_t v = F[__ldg(a + o) * K + k];
-                const uint64_t col = col0 + uint64_t(k);
-                if (col == P.n_cols - 1) v &= P.last_mask;
-                P.obs[uint64_t(o) * P.n_cols + col] = v;
+            case L_DET: {
+                for (uint32_t d = tid; d < ly.count; d += T_) {
+                    const uint32_t lo = st[d], hi = st[d + 1];
+                    VecT v[KV];
+#pragma unroll
+                    for (int q = 0; q < KV; q++) {
+                        if constexpr (V == 2) v[q] = make_ulonglong2(0ull, 0ull); else v[q] = 0ull;
+                    }
+                    for (uint32_t t = lo; t < hi; t++) {
+                        const VecT *x = Fv + st[t] * KV;
+#pragma unroll
+                        for (int q = 0; q < KV; q++) {
+                            if constexpr (V == 2) {
+                                const VecT y = x[q];
+                                v[q].x ^= y.x;
+                                v[q].y ^= y.y;
+                            } else {
+                                v[q] ^= x[q];
+                            }
+                        }
+                    }
+                    uint64_t *out = P.det + uint64_t(ly.aux + d) * P.n_cols + col0;
+                    const bool full = nvalid == K && col0 + K != P.n_cols;
+                    if (full && (reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
+#pragma unroll
+                        for (int q = 0; q < KV; q++) reinterpret_cast<VecT *>(out)[q] = v[q];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < KV; q++) {
+#pragma unroll
+                            for (int h = 0; h < V; h++) {
+                                const int k = q * V + h;
+                                uint64_t w;
+                                if constexpr (V == 2) w = h ? v[q].y : v[q].x; else w = v[q];
+                                if (k < nvalid)
+                                    out[k] = (col0 + uint64_t(k) == P.n_cols - 1) ? (w & P.last_mask) : w;
+                            }
+                        }
+                    }
+                }
+                break;
             }
-            break;
-        default:
-            break;
+            case L_OBS: {
+                const uint32_t n = ly.count * K;
+                for (uint32_t i = tid; i < n; i += T_) {
+                    const uint32_t d = i / K;
+                    const int k = int(i % K);
+                    const uint32_t b = st[d], e = st[d + 1];
+                    uint64_t v = 0;
+                    for (uint32_t t = b + 1; t < e; t++) v ^= F[st[t] * K + k];
+                    F[st[b] * K + k] ^= v;
+                }
+                break;
+            }
+            case L_OBSOUT: {
+                const uint32_t n = ly.count * K;
+                for (uint32_t i = tid; i < n; i += T_) {
+                    const uint32_t o = i / K;
+                    const int k = int(i % K);
+                    if (k >= nvalid) continue;
+                    uint64_t v = F[st[o] * K + k];
+                    const uint64_t col = col0 + uint64_t(k);
+                    if (col == P.n_cols - 1) v &= P.last_mask;
+                    P.obs[uint64_t(o) * P.n_cols + col] = v;
+                }
+                break;
+            }
+            default:
+                break;
+            }
         }
         __syncthreads();
+        if (*abort_flag) {
+            // a staging copy never arrived: wait (bounded) for the one still in
+            // flight, record the failure and leave together
+            if (tid == 0) {
+                if (L + 1 < P.n_layers && P.layers[L + 1].nwords)
+                    mbar_wait_bounded(&bars[(L + 1) & 1u], parity[(L + 1) & 1u]);
+                atomicOr(P.status, 1u);
+            }
+            return;
+        }
     }
 }
 
 template <int K>
-__global__ void __launch_bounds__(1024) frame_kernel(const KernelArgs P) {
-    extern __shared__ uint64_t smem[];
-    run_tile<K>(P, smem, uint64_t(blockIdx.x) * K);
+__global__ void __launch_bounds__(512) frame_kernel(const KernelArgs P) {
+    extern __shared__ __align__(128) uint64_t smem[];
+    uint64_t *F = smem;
+    uint8_t *base = reinterpret_cast<uint8_t *>(smem) + ((size_t(P.n_slots) * K * 8 + 127) & ~size_t(127));
+    uint32_t *stage0 = reinterpret_cast<uint32_t *>(base);
+    uint32_t *stage1 = stage0 + kStageWords;
+    EvUnit *evbuf = reinterpret_cast<EvUnit *>(stage1 + kStageWords);
+    // same layout as kernel_smem_bytes(n_slots, max_window_segs, K)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(evbuf + size_t(P.max_window_segs) * K);
+    int *abort_flag = reinterpret_cast<int *>(bars + 2);
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    run_tile<K>(P, F, stage0, stage1, evbuf, bars, abort_flag, uint64_t(blockIdx.x) * K);
+}
+
+// Dynamic shared memory of frame_kernel<K>.
+static size_t kernel_smem_bytes(uint32_t n_slots, uint32_t max_window_segs, int K) {
+    size_t b = (size_t(n_slots) * K * 8 + 127) & ~size_t(127);
+    b += 2 * size_t(kStageWords) * 4;
+    b += size_t(max_window_segs) * K * sizeof(EvUnit);
+    b += 2 * 8 + 16;
+    return b;
 }
 
 // ------------------------------------------------------------- host code
@@ -310,34 +566,46 @@ struct LaunchShape {
     uint64_t tiles = 0;
 };
 
-// Tile shape: as many chunks per CTA as shared memory allows (fewer program
-// re-reads, wider detector stores), but enough tiles to fill every SM.
 static int env_int(const char *name, int dflt) {
     const char *v = std::getenv(name);
     return (v && *v) ? std::atoi(v) : dflt;
 }
 
-// Tuning knobs (autotuner / sweeps): TMCS_TILE_K caps the chunks per CTA,
-// TMCS_THREADS fixes the CTA size. Both only change the launch shape, never
-// the output bits.
-static LaunchShape choose_shape(const Program &P, uint64_t n_cols, const DeviceLimits &lim) {
-    const size_t tbytes = 0;  // gap tables are read through L1, not staged
+// Tile shape. Shared memory per 64-shot chunk is fixed by the circuit (its
+// frame slots), so the choice is how many chunks one CTA owns (K) and how many
+// threads run each layer: larger tiles amortise the per-layer cost (staging,
+// dispatch, barrier) over more shots, smaller ones put more CTAs on an SM to
+// overlap one CTA's barriers and noise walks with another's updates. The
+// autotuner below times the feasible shapes; this heuristic is its fallback.
+// Tuning knobs (they change only the launch shape, never the output bits):
+// TMCS_TILE_K caps the chunks per CTA, TMCS_THREADS fixes the CTA size,
+// TMCS_AUTOTUNE=0 disables timing.
+static bool shape_fits(const Program &P, const DeviceLimits &lim, int K) {
+    return kernel_smem_bytes(P.n_slots, P.max_window_segs, K) <= lim.smem_optin;
+}
+
+static LaunchShape make_shape(const Program &P, uint64_t n_cols, int K, int threads) {
     LaunchShape s;
-    int K = 16;
-    const int kcap = env_int("TMCS_TILE_K", 16);
-    while (K > 1 && K > kcap) K >>= 1;
-    while (K > 1 && size_t(P.n_slots) * 8 * K + tbytes > lim.smem_optin) K >>= 1;
-    while (K > 1 && (n_cols + K - 1) / K < uint64_t(2 * lim.sms)) K >>= 1;
     s.K = K;
-    s.smem = size_t(P.n_slots) * 8 * K + tbytes;
-    s.tiles = (n_cols + K - 1) / K;
-    const size_t per_sm = std::max<size_t>(1, lim.smem_per_sm / std::max<size_t>(s.smem + 1024, 1));
-    int threads = int(2048 / std::min<size_t>(per_sm, 8));
-    threads = std::max(128, std::min(1024, threads));
-    const int tforce = env_int("TMCS_THREADS", 0);
-    if (tforce >= 32 && tforce <= 1024 && tforce % 32 == 0) threads = tforce;
     s.threads = threads;
+    s.smem = kernel_smem_bytes(P.n_slots, P.max_window_segs, K);
+    s.tiles = (n_cols + K - 1) / K;
     return s;
+}
+
+static LaunchShape choose_shape(const Program &P, uint64_t n_cols, const DeviceLimits &lim) {
+    const int kcap = env_int("TMCS_TILE_K", 0);
+    int K = 16;
+    if (kcap > 0)
+        while (K > 1 && K > kcap) K >>= 1;
+    while (K > 1 && !shape_fits(P, lim, K)) K >>= 1;
+    if (kcap <= 0)
+        while (K > 1 && 2 * (kernel_smem_bytes(P.n_slots, P.max_window_segs, K) + 1024) > lim.smem_per_sm) K >>= 1;
+    while (K > 1 && (n_cols + K - 1) / K < uint64_t(2 * lim.sms)) K >>= 1;
+    int threads = 256;
+    const int tforce = env_int("TMCS_THREADS", 0);
+    if (tforce >= 32 && tforce <= 512 && tforce % 32 == 0) threads = tforce;
+    return make_shape(P, n_cols, K, threads);
 }
 
 template <int K>
@@ -358,6 +626,83 @@ static cudaError_t launch(const KernelArgs &a, const LaunchShape &s, cudaStream_
     }
 }
 
+// ---- per-device status word (library scratch, allocated on first use)
+
+static std::mutex g_status_mu;
+static std::map<int, uint32_t *> g_status;
+
+uint32_t *device_status_word(int device) {
+    std::lock_guard<std::mutex> lock(g_status_mu);
+    auto it = g_status.find(device);
+    if (it != g_status.end()) return it->second;
+    void *p = nullptr;
+    if (cudaMalloc(&p, 256) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaMemset(p, 0, 256) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p);
+        return nullptr;
+    }
+    g_status[device] = static_cast<uint32_t *>(p);
+    return static_cast<uint32_t *>(p);
+}
+
+// Times every feasible (K, threads) shape on the first columns of this call
+// (the real launch overwrites them) and records the fastest per chunk for the
+// circuit on this device. Synchronous; runs once per circuit and device.
+static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const DeviceLimits &lim, uint64_t n_cols,
+                    cudaStream_t st, LaunchShape *best) {
+    const Program &P = c->prog;
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    double best_per_chunk = 1e30;
+    LaunchShape chosen = *best;
+    for (int K = 1; K <= 16; K *= 2) {
+        if (!shape_fits(P, lim, K)) break;
+        const uint64_t cols = std::min<uint64_t>(n_cols, uint64_t(4) * lim.sms * K);
+        if (cols / K < uint64_t(lim.sms)) break;
+        for (int threads : {128, 256, 512}) {
+            LaunchShape s = make_shape(P, cols, K, threads);
+            KernelArgs t = a;
+            t.n_cols = cols;
+            t.last_mask = ~uint64_t(0);
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
+                if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+                if ((e = launch(t, s, st)) != cudaSuccess) break;
+                if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+                if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+                e = cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(e, "autotune launch");
+            }
+            const double per_chunk = double(ms) / double(cols);
+            if (per_chunk < best_per_chunk) {
+                best_per_chunk = per_chunk;
+                chosen = make_shape(P, n_cols, K, threads);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *best = chosen;
+    std::lock_guard<std::mutex> lock(c->mu);
+    DeviceProgram &mdp = c->dev[device];
+    mdp.tuned_K = chosen.K;
+    mdp.tuned_threads = chosen.threads;
+    return TMCS_OK;
+}
+
 static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
                         uint64_t *det, uint64_t *obs, void *stream) {
     if (!c) return fail(TMCS_E_INVALID, "circuit is NULL");
@@ -373,18 +718,29 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
     DeviceLimits lim;
     if ((rc = device_limits(&lim))) return rc;
     const Program &P = c->prog;
-    if (size_t(P.n_slots) * 8 > lim.smem_optin)
+    if (kernel_smem_bytes(P.n_slots, P.max_window_segs, 1) > lim.smem_optin)
         return fail(TMCS_E_INVALID, "circuit needs " + std::to_string(P.n_slots) +
                                         " frame slots; one 64-shot chunk does not fit in shared memory");
     if (P.layers.empty()) return TMCS_OK;
+    uint32_t *status = device_status_word(dp->device);
+    if (!status) return fail(TMCS_E_OOM, "cannot allocate the device status word");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     LaunchShape s = choose_shape(P, n_cols, lim);
+    const bool forced = env_int("TMCS_TILE_K", 0) > 0 || env_int("TMCS_THREADS", 0) > 0;
+    if (!forced) {
+        std::lock_guard<std::mutex> lock(c->mu);
+        DeviceProgram &mdp = c->dev[dp->device];
+        if (mdp.tuned_K) s = make_shape(P, n_cols, mdp.tuned_K, mdp.tuned_threads);
+    }
     KernelArgs a{};
     a.layers = dp->layers;
     a.args = dp->args;
     a.noise = dp->noise;
     a.tables = dp->tables;
+    a.status = status;
     a.n_layers = uint32_t(P.layers.size());
     a.n_slots = P.n_slots;
+    a.max_window_segs = P.max_window_segs;
     a.key0 = uint32_t(seed);
     a.key1 = uint32_t(seed >> 32);
     a.first_chunk = uint32_t(first_chunk);
@@ -392,7 +748,20 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
     a.last_mask = (shots % 64) ? ((uint64_t(1) << (shots % 64)) - 1) : ~uint64_t(0);
     a.det = det;
     a.obs = obs;
-    cudaError_t e = launch(a, s, static_cast<cudaStream_t>(stream));
+    if (!forced && env_int("TMCS_AUTOTUNE", 1) != 0) {
+        bool tuned;
+        {
+            std::lock_guard<std::mutex> lock(c->mu);
+            tuned = c->dev[dp->device].tuned_K != 0;
+        }
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cap);
+        if (!tuned && cap == cudaStreamCaptureStatusNone && n_cols >= uint64_t(16 * lim.sms)) {
+            int rc2 = autotune(c, dp->device, a, lim, n_cols, st, &s);
+            if (rc2) return rc2;
+        }
+    }
+    cudaError_t e = launch(a, s, st);
     if (e != cudaSuccess) return cuda_fail(e, "frame kernel launch");
     return TMCS_OK;
 }
@@ -411,6 +780,21 @@ int tmcs_sample(const tmcs_circuit *c, uint64_t shots, uint64_t seed, uint64_t *
 int tmcs_sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
                       uint64_t *detector_bits, uint64_t *observable_bits, void *stream) {
     return sample_range(c, first_chunk, shots, seed, detector_bits, observable_bits, stream);
+}
+
+int tmcs_check_device(void) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    uint32_t *w = device_status_word(dev);
+    if (!w) return fail(TMCS_E_OOM, "cannot allocate the device status word");
+    uint32_t v = 0;
+    if ((e = cudaMemcpy(&v, w, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e, "status read");
+    if (v) {
+        if ((e = cudaMemset(w, 0, 4)) != cudaSuccess) return cuda_fail(e, "status clear");
+        return fail(TMCS_E_TIMEOUT, "a kernel gave up waiting for a staged program block");
+    }
+    return TMCS_OK;
 }
 
 int tmcs_batch_sample(const tmcs_job *jobs, size_t n_jobs, void *stream) {

@@ -72,11 +72,12 @@ def lib() -> ctypes.CDLL:
         L.tmcs_sample_range.argtypes = [P, U64, U64, U64, P, P, P]
         L.tmcs_batch_sample.argtypes = [P, ctypes.c_size_t, P]
         L.tmcs_debug_gap_table.argtypes = [ctypes.c_double, P]
+        L.tmcs_check_device.argtypes = []
         L.tmcs_last_error.argtypes = []
         L.tmcs_last_error.restype = ctypes.c_char_p
         for f in ("tmcs_circuit_build", "tmcs_circuit_free", "tmcs_circuit_info", "tmcs_circuit_stats",
                   "tmcs_reference_sample", "tmcs_sample", "tmcs_sample_range", "tmcs_batch_sample",
-                  "tmcs_debug_gap_table"):
+                  "tmcs_debug_gap_table", "tmcs_check_device"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -142,6 +143,12 @@ def tmcs_reference_sample(handle: int) -> np.ndarray:
     buf = np.zeros(max((n + 7) // 8, 1), dtype=np.uint8)
     _check(lib().tmcs_reference_sample(ctypes.c_void_p(handle), buf.ctypes.data))
     return np.unpackbits(buf, bitorder="little")[:n]
+
+
+def tmcs_check_device() -> None:
+    """Raise TmcsError(TMCS_E_TIMEOUT) if a kernel on the current device gave
+    up on a bounded wait since the last check."""
+    _check(lib().tmcs_check_device())
 
 
 def tmcs_debug_gap_table(p: float) -> np.ndarray:

@@ -102,3 +102,15 @@ def test_rejects_invalid_ops(tmcs):
         tmcs.tmcs_circuit_build(c)
     with pytest.raises(tmcs.TmcsError):
         tmcs.tmcs_circuit_build(C.Circuit(), flags=0x80)
+
+
+@pytest.mark.parametrize("trial", range(40))
+def test_random_circuits_compile_and_validate(tmcs, trial):
+    """The compiler's output passes its own program check (slot, block and
+    window bounds the kernel relies on) for random circuits, pruned or not."""
+    from circuit_gen import random_noisy_circuit
+    rng = np.random.default_rng(300 + trial)
+    c = random_noisy_circuit(rng, int(rng.integers(2, 12)), int(rng.integers(4, 80)))
+    for flags in (0, tmcs.TMCS_FLAG_NO_PRUNE):
+        h = tmcs.tmcs_circuit_build(c, flags)
+        tmcs.tmcs_circuit_free(h)

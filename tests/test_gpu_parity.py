@@ -19,6 +19,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 from paper_2504_05611_gb300 import tmcs  # noqa: E402
+from circuit_gen import random_noisy_circuit  # noqa: E402
 
 
 def gpu_sample(circ, shots, seed, first_chunk=0, flags=0):
@@ -116,57 +117,6 @@ def test_noiseless_is_zero_and_certain_noise():
     assert not d[0].any() and (d[1][0] == np.uint64(2 ** 64 - 1)) and not o.any()
 
 
-def random_noisy_circuit(rng, n, depth):
-    """Random Clifford body + inverse on |0>/|+> inputs with noise sprinkled
-    in, a mid-circuit measurement feeding conditioned Paulis, and one detector
-    per (deterministic) final measurement."""
-    c = C.Circuit()
-    xb = [q for q in range(n) if rng.random() < 0.4]
-    zb = [q for q in range(n) if q not in xb]
-    if zb:
-        c.append("R", zb)
-    if xb:
-        c.append("RX", xb)
-    body = []
-    for _ in range(depth):
-        u = rng.integers(3)
-        if u == 0:
-            body.append(("H", [int(rng.integers(n))]))
-        elif u == 1:
-            body.append(("S", [int(rng.integers(n))]))
-        else:
-            a, b = rng.choice(n, 2, replace=False)
-            body.append(("CX", [int(a), int(b)]))
-    inv = []
-    for name, t in reversed(body):
-        inv += [("S", t)] * 3 if name == "S" else [(name, t)]
-    for i, (name, t) in enumerate(body + inv):
-        c.append(name, t)
-        if rng.random() < 0.3:
-            kind = ["X_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2"][int(rng.integers(4))]
-            if kind == "DEPOLARIZE2":
-                a, b = rng.choice(n, 2, replace=False)
-                c.append(kind, [int(a), int(b)], p=float(rng.uniform(0.01, 0.3)))
-            else:
-                qs = sorted(set(int(v) for v in rng.integers(0, n, 2)))
-                c.append(kind, qs, p=float(rng.uniform(0.01, 0.3)))
-    if zb:
-        anc = n
-        c.append("R", [anc])
-        c.append("CX", [zb[0], anc])
-        r = c.append("M", [anc])
-        c.append("XFEED", [int(r[0]), int(rng.integers(n))])
-        c.append("ZFEED", [int(r[0]), int(rng.integers(n))])
-    if zb:
-        c.append("M", zb)
-    if xb:
-        c.append("MX", xb)
-    for r in range(c.n_meas):
-        c.append("DETECTOR", [r])
-    c.append("OBSERVABLE", [c.n_meas - 1], arg=0)
-    return c
-
-
 @pytest.mark.parametrize("trial", range(12))
 def test_random_circuits(trial):
     rng = np.random.default_rng(900 + trial)
@@ -211,3 +161,29 @@ def test_headline_full_size_sampled_chunks():
     # every detector word has zero pad bits (shots is a multiple of 64 here)
     assert shots % 64 == 0
     s.close()
+
+
+def test_device_status_clean_after_sampling():
+    """No kernel gave up on a bounded wait during the runs above."""
+    tmcs.tmcs_check_device()
+
+
+@pytest.mark.parametrize("tile_k,threads", [(1, 128), (1, 256), (2, 256), (4, 512), (8, 256), (16, 512)])
+def test_every_launch_shape_is_bit_exact(monkeypatch, tile_k, threads):
+    """Tile shape (chunks per CTA, CTA size) changes only the schedule: every
+    forced shape reproduces the oracle, ragged tail included."""
+    monkeypatch.setenv("TMCS_TILE_K", str(tile_k))
+    monkeypatch.setenv("TMCS_THREADS", str(threads))
+    circ = C.teleport_circuit(C.code_by_name("sc5"), 2, 2, C.NoiseModel(0.01, 0.05))
+    assert_parity(circ, 64 * 53 + 17, seed=21)
+
+
+def test_autotuned_large_call_matches_forced_shape(monkeypatch):
+    """A call large enough to trigger the autotuner equals a forced-shape call."""
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc5"), 3, 3, C.NoiseModel(0.003, 0.03))
+    shots = 64 * 152 * 40 + 9
+    a = gpu_sample(circ, shots, 77)
+    monkeypatch.setenv("TMCS_TILE_K", "1")
+    monkeypatch.setenv("TMCS_THREADS", "128")
+    b = gpu_sample(circ, shots, 77)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
