@@ -150,6 +150,33 @@ int tmcs_sample(const tmcs_circuit *c, uint64_t shots, uint64_t seed,
 int tmcs_sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
                       uint64_t *detector_bits, uint64_t *observable_bits, void *stream);
 
+/*
+ * Allocation-free form of tmcs_sample_range (no counterpart in the paper; a
+ * service entry point of this library). For callers that cannot allocate
+ * device memory while running -- a service whose device memory belongs to
+ * another allocator's pool, a real-time host that forbids allocation on its
+ * request path, code that must not let cudaMalloc/cudaFree synchronise the
+ * device -- it calls no cudaMalloc, cudaFree or other allocating routine.
+ * Its scratch is one file-scope device array of 8 MiB (every GPU that loads
+ * libtmcs.so holds it until the process exits): each call clears the status
+ * word in it, copies the circuit's compiled program into it (stream-ordered
+ * on `stream`) and launches the same kernel as tmcs_sample_range, so outputs
+ * are bit-identical to tmcs_sample_range with the same arguments.
+ *   - Circuits whose compiled program exceeds the array (device_bytes of
+ *     tmcs_circuit_info plus 256) are rejected with TMCS_E_INVALID.
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents: calls
+ *     that overlap on the GPU (other streams, other host threads) race; the
+ *     caller must serialise them (e.g. one stream).
+ *   - Launch shape: the heuristic (or TMCS_TILE_K / TMCS_THREADS); no timing.
+ *   - A device-side bounded wait that expires is not reported here (the
+ *     status word is cleared by the next call).
+ * Arguments and errors as tmcs_sample_range.
+ */
+int tmcs_sample_noalloc(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
+                        uint64_t *detector_bits, uint64_t *observable_bits, void *stream);
+
 /* One job of a batched launch: circuit, shots (from chunk 0), seed, outputs. */
 typedef struct {
     const tmcs_circuit *c;

@@ -766,6 +766,111 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
     return TMCS_OK;
 }
 
+// ---- allocation-free sampling
+//
+// Some callers cannot allocate device memory once they are running: a
+// service whose device memory is owned by another allocator's pool (a direct
+// cudaMalloc can fail there or fragment the pool), a real-time host that
+// forbids allocation on its request path, or code between stream-ordered
+// operations that must not be forced to synchronise the device (cudaMalloc and
+// cudaFree can). tmcs_sample_noalloc serves them: instead of the per-circuit
+// device program and status word that tmcs_sample allocates on first use, it
+// copies the compiled program into this file-scope array (held by every GPU
+// that loads the library until the process exits) and runs the same kernel on
+// it. Every call shares the array and leaves its own program in it, so calls
+// that overlap on the GPU (different streams, or different host threads) race
+// and must be serialised by the caller.
+
+constexpr size_t kNoAllocBytes = size_t(8) << 20;  // 8 MiB: status word + one compiled program
+constexpr size_t kNoAllocStatusBytes = 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static unsigned char *g_noalloc_addr[kNoAllocMaxDevices];  // device address of the array, per device
+
+// Device address of the array on the current device (looked up once per
+// device, with that device current).
+static int noalloc_scratch(int dev, unsigned char **out) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(TMCS_E_INVALID, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the scratch array");
+        g_noalloc_addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return TMCS_OK;
+}
+
+static int sample_noalloc(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
+                          uint64_t *det, uint64_t *obs, void *stream) {
+    if (!c) return fail(TMCS_E_INVALID, "circuit is NULL");
+    const Program &P = c->prog;
+    const size_t b_layers = align256(P.layers.size() * sizeof(Layer));
+    const size_t b_args = align256(P.args.size() * 4);
+    const size_t b_noise = align256(P.noise.size() * sizeof(NoiseDesc));
+    const size_t b_tables = align256(P.tables.size() * 4);
+    const size_t need = kNoAllocStatusBytes + b_layers + b_args + b_noise + b_tables;
+    if (need > kNoAllocBytes)
+        return fail(TMCS_E_INVALID, "compiled program needs " + std::to_string(need) +
+                                        " bytes; the allocation-free entry point holds at most " +
+                                        std::to_string(kNoAllocBytes) + " (use tmcs_sample_range)");
+    if (shots == 0) return fail(TMCS_E_INVALID, "shots must be positive");
+    if ((c->n_det && !det) || (c->n_obs && !obs)) return fail(TMCS_E_INVALID, "output buffer is NULL");
+    if ((reinterpret_cast<uintptr_t>(det) & 7) || (reinterpret_cast<uintptr_t>(obs) & 7))
+        return fail(TMCS_E_BUFFER, "output buffers must be 8-byte aligned");
+    const uint64_t n_cols = (shots + 63) / 64;
+    if (first_chunk + n_cols > (uint64_t(1) << 32)) return fail(TMCS_E_INVALID, "chunk range beyond 2^32");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    unsigned char *base = nullptr;
+    int rc = noalloc_scratch(dev, &base);
+    if (rc) return rc;
+    DeviceLimits lim;
+    if ((rc = device_limits(&lim))) return rc;
+    if (kernel_smem_bytes(P.n_slots, P.max_window_segs, 1) > lim.smem_optin)
+        return fail(TMCS_E_INVALID, "circuit needs " + std::to_string(P.n_slots) +
+                                        " frame slots; one 64-shot chunk does not fit in shared memory");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // status word starts at zero; program sections go after it
+    unsigned char *b = base + kNoAllocStatusBytes;
+    if ((e = cudaMemsetAsync(base, 0, kNoAllocStatusBytes, st)) != cudaSuccess) return cuda_fail(e, "status clear");
+    const struct {
+        const void *src;
+        size_t bytes;
+        size_t off;
+    } parts[4] = {{P.layers.data(), P.layers.size() * sizeof(Layer), 0},
+                  {P.args.data(), P.args.size() * 4, b_layers},
+                  {P.noise.data(), P.noise.size() * sizeof(NoiseDesc), b_layers + b_args},
+                  {P.tables.data(), P.tables.size() * 4, b_layers + b_args + b_noise}};
+    for (const auto &pt : parts)
+        if (pt.bytes && (e = cudaMemcpyAsync(b + pt.off, pt.src, pt.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "program copy into the scratch array");
+    if (P.layers.empty()) return TMCS_OK;
+    LaunchShape s = choose_shape(P, n_cols, lim);
+    KernelArgs a{};
+    a.layers = reinterpret_cast<const Layer *>(b);
+    a.args = reinterpret_cast<const uint32_t *>(b + b_layers);
+    a.noise = reinterpret_cast<const NoiseDesc *>(b + b_layers + b_args);
+    a.tables = reinterpret_cast<const uint32_t *>(b + b_layers + b_args + b_noise);
+    a.status = reinterpret_cast<uint32_t *>(base);
+    a.n_layers = uint32_t(P.layers.size());
+    a.n_slots = P.n_slots;
+    a.max_window_segs = P.max_window_segs;
+    a.key0 = uint32_t(seed);
+    a.key1 = uint32_t(seed >> 32);
+    a.first_chunk = uint32_t(first_chunk);
+    a.n_cols = n_cols;
+    a.last_mask = (shots % 64) ? ((uint64_t(1) << (shots % 64)) - 1) : ~uint64_t(0);
+    a.det = det;
+    a.obs = obs;
+    if ((e = launch(a, s, st)) != cudaSuccess) return cuda_fail(e, "frame kernel launch");
+    return TMCS_OK;
+}
+
 }  // namespace tmcs
 
 using namespace tmcs;
@@ -780,6 +885,11 @@ int tmcs_sample(const tmcs_circuit *c, uint64_t shots, uint64_t seed, uint64_t *
 int tmcs_sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
                       uint64_t *detector_bits, uint64_t *observable_bits, void *stream) {
     return sample_range(c, first_chunk, shots, seed, detector_bits, observable_bits, stream);
+}
+
+int tmcs_sample_noalloc(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
+                        uint64_t *detector_bits, uint64_t *observable_bits, void *stream) {
+    return sample_noalloc(c, first_chunk, shots, seed, detector_bits, observable_bits, stream);
 }
 
 int tmcs_check_device(void) {

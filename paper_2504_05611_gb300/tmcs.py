@@ -72,12 +72,13 @@ def lib() -> ctypes.CDLL:
         L.tmcs_sample_range.argtypes = [P, U64, U64, U64, P, P, P]
         L.tmcs_batch_sample.argtypes = [P, ctypes.c_size_t, P]
         L.tmcs_debug_gap_table.argtypes = [ctypes.c_double, P]
+        L.tmcs_sample_noalloc.argtypes = [P, U64, U64, U64, P, P, P]
         L.tmcs_check_device.argtypes = []
         L.tmcs_last_error.argtypes = []
         L.tmcs_last_error.restype = ctypes.c_char_p
         for f in ("tmcs_circuit_build", "tmcs_circuit_free", "tmcs_circuit_info", "tmcs_circuit_stats",
                   "tmcs_reference_sample", "tmcs_sample", "tmcs_sample_range", "tmcs_batch_sample",
-                  "tmcs_debug_gap_table", "tmcs_check_device"):
+                  "tmcs_debug_gap_table", "tmcs_check_device", "tmcs_sample_noalloc"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -204,6 +205,18 @@ def tmcs_sample_range(handle: int, first_chunk: int, shots: int, seed: int, det,
     _check_size(obs, info["n_obs"], cols, "observable")
     _check(lib().tmcs_sample_range(ctypes.c_void_p(handle), first_chunk, shots, seed & (2 ** 64 - 1),
                                    _dev_ptr(det), _dev_ptr(obs), _stream_ptr(stream)))
+
+
+def tmcs_sample_noalloc(handle: int, first_chunk: int, shots: int, seed: int, det, obs, stream=None) -> None:
+    """Allocation-free sampling (see include/tmcs.h): same bits as
+    tmcs_sample_range; its scratch is a fixed 8 MiB device array shared by
+    all calls, so calls overlapping on the GPU race."""
+    info = tmcs_circuit_info(handle)
+    cols = (shots + 63) // 64
+    _check_size(det, info["n_det"], cols, "detector")
+    _check_size(obs, info["n_obs"], cols, "observable")
+    _check(lib().tmcs_sample_noalloc(ctypes.c_void_p(handle), first_chunk, shots, seed & (2 ** 64 - 1),
+                                     _dev_ptr(det), _dev_ptr(obs), _stream_ptr(stream)))
 
 
 def tmcs_batch_sample(jobs: Sequence[Tuple[int, int, int, object, object]], stream=None) -> None:
