@@ -96,9 +96,11 @@ struct IRParity {
 static int validate_program(const Program &P, uint64_t n_det, uint64_t n_obs) {
     auto bad = [](const std::string &m) { return fail(TMCS_E_INVALID, "internal: program check failed: " + m); };
     if (P.args.size() % 4) return bad("args not padded");
+    uint32_t staged = 0;
     for (size_t l = 0; l < P.layers.size(); l++) {
         const Layer &ly = P.layers[l];
         const std::string at = "layer " + std::to_string(l);
+        if (ly.nwords && ly.seq != staged++) return bad(at + ": staged sequence number");
         if (ly.nwords) {
             if (ly.off % 4 || ly.nwords % 4 || ly.nwords > kStageWords || size_t(ly.off) + ly.nwords > P.args.size())
                 return bad(at + ": staged block misaligned or out of range");
@@ -645,6 +647,10 @@ int compile(tmcs_circuit *c, uint32_t flags) {
         emit_words(L_OBSOUT, w, false);
     }
     pad4();
+    {
+        uint32_t q = 0;
+        for (Layer &ly : P.layers) ly.seq = ly.nwords ? q++ : 0u;
+    }
     P.n_slots = n_slots;
     P.n_det = c->n_det;
     P.n_obs = c->n_obs;

@@ -48,7 +48,8 @@ struct Layer {
     uint32_t nwords;
     uint32_t aux;
     uint32_t aux2;
-    uint32_t pad0, pad1;
+    uint32_t seq;   // index of this layer among the staged layers (nwords > 0)
+    uint32_t pad1;
 };
 
 constexpr uint32_t kStageWords = 2048;  // 8 KB per staging buffer (two buffers)
@@ -100,7 +101,10 @@ struct DeviceProgram {
     const uint32_t *args = nullptr;
     const NoiseDesc *noise = nullptr;
     const uint32_t *tables = nullptr;
-    int tuned_K = 0;        // launch shape chosen by the autotuner (0: not tuned)
+    int tuned_mode = 0;     // launch shape chosen by the autotuner (0: not tuned)
+    int tuned_K = 0;
+    int tuned_warps = 0;
+    int tuned_group = 0;
     int tuned_threads = 0;
 };
 

@@ -75,6 +75,7 @@ struct KernelArgs {
     uint32_t n_layers;
     uint32_t n_slots;
     uint32_t max_window_segs;  // event buffer holds max_window_segs * K units
+    uint32_t group_warps;      // frame_kernel_w: warps per chunk group
     uint32_t key0, key1;
     uint32_t first_chunk;  // global chunk of output column 0
     uint64_t n_cols;       // output columns (chunks) of this call
@@ -95,7 +96,7 @@ struct EvUnit {
 };
 static_assert(sizeof(EvUnit) == 24, "EvUnit layout");
 
-constexpr uint32_t kSpinLimit = 1u << 20;  // bounded mbarrier waits
+constexpr uint64_t kWaitNs = 2000000000ull;  // bounded mbarrier waits: 2 s of wall time
 
 // ---- PTX wrappers: mbarrier + bulk asynchronous copy (TMA, 1-D)
 
@@ -133,11 +134,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Waits for phase `parity` of `bar`; gives up after kSpinLimit polls.
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for phase `parity` of `bar`; gives up after kWaitNs of wall time.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kSpinLimit; it++)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer_ns() - t0 > kWaitNs) return false;
+    return true;
 }
 __device__ __forceinline__ void prefetch_l1(const void *p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
@@ -460,6 +468,273 @@ __global__ void __launch_bounds__(512) frame_kernel(const KernelArgs P) {
     run_tile<K>(P, F, stage0, stage1, evbuf, bars, abort_flag, uint64_t(blockIdx.x) * K);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-owned chunks (frame_kernel_w). Frame updates of different 64-shot
+// chunks never interact, so each consumer warp owns KW chunks outright and
+// runs the whole program on them, synchronising only within the warp. Warp 0
+// is a producer: one lane streams every staged layer's argument block into a
+// ring of kRing shared-memory stages with bulk asynchronous copies; a "full"
+// mbarrier per stage completes when the bytes land, an "empty" mbarrier when
+// every active consumer warp has finished with it. Consumers therefore drift
+// apart by up to kRing staged layers instead of meeting at a CTA barrier after
+// every layer, and a warp busy in a long noise walk does not stall the others.
+
+constexpr uint32_t kRing = 4;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__host__ __device__ constexpr size_t ring_region_bytes() {
+    return (size_t(kRing) * kStageWords * 4 + 2 * kRing * 8 + 16 + 127) & ~size_t(127);
+}
+
+__device__ __forceinline__ void group_sync(uint32_t bar_id, uint32_t nthreads) {
+    if (nthreads == 32)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthreads) : "memory");
+}
+
+// One chunk group: GT threads (GT/32 warps) run the program on the group's
+// KW chunks; gtid is the thread's index in the group, bar_id its named
+// barrier (1..15; a single-warp group uses __syncwarp).
+template <int KW>
+__device__ __forceinline__ void consumer_group(const KernelArgs &P, uint64_t *Fw, EvUnit *evbuf, const uint32_t *ring,
+                                               uint64_t *full, uint64_t *empty, int *abort_flag, uint64_t col0,
+                                               int nvalid, uint32_t gtid, uint32_t GT, uint32_t bar_id) {
+    const uint32_t chunk0 = P.first_chunk + uint32_t(col0);
+    Layer cur = P.layers[0];
+    for (uint32_t L = 0; L < P.n_layers; L++) {
+        const Layer nxt = (L + 1 < P.n_layers) ? P.layers[L + 1] : cur;
+        const uint32_t *st = nullptr;
+        uint32_t b = 0;
+        if (cur.nwords) {
+            b = cur.seq % kRing;
+            if (!mbar_wait_bounded(&full[b], (cur.seq / kRing) & 1u)) {
+                *reinterpret_cast<volatile int *>(abort_flag) = 1;
+                if (gtid == 0) atomicOr(P.status, 1u);
+                return;
+            }
+            st = ring + size_t(b) * kStageWords;
+        }
+        switch (cur.kind) {
+        case L_ZERO:
+            for (uint32_t i = gtid; i < cur.count; i += GT) {
+                uint64_t *d = Fw + st[i] * KW;
+#pragma unroll
+                for (int k = 0; k < KW; k++) d[k] = 0ull;
+            }
+            break;
+        case L_XOR:
+        case L_COPY: {
+            constexpr int U = 8;
+            const bool is_xor = cur.kind == L_XOR;
+            for (uint32_t i0 = gtid; i0 < cur.count; i0 += GT * U) {
+                uint32_t w[U];
+#pragma unroll
+                for (int r = 0; r < U; r++) {
+                    const uint32_t i = i0 + GT * r;
+                    w[r] = i < cur.count ? st[i] : 0xFFFFFFFFu;
+                }
+                uint64_t a[U][KW], bb[U][KW];
+#pragma unroll
+                for (int r = 0; r < U; r++)
+                    if (w[r] != 0xFFFFFFFFu) {
+#pragma unroll
+                        for (int k = 0; k < KW; k++) {
+                            bb[r][k] = Fw[(w[r] >> 16) * KW + k];
+                            if (is_xor) a[r][k] = Fw[(w[r] & 0xFFFFu) * KW + k];
+                        }
+                    }
+#pragma unroll
+                for (int r = 0; r < U; r++)
+                    if (w[r] != 0xFFFFFFFFu) {
+#pragma unroll
+                        for (int k = 0; k < KW; k++)
+                            Fw[(w[r] & 0xFFFFu) * KW + k] = is_xor ? (a[r][k] ^ bb[r][k]) : bb[r][k];
+                    }
+            }
+            break;
+        }
+        case L_NGEN: {
+            // walk the event streams of a window of upcoming noise ops into
+            // the group's event buffer (one thread per (segment, chunk))
+            const uint32_t units = cur.aux2 * KW;
+            for (uint32_t u = gtid; u < units; u += GT) {
+                const uint32_t ws = u / KW;
+                const int k = int(u % KW);
+                uint32_t di = cur.aux, base = 0;
+                uint32_t nseg = P.noise[di].n_seg;
+                while (ws >= base + nseg) {
+                    base += nseg;
+                    nseg = P.noise[++di].n_seg;
+                }
+                EvUnit *E = evbuf + u;
+                if (k >= nvalid) {
+                    E->n = 0;
+                    E->cont_d = 0xFFFFu;
+                    continue;
+                }
+                const NoiseDesc nd = P.noise[di];
+                const uint32_t *Tt = P.tables + size_t(nd.table) * kTableWords;
+                const float inv = __uint_as_float(__ldg(Tt + kGapLen));
+                walk_segment<KW>(nd, Tt, inv, ws - base, chunk0 + uint32_t(k), P.key0, P.key1, 0u, -1, E,
+                                 nullptr, P.args + nd.tgt_off, k);
+            }
+            break;
+        }
+        case L_NAPPLY: {
+            // apply the buffered events of one op (one thread per event slot);
+            // a walk that overflowed its buffer resumes here
+            const NoiseDesc nd = P.noise[cur.aux];
+            const uint32_t *tg = P.args + nd.tgt_off;
+            const uint32_t items = nd.n_seg * KW * kEvCap;
+            for (uint32_t i = gtid; i < items; i += GT) {
+                const uint32_t uu = i / kEvCap, e = i % kEvCap;
+                const uint32_t sg = uu / KW;
+                const int k = int(uu % KW);
+                if (k >= nvalid) continue;
+                const EvUnit *E = evbuf + (cur.aux2 + sg) * KW + uint32_t(k);
+                if (e < E->n) {
+                    const uint32_t v = E->ev[e];
+                    apply_event<KW>(Fw, tg, nd.kind, sg, int(v & 0xFFFu), v >> 12, k);
+                }
+                if (e == 0 && E->cont_d != 0xFFFFu) {
+                    const uint32_t *Tt = P.tables + size_t(nd.table) * kTableWords;
+                    const float inv = __uint_as_float(__ldg(Tt + kGapLen));
+                    walk_segment<KW>(nd, Tt, inv, sg, chunk0 + uint32_t(k), P.key0, P.key1, E->cont_d,
+                                     E->cont_pos, nullptr, Fw, tg, k);
+                }
+            }
+            break;
+        }
+        case L_DET:
+            for (uint32_t d = gtid; d < cur.count; d += GT) {
+                const uint32_t lo = st[d], hi = st[d + 1];
+                uint64_t v[KW];
+#pragma unroll
+                for (int k = 0; k < KW; k++) v[k] = 0ull;
+                for (uint32_t t = lo; t < hi; t++) {
+                    const uint64_t *x = Fw + st[t] * KW;
+#pragma unroll
+                    for (int k = 0; k < KW; k++) v[k] ^= x[k];
+                }
+                uint64_t *out = P.det + uint64_t(cur.aux + d) * P.n_cols + col0;
+#pragma unroll
+                for (int k = 0; k < KW; k++)
+                    if (k < nvalid) out[k] = (col0 + uint64_t(k) == P.n_cols - 1) ? (v[k] & P.last_mask) : v[k];
+            }
+            break;
+        case L_OBS:
+            for (uint32_t d = gtid; d < cur.count; d += GT) {
+                const uint32_t lo = st[d], hi = st[d + 1];
+                uint64_t v[KW];
+#pragma unroll
+                for (int k = 0; k < KW; k++) v[k] = 0ull;
+                for (uint32_t t = lo + 1; t < hi; t++) {
+                    const uint64_t *x = Fw + st[t] * KW;
+#pragma unroll
+                    for (int k = 0; k < KW; k++) v[k] ^= x[k];
+                }
+                uint64_t *acc = Fw + st[lo] * KW;
+#pragma unroll
+                for (int k = 0; k < KW; k++) acc[k] ^= v[k];
+            }
+            break;
+        case L_OBSOUT:
+            for (uint32_t o = gtid; o < cur.count; o += GT) {
+                const uint64_t *acc = Fw + st[o] * KW;
+                uint64_t *out = P.obs + uint64_t(o) * P.n_cols + col0;
+#pragma unroll
+                for (int k = 0; k < KW; k++)
+                    if (k < nvalid) out[k] = (col0 + uint64_t(k) == P.n_cols - 1) ? (acc[k] & P.last_mask) : acc[k];
+            }
+            break;
+        default:
+            break;
+        }
+        group_sync(bar_id, GT);
+        if (cur.nwords && gtid == 0) mbar_arrive(&empty[b]);
+        if (*reinterpret_cast<volatile int *>(abort_flag)) return;
+        cur = nxt;
+    }
+}
+
+__device__ __forceinline__ void producer_lane(const KernelArgs &P, uint32_t *ring, uint64_t *full, uint64_t *empty,
+                                              int *abort_flag) {
+    uint32_t q = 0;
+    bool aborted = false;
+    for (uint32_t L = 0; L < P.n_layers; L++) {
+        const Layer ly = P.layers[L];
+        if (!ly.nwords) continue;
+        const uint32_t b = q % kRing, r = q / kRing;
+        if (r >= 1 && !mbar_wait_bounded(&empty[b], (r - 1) & 1u)) {
+            aborted = true;
+            break;
+        }
+        if (*reinterpret_cast<volatile int *>(abort_flag)) {
+            aborted = true;
+            break;
+        }
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[b], ly.nwords * 4u);
+        bulk_copy_g2s(ring + size_t(b) * kStageWords, P.args + ly.off, ly.nwords * 4u, &full[b]);
+        q++;
+    }
+    if (aborted) {
+        *reinterpret_cast<volatile int *>(abort_flag) = 1;
+        // wait (bounded) for the copies still in flight before leaving
+        for (uint32_t j = q > kRing ? q - kRing : 0; j < q; j++) mbar_wait_bounded(&full[j % kRing], (j / kRing) & 1u);
+        atomicOr(P.status, 1u);
+    }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(544) frame_kernel_w(const KernelArgs P) {
+    extern __shared__ __align__(128) uint64_t smem[];
+    uint32_t *ring = reinterpret_cast<uint32_t *>(smem);
+    uint64_t *full = reinterpret_cast<uint64_t *>(ring + size_t(kRing) * kStageWords);
+    uint64_t *empty = full + kRing;
+    int *abort_flag = reinterpret_cast<int *>(empty + kRing);
+    uint64_t *F = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(smem) + ring_region_bytes());
+    const uint32_t warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t G = P.group_warps;                // warps per chunk group
+    const uint32_t W = (blockDim.x / 32 - 1) / G;    // chunk groups
+    const uint64_t tile0 = uint64_t(blockIdx.x) * W * KW;
+    const uint64_t left = P.n_cols - tile0;
+    const uint64_t need = (left + KW - 1) / KW;
+    const uint32_t active = need < uint64_t(W) ? uint32_t(need) : W;
+    if (threadIdx.x == 0) {
+        for (uint32_t i = 0; i < kRing; i++) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], active);
+        }
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        if (lane == 0) producer_lane(P, ring, full, empty, abort_flag);
+        return;
+    }
+    const uint32_t g = (warp - 1) / G;
+    if (g >= active) return;
+    const uint64_t col0 = tile0 + uint64_t(g) * KW;
+    const uint64_t rem = P.n_cols - col0;
+    const int nvalid = rem < uint64_t(KW) ? int(rem) : KW;
+    // event buffers follow the frames of all W groups
+    EvUnit *ev = reinterpret_cast<EvUnit *>(F + size_t(W) * P.n_slots * KW) + size_t(g) * P.max_window_segs * KW;
+    consumer_group<KW>(P, F + size_t(g) * P.n_slots * KW, ev, ring, full, empty, abort_flag, col0, nvalid,
+                       ((warp - 1) % G) * 32 + lane, 32 * G, 1 + g);
+}
+
+// Dynamic shared memory of frame_kernel_w<KW> with W chunk groups: ring,
+// then every group's frames, then every group's event buffer.
+static size_t kernel_w_smem_bytes(uint32_t n_slots, uint32_t max_window_segs, int KW, int W) {
+    return ring_region_bytes() + size_t(W) * n_slots * KW * 8 + size_t(W) * max_window_segs * KW * sizeof(EvUnit);
+}
+
 // Dynamic shared memory of frame_kernel<K>.
 static size_t kernel_smem_bytes(uint32_t n_slots, uint32_t max_window_segs, int K) {
     size_t b = (size_t(n_slots) * K * 8 + 127) & ~size_t(127);
@@ -560,7 +835,10 @@ static int device_limits(DeviceLimits *lim) {
 }
 
 struct LaunchShape {
-    int K = 1;
+    int mode = 3;      // 3: CTA-wide layers (frame_kernel), 4: warp-owned chunks (frame_kernel_w)
+    int K = 1;         // chunks per CTA (mode 3) or per consumer warp (mode 4)
+    int warps = 0;     // chunk groups (mode 4)
+    int group = 1;     // warps per chunk group (mode 4)
     int threads = 256;
     size_t smem = 0;
     uint64_t tiles = 0;
@@ -586,6 +864,7 @@ static bool shape_fits(const Program &P, const DeviceLimits &lim, int K) {
 
 static LaunchShape make_shape(const Program &P, uint64_t n_cols, int K, int threads) {
     LaunchShape s;
+    s.mode = 3;
     s.K = K;
     s.threads = threads;
     s.smem = kernel_smem_bytes(P.n_slots, P.max_window_segs, K);
@@ -593,8 +872,39 @@ static LaunchShape make_shape(const Program &P, uint64_t n_cols, int K, int thre
     return s;
 }
 
+// Largest chunk-group count (<= 15: one named barrier each) whose frames
+// fit next to the ring, with at most 16 consumer warps.
+static int max_groups_w(const Program &P, const DeviceLimits &lim, int KW, int G) {
+    int W = std::min(15, 16 / G);
+    while (W > 0 && kernel_w_smem_bytes(P.n_slots, P.max_window_segs, KW, W) > lim.smem_optin) W--;
+    return W;
+}
+
+static LaunchShape make_shape_w(const Program &P, uint64_t n_cols, int KW, int W, int G) {
+    LaunchShape s;
+    s.mode = 4;
+    s.K = KW;
+    s.warps = W;
+    s.group = G;
+    s.threads = 32 * (W * G + 1);
+    s.smem = kernel_w_smem_bytes(P.n_slots, P.max_window_segs, KW, W);
+    s.tiles = (n_cols + uint64_t(W) * KW - 1) / (uint64_t(W) * KW);
+    return s;
+}
+
 static LaunchShape choose_shape(const Program &P, uint64_t n_cols, const DeviceLimits &lim) {
+    const int mode = env_int("TMCS_KERNEL", 0);
     const int kcap = env_int("TMCS_TILE_K", 0);
+    if (mode == 4) {
+        const int KW = kcap >= 2 ? 2 : 1;
+        int G = env_int("TMCS_GROUP", 1);
+        G = (G == 2 || G == 4 || G == 8) ? G : 1;
+        int W = max_groups_w(P, lim, KW, G);
+        const int wforce = env_int("TMCS_WARPS", 0);
+        if (wforce > 0 && wforce < W) W = wforce;
+        if (W >= 1) return make_shape_w(P, n_cols, KW, W, G);
+        // frames of even one group do not fit next to the ring: use mode 3
+    }
     int K = 16;
     if (kcap > 0)
         while (K > 1 && K > kcap) K >>= 1;
@@ -616,7 +926,18 @@ static cudaError_t launch_k(const KernelArgs &a, const LaunchShape &s, cudaStrea
     return cudaGetLastError();
 }
 
-static cudaError_t launch(const KernelArgs &a, const LaunchShape &s, cudaStream_t st) {
+template <int KW>
+static cudaError_t launch_w(const KernelArgs &a, const LaunchShape &s, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(frame_kernel_w<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem));
+    if (e != cudaSuccess) return e;
+    frame_kernel_w<KW><<<unsigned(s.tiles), s.threads, s.smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream_t st) {
+    KernelArgs a = a0;
+    a.group_warps = uint32_t(s.group);
+    if (s.mode == 4) return s.K == 2 ? launch_w<2>(a, s, st) : launch_w<1>(a, s, st);
     switch (s.K) {
     case 16: return launch_k<16>(a, s, st);
     case 8: return launch_k<8>(a, s, st);
@@ -649,12 +970,25 @@ uint32_t *device_status_word(int device) {
     return static_cast<uint32_t *>(p);
 }
 
-// Times every feasible (K, threads) shape on the first columns of this call
-// (the real launch overwrites them) and records the fastest per chunk for the
-// circuit on this device. Synchronous; runs once per circuit and device.
+// Times every feasible launch shape of both kernels on the first columns of
+// this call (the real launch overwrites them) and records the fastest per
+// chunk for the circuit on this device. Synchronous; runs once per circuit
+// and device.
 static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const DeviceLimits &lim, uint64_t n_cols,
                     cudaStream_t st, LaunchShape *best) {
     const Program &P = c->prog;
+    std::vector<LaunchShape> cands;
+    for (int K = 1; K <= 16; K *= 2) {
+        if (!shape_fits(P, lim, K)) break;
+        for (int threads : {128, 256, 512}) cands.push_back(make_shape(P, n_cols, K, threads));
+    }
+    for (int KW = 1; KW <= 2; KW++)
+        for (int G : {1, 2, 4}) {
+            const int Wmax = max_groups_w(P, lim, KW, G);
+            if (Wmax >= 1) cands.push_back(make_shape_w(P, n_cols, KW, Wmax, G));
+            if ((Wmax + 1) / 2 >= 1 && (Wmax + 1) / 2 < Wmax)
+                cands.push_back(make_shape_w(P, n_cols, KW, (Wmax + 1) / 2, G));
+        }
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
@@ -664,33 +998,32 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
     }
     double best_per_chunk = 1e30;
     LaunchShape chosen = *best;
-    for (int K = 1; K <= 16; K *= 2) {
-        if (!shape_fits(P, lim, K)) break;
-        const uint64_t cols = std::min<uint64_t>(n_cols, uint64_t(4) * lim.sms * K);
-        if (cols / K < uint64_t(lim.sms)) break;
-        for (int threads : {128, 256, 512}) {
-            LaunchShape s = make_shape(P, cols, K, threads);
-            KernelArgs t = a;
-            t.n_cols = cols;
-            t.last_mask = ~uint64_t(0);
-            float ms = 0.f;
-            for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
-                if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
-                if ((e = launch(t, s, st)) != cudaSuccess) break;
-                if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
-                if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-                e = cudaEventElapsedTime(&ms, e0, e1);
-            }
-            if (e != cudaSuccess) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return cuda_fail(e, "autotune launch");
-            }
-            const double per_chunk = double(ms) / double(cols);
-            if (per_chunk < best_per_chunk) {
-                best_per_chunk = per_chunk;
-                chosen = make_shape(P, n_cols, K, threads);
-            }
+    for (const LaunchShape &full : cands) {
+        const uint64_t per_tile = full.mode == 4 ? uint64_t(full.warps) * full.K : uint64_t(full.K);
+        const uint64_t cols = std::min<uint64_t>(n_cols, uint64_t(4) * lim.sms * per_tile);
+        if (cols / per_tile < uint64_t(lim.sms)) continue;
+        LaunchShape s = full;
+        s.tiles = (cols + per_tile - 1) / per_tile;
+        KernelArgs t = a;
+        t.n_cols = cols;
+        t.last_mask = ~uint64_t(0);
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
+            if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+            if ((e = launch(t, s, st)) != cudaSuccess) break;
+            if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            e = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(e, "autotune launch");
+        }
+        const double per_chunk = double(ms) / double(cols);
+        if (per_chunk < best_per_chunk) {
+            best_per_chunk = per_chunk;
+            chosen = full;
         }
     }
     cudaEventDestroy(e0);
@@ -698,7 +1031,10 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
     *best = chosen;
     std::lock_guard<std::mutex> lock(c->mu);
     DeviceProgram &mdp = c->dev[device];
+    mdp.tuned_mode = chosen.mode;
     mdp.tuned_K = chosen.K;
+    mdp.tuned_warps = chosen.warps;
+    mdp.tuned_group = chosen.group;
     mdp.tuned_threads = chosen.threads;
     return TMCS_OK;
 }
@@ -726,11 +1062,14 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
     if (!status) return fail(TMCS_E_OOM, "cannot allocate the device status word");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     LaunchShape s = choose_shape(P, n_cols, lim);
-    const bool forced = env_int("TMCS_TILE_K", 0) > 0 || env_int("TMCS_THREADS", 0) > 0;
+    const bool forced = env_int("TMCS_TILE_K", 0) > 0 || env_int("TMCS_THREADS", 0) > 0 ||
+                        env_int("TMCS_KERNEL", 0) > 0 || env_int("TMCS_WARPS", 0) > 0 ||
+                        env_int("TMCS_GROUP", 0) > 0;
     if (!forced) {
         std::lock_guard<std::mutex> lock(c->mu);
         DeviceProgram &mdp = c->dev[dp->device];
-        if (mdp.tuned_K) s = make_shape(P, n_cols, mdp.tuned_K, mdp.tuned_threads);
+        if (mdp.tuned_mode == 3) s = make_shape(P, n_cols, mdp.tuned_K, mdp.tuned_threads);
+        if (mdp.tuned_mode == 4) s = make_shape_w(P, n_cols, mdp.tuned_K, mdp.tuned_warps, mdp.tuned_group);
     }
     KernelArgs a{};
     a.layers = dp->layers;
@@ -752,7 +1091,7 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
         bool tuned;
         {
             std::lock_guard<std::mutex> lock(c->mu);
-            tuned = c->dev[dp->device].tuned_K != 0;
+            tuned = c->dev[dp->device].tuned_mode != 0;
         }
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         cudaStreamIsCapturing(st, &cap);

@@ -168,12 +168,22 @@ def test_device_status_clean_after_sampling():
     tmcs.tmcs_check_device()
 
 
-@pytest.mark.parametrize("tile_k,threads", [(1, 128), (1, 256), (2, 256), (4, 512), (8, 256), (16, 512)])
-def test_every_launch_shape_is_bit_exact(monkeypatch, tile_k, threads):
-    """Tile shape (chunks per CTA, CTA size) changes only the schedule: every
-    forced shape reproduces the oracle, ragged tail included."""
+@pytest.mark.parametrize("kernel,tile_k,threads,warps,group", [
+    (3, 1, 128, 0, 0), (3, 1, 256, 0, 0), (3, 2, 256, 0, 0), (3, 4, 512, 0, 0), (3, 8, 256, 0, 0),
+    (3, 16, 512, 0, 0), (4, 1, 0, 1, 1), (4, 1, 0, 5, 1), (4, 1, 0, 15, 1), (4, 2, 0, 3, 1), (4, 2, 0, 15, 1),
+    (4, 1, 0, 3, 2), (4, 1, 0, 8, 2), (4, 2, 0, 4, 4), (4, 1, 0, 2, 8)])
+def test_every_launch_shape_is_bit_exact(monkeypatch, kernel, tile_k, threads, warps, group):
+    """Launch shape (kernel, chunks per CTA or per warp, CTA size, warps)
+    changes only the schedule: every forced shape reproduces the oracle,
+    ragged tail included."""
+    monkeypatch.setenv("TMCS_KERNEL", str(kernel))
     monkeypatch.setenv("TMCS_TILE_K", str(tile_k))
-    monkeypatch.setenv("TMCS_THREADS", str(threads))
+    if threads:
+        monkeypatch.setenv("TMCS_THREADS", str(threads))
+    if warps:
+        monkeypatch.setenv("TMCS_WARPS", str(warps))
+    if group:
+        monkeypatch.setenv("TMCS_GROUP", str(group))
     circ = C.teleport_circuit(C.code_by_name("sc5"), 2, 2, C.NoiseModel(0.01, 0.05))
     assert_parity(circ, 64 * 53 + 17, seed=21)
 
@@ -183,6 +193,7 @@ def test_autotuned_large_call_matches_forced_shape(monkeypatch):
     circ = C.nonlocal_cnot_circuit(C.code_by_name("sc5"), 3, 3, C.NoiseModel(0.003, 0.03))
     shots = 64 * 152 * 40 + 9
     a = gpu_sample(circ, shots, 77)
+    monkeypatch.setenv("TMCS_KERNEL", "3")
     monkeypatch.setenv("TMCS_TILE_K", "1")
     monkeypatch.setenv("TMCS_THREADS", "128")
     b = gpu_sample(circ, shots, 77)
