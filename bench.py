@@ -154,9 +154,17 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=120, help="serve: number of requests")
+    ap.add_argument("--load", type=float, default=0.7, help="serve: offered load / solo capacity")
     args = ap.parse_args()
 
     from paper_2504_05611_gb300 import circuits
+    if args.workload == "batch64":
+        batch_bench(args)
+        return
+    if args.workload == "serve":
+        serve_bench(args)
+        return
     workload = circuits.WORKLOADS[args.workload]
     if args.shots:
         workload = circuits.Workload(workload.name, workload.code, workload.op, workload.rounds_before,
@@ -340,6 +348,187 @@ def main():
     sampler.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def batch_bench(args):
+    """Batched launch over the seeded 64-job mix (uneven circuits and shot
+    counts) against the same jobs sampled one call each on the same stream."""
+    import torch
+    from paper_2504_05611_gb300 import build as lib_build
+    from paper_2504_05611_gb300 import circuits, tmcs
+    lib_build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    jobs = circuits.batch_mix(64, seed=1)
+    cache = {}
+    samplers, outs, total_det_bits, total_shots = [], [], 0, 0
+    for w in jobs:
+        key = (w.code, w.op, w.rounds_before, w.p)
+        if key not in cache:
+            cache[key] = tmcs.Sampler(w.circuit())
+        s = cache[key]
+        samplers.append(s)
+        cols = (w.shots + 63) // 64
+        outs.append((torch.empty((s.info["n_det"], cols), dtype=torch.int64, device=dev),
+                     torch.empty((max(s.info["n_obs"], 1), cols), dtype=torch.int64, device=dev)))
+        total_det_bits += s.info["n_det"] * w.shots
+        total_shots += w.shots
+    stream = torch.cuda.Stream(device=dev)
+    jl = [(s.handle, w.shots, w.seed, d, o if s.info["n_obs"] else None)
+          for s, w, (d, o) in zip(samplers, jobs, outs)]
+
+    def timed(fn, steps):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / steps
+
+    def batched():
+        tmcs.tmcs_batch_sample(jl, stream)
+
+    def solo():
+        for (h, n, seed, d, o) in jl:
+            tmcs.tmcs_sample(h, n, seed, d, o, stream)
+
+    for _ in range(max(1, args.warmup)):
+        batched()
+        solo()
+    torch.cuda.synchronize()
+    # a CUDA graph of the batched launch
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            batched()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_batch = timed(batched, args.steps)
+
+    def replay():
+        with torch.cuda.stream(stream):
+            g.replay()
+
+    ms_graph = timed(replay, args.steps)
+    clk = clocks.stop()
+    ms_solo = timed(solo, max(1, args.steps // 2))
+    value = total_det_bits / (min(ms_batch, ms_graph) / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": min(ms_batch, ms_graph), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "shots_per_s": total_shots / (min(ms_batch, ms_graph) / 1e3),
+        "config": {"workload": "batch64", "jobs": len(jobs), "distinct_circuits": len(cache),
+                   "total_shots": total_shots, "mix": "circuits.batch_mix(64, seed=1)"},
+        "batched_ms": ms_batch, "graph_replay_ms": ms_graph, "solo_calls_ms": ms_solo,
+        "batched_vs_solo": ms_solo / min(ms_batch, ms_graph), "clocks": clk,
+        "gpu_launches": 1,
+    }
+    print(json.dumps(line), flush=True)
+    for s in cache.values():
+        s.close()
+
+
+def serve_requests(n, seed):
+    """Seeded request stream of the batched family: SC d = 3..29 (odd) and
+    BB[[144,12,12]], NL or teleport, p in {1e-4, 3e-4, 1e-3} with p_ebit =
+    10 p, shots log-uniform in [1e4, 1e7]."""
+    from paper_2504_05611_gb300 import circuits
+    return circuits.batch_mix(n, seed=seed)
+
+
+def serve_bench(args):
+    """Poisson arrivals into the continuous-batching server at a fixed
+    fraction of the measured solo capacity; reports throughput and latency."""
+    import threading
+    import numpy as np
+    import torch
+    from paper_2504_05611_gb300 import build as lib_build
+    from paper_2504_05611_gb300 import tmcs
+    lib_build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    reqs = serve_requests(args.requests, seed=7)
+    cache, handles = {}, []
+    for w in reqs:
+        key = (w.code, w.op, w.rounds_before, w.p)
+        if key not in cache:
+            cache[key] = tmcs.Sampler(w.circuit())
+        handles.append(cache[key])
+    det_bits = sum(h.info["n_det"] * w.shots for h, w in zip(handles, reqs))
+    shots_total = sum(w.shots for w in reqs)
+    # solo capacity: every request as one tmcs_sample call, back to back
+    words = max((h.info["n_det"] + h.info["n_obs"]) * ((w.shots + 63) // 64) for h, w in zip(handles, reqs))
+    scratch = torch.empty(words, dtype=torch.int64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def solo_pass():
+        for h, w in zip(handles, reqs):
+            cols = (w.shots + 63) // 64
+            d = scratch[: h.info["n_det"] * cols]
+            o = scratch[h.info["n_det"] * cols: (h.info["n_det"] + h.info["n_obs"]) * cols]
+            tmcs.tmcs_sample(h.handle, w.shots, w.seed, d, o if h.info["n_obs"] else None, stream)
+
+    solo_pass()                      # uploads and autotunes every circuit
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    solo_pass()
+    torch.cuda.synchronize()
+    solo_s = time.perf_counter() - t0
+    del scratch
+    torch.cuda.empty_cache()
+    load = args.load
+    mean_gap = solo_s / len(reqs) / load
+    rng = np.random.default_rng(11)
+    gaps = rng.exponential(mean_gap, size=len(reqs))
+    srv = tmcs.Server(n_streams=4)
+    ids = [None] * len(reqs)
+    submitted = threading.Event()
+
+    def client():
+        t = time.perf_counter()
+        for i, (h, w) in enumerate(zip(handles, reqs)):
+            t += gaps[i]
+            delay = t - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids[i] = srv.submit(h, w.shots, w.seed)
+        submitted.set()
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    start = time.perf_counter()
+    th = threading.Thread(target=client)
+    th.start()
+    done = 0
+    while done < len(reqs):
+        while ids[done] is None:
+            time.sleep(0.0005)
+        srv.release(ids[done])
+        done += 1
+    th.join()
+    makespan = time.perf_counter() - start
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    value = det_bits / makespan
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic", "shots_per_s": shots_total / makespan,
+        "config": {"workload": "serve", "requests": len(reqs), "offered_load": load,
+                   "arrivals": "Poisson", "family": "circuits.batch_mix(n, seed=7)", "n_streams": 4},
+        "latency_p50_s": st["latency_p50_s"], "latency_p99_s": st["latency_p99_s"],
+        "latency_mean_s": st["latency_mean_s"], "solo_capacity_s": solo_s,
+        "served_vs_solo_throughput": solo_s / makespan, "completed": st["completed"], "failed": st["failed"],
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    for h in cache.values():
+        h.close()
 
 
 def _kernel_sha():

@@ -202,6 +202,57 @@ int tmcs_batch_sample(const tmcs_job *jobs, size_t n_jobs, void *stream);
  */
 int tmcs_check_device(void);
 
+/*
+ * Sampling server (continuous batching). A host scheduler thread admits
+ * submitted requests in arrival order as soon as their output words fit in a
+ * device arena (admission by HBM footprint), cuts every admitted request into
+ * slices of 64-shot chunks and issues slices round-robin over all admitted
+ * requests on n_streams CUDA streams, so a request that arrives while others
+ * run starts on the next free stream and its work overlaps theirs on the
+ * GPU. Each slice is one tmcs_sample_range call, so every request's output is
+ * bit-identical to a solo tmcs_sample of the same circuit, shots and seed.
+ * Circuits stay device-resident (uploaded on first use) and must outlive their
+ * requests. All functions are thread-safe; the server uses the device that is
+ * current when it is opened.
+ */
+typedef struct tmcs_server tmcs_server;
+
+typedef struct {
+    uint32_t n_streams;         /* concurrent streams (0: 4) */
+    uint32_t slice_chunks;      /* 64-shot chunks per slice (0: 4096) */
+    uint64_t arena_bytes;       /* device bytes for outputs of admitted requests
+                                   (0: half of the free device memory) */
+} tmcs_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, failed, queued, running;
+    uint64_t arena_bytes, arena_in_use;
+    double latency_p50_s, latency_p99_s, latency_mean_s; /* submit -> all slices done */
+    double busy_seconds;        /* wall time with at least one request admitted */
+    uint64_t shots_done;
+} tmcs_server_stats;
+
+enum { TMCS_REQ_QUEUED = 0, TMCS_REQ_RUNNING = 1, TMCS_REQ_DONE = 2, TMCS_REQ_FAILED = 3 };
+
+/* Open a server on the current device (allocates the arena, starts the
+ * scheduler thread). Errors: TMCS_E_OOM, TMCS_E_CUDA. */
+int tmcs_server_open(const tmcs_server_config *cfg, tmcs_server **out);
+/* Queue one request; *request_id identifies it. Fails with TMCS_E_BUFFER if
+ * its outputs, (n_det + n_obs) * ceil(shots/64) * 8 bytes, exceed the arena. */
+int tmcs_server_submit(tmcs_server *srv, const tmcs_circuit *c, uint64_t shots, uint64_t seed,
+                       uint64_t *request_id);
+/* State of a request (TMCS_REQ_*). */
+int tmcs_server_poll(tmcs_server *srv, uint64_t request_id, int *state);
+/* Wait for a request, copy its outputs to host memory in the tmcs_sample
+ * layout (host_det: n_det * ceil(shots/64) words, host_obs: n_obs * ... ;
+ * either may be NULL to skip), then release its arena space. */
+int tmcs_server_fetch(tmcs_server *srv, uint64_t request_id, uint64_t *host_det, uint64_t *host_obs);
+/* Wait for a request and release it without copying its outputs. */
+int tmcs_server_release(tmcs_server *srv, uint64_t request_id);
+int tmcs_server_get_stats(tmcs_server *srv, tmcs_server_stats *out);
+/* Stop the scheduler (after in-flight slices finish) and free the arena. */
+int tmcs_server_close(tmcs_server *srv);
+
 /* Thread-local description of the last error of this thread ("" if none). */
 const char *tmcs_last_error(void);
 

@@ -226,8 +226,9 @@ __device__ __forceinline__ void walk_segment(const NoiseDesc &nd, const uint32_t
 // are contiguous, so one item moves KV vectors (128-bit when K >= 2). Ops
 // are unrolled by U so a thread keeps U*KV independent loads in flight.
 template <int K>
-__device__ __forceinline__ void run_tile(const KernelArgs &P, uint64_t *F, uint32_t *stage0, uint32_t *stage1,
-                                         EvUnit *evbuf, uint64_t *bars, int *abort_flag, uint64_t col0) {
+__device__ __forceinline__ void run_tile(const KernelArgs P, uint64_t *F, uint32_t *stage0, uint32_t *stage1,
+                                         EvUnit *evbuf, uint64_t *bars, int *abort_flag, uint64_t col0,
+                                         uint32_t (&parity)[2]) {
     constexpr int V = K >= 2 ? 2 : 1;  // 64-bit words per vector
     constexpr int KV = K / V;          // vectors per slot
     constexpr int U = KV >= 4 ? 1 : 4 / KV;  // ops per unrolled step
@@ -237,7 +238,6 @@ __device__ __forceinline__ void run_tile(const KernelArgs &P, uint64_t *F, uint3
     const int nvalid = rem < uint64_t(K) ? int(rem) : K;
     const uint32_t chunk0 = P.first_chunk + uint32_t(col0);
     const uint32_t T_ = blockDim.x, tid = threadIdx.x;
-    uint32_t parity[2] = {0u, 0u};
 
     auto issue = [&](uint32_t L) {
         if (tid == 0 && L < P.n_layers) {
@@ -465,7 +465,101 @@ __global__ void __launch_bounds__(512) frame_kernel(const KernelArgs P) {
         fence_barrier_init();
     }
     __syncthreads();
-    run_tile<K>(P, F, stage0, stage1, evbuf, bars, abort_flag, uint64_t(blockIdx.x) * K);
+    uint32_t parity[2] = {0u, 0u};
+    run_tile<K>(P, F, stage0, stage1, evbuf, bars, abort_flag, uint64_t(blockIdx.x) * K, parity);
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent launch: resident CTAs pull work items (job, tile) from a
+// device counter until none are left; each item runs its job's program on
+// one tile with the CTA-wide layer loop above. Jobs may have different
+// circuits, tile sizes (K), seeds and outputs; the job table is a kernel
+// parameter, so a launch needs no host-to-device copy.
+
+constexpr int kMaxBatch = 96;
+
+struct BatchJob {
+    const Layer *layers;
+    const uint32_t *args;
+    const NoiseDesc *noise;
+    const uint32_t *tables;
+    uint64_t *det;
+    uint64_t *obs;
+    uint64_t n_cols;
+    uint64_t last_mask;
+    uint64_t item_begin;  // first work item of this job (items of a job are consecutive)
+    uint32_t n_layers, n_slots, max_window_segs, key0, key1, K;
+};
+
+struct BatchArgs {
+    uint32_t n_jobs;
+    uint32_t pad;
+    uint64_t total_items;
+    unsigned long long *counter;  // work-queue head, zeroed before the launch
+    uint32_t *status;
+    BatchJob jobs[kMaxBatch];
+};
+
+template <int KMAX>
+__global__ void __launch_bounds__(256, KMAX == 1 ? 4 : 3) batch_kernel(const __grid_constant__ BatchArgs B) {
+    extern __shared__ __align__(128) uint64_t smem[];
+    uint64_t *bars = smem;                                           // 2 mbarriers
+    int *abort_flag = reinterpret_cast<int *>(smem + 2);
+    unsigned long long *item_slot = reinterpret_cast<unsigned long long *>(smem + 3);
+    uint32_t *stage0 = reinterpret_cast<uint32_t *>(smem + 16);      // 128-byte offset
+    uint32_t *stage1 = stage0 + kStageWords;
+    uint64_t *F = reinterpret_cast<uint64_t *>(stage1 + kStageWords);
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    uint32_t parity[2] = {0u, 0u};
+    for (;;) {
+        if (threadIdx.x == 0) *item_slot = atomicAdd(B.counter, 1ull);
+        __syncthreads();
+        const unsigned long long item = *item_slot;
+        __syncthreads();
+        if (item >= B.total_items) break;
+        uint32_t lo = 0, hi = B.n_jobs;  // last job with item_begin <= item
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) / 2;
+            if (B.jobs[mid].item_begin <= item) lo = mid; else hi = mid;
+        }
+        const BatchJob &J = B.jobs[lo];
+        KernelArgs a{};
+        a.layers = J.layers;
+        a.args = J.args;
+        a.noise = J.noise;
+        a.tables = J.tables;
+        a.status = B.status;
+        a.n_layers = J.n_layers;
+        a.n_slots = J.n_slots;
+        a.max_window_segs = J.max_window_segs;
+        a.key0 = J.key0;
+        a.key1 = J.key1;
+        a.first_chunk = 0;
+        a.n_cols = J.n_cols;
+        a.last_mask = J.last_mask;
+        a.det = J.det;
+        a.obs = J.obs;
+        const uint64_t col0 = (item - J.item_begin) * J.K;
+        EvUnit *ev = reinterpret_cast<EvUnit *>(F + size_t(J.n_slots) * J.K);
+        if (KMAX >= 4 && J.K == 4)
+            run_tile<KMAX >= 4 ? 4 : 1>(a, F, stage0, stage1, ev, bars, abort_flag, col0, parity);
+        else if (KMAX >= 2 && J.K == 2)
+            run_tile<KMAX >= 2 ? 2 : 1>(a, F, stage0, stage1, ev, bars, abort_flag, col0, parity);
+        else
+            run_tile<1>(a, F, stage0, stage1, ev, bars, abort_flag, col0, parity);
+        if (*abort_flag) break;
+    }
+}
+
+// Shared memory of batch_kernel for one job with tile size K.
+static size_t batch_smem_bytes(uint32_t n_slots, uint32_t max_window_segs, int K) {
+    return 128 + 2 * size_t(kStageWords) * 4 + size_t(n_slots) * K * 8 + size_t(max_window_segs) * K * sizeof(EvUnit);
 }
 
 // ---------------------------------------------------------------------------
@@ -1105,6 +1199,175 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
     return TMCS_OK;
 }
 
+// ---- batched launch
+
+static std::mutex g_batch_mu;
+static std::map<int, unsigned long long *> g_batch_counter;
+
+// Per-device work-queue counter of batch_kernel (library scratch, allocated
+// on the first batched call on a device; make that call before any capture).
+static int batch_counter(int dev, unsigned long long **out) {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    auto it = g_batch_counter.find(dev);
+    if (it != g_batch_counter.end()) {
+        *out = it->second;
+        return TMCS_OK;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, 256);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TMCS_E_OOM, std::string("cudaMalloc of the batch work queue: ") + cudaGetErrorString(e));
+    }
+    g_batch_counter[dev] = static_cast<unsigned long long *>(p);
+    *out = static_cast<unsigned long long *>(p);
+    return TMCS_OK;
+}
+
+// Per-device side stream and fork/join events of batched launches (created
+// on the first batched call that needs them; make that call before capture).
+struct BatchSide {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+static std::map<int, BatchSide> g_batch_side;
+
+static cudaError_t batch_side_stream(int dev, cudaStream_t *s, cudaEvent_t *f, cudaEvent_t *j) {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    BatchSide &b = g_batch_side[dev];
+    cudaError_t e = cudaSuccess;
+    if (!b.s && (e = cudaStreamCreateWithFlags(&b.s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if (!b.fork && (e = cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if (!b.join && (e = cudaEventCreateWithFlags(&b.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+    *s = b.s;
+    *f = b.fork;
+    *j = b.join;
+    return cudaSuccess;
+}
+
+static int batch_sample(const tmcs_job *jobs, size_t n_jobs, void *stream) {
+    if (n_jobs && !jobs) return fail(TMCS_E_INVALID, "jobs is NULL");
+    if (n_jobs == 0) return TMCS_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    DeviceLimits lim;
+    int rc = device_limits(&lim);
+    if (rc) return rc;
+    uint32_t *status = device_status_word(dev);
+    if (!status) return fail(TMCS_E_OOM, "cannot allocate the device status word");
+    unsigned long long *counter = nullptr;
+    if ((rc = batch_counter(dev, &counter))) return rc;
+    // validate and upload every job's program; order by decreasing work
+    struct Item {
+        size_t j;
+        const DeviceProgram *dp;
+        double cost;
+    };
+    std::vector<Item> order;
+    order.reserve(n_jobs);
+    for (size_t j = 0; j < n_jobs; j++) {
+        const tmcs_job &J = jobs[j];
+        const std::string at = "job " + std::to_string(j) + ": ";
+        if (!J.c) return fail(TMCS_E_INVALID, at + "circuit is NULL");
+        if (J.shots == 0) return fail(TMCS_E_INVALID, at + "shots must be positive");
+        if ((J.c->n_det && !J.det) || (J.c->n_obs && !J.obs)) return fail(TMCS_E_INVALID, at + "output buffer is NULL");
+        if ((reinterpret_cast<uintptr_t>(J.det) & 7) || (reinterpret_cast<uintptr_t>(J.obs) & 7))
+            return fail(TMCS_E_BUFFER, at + "output buffers must be 8-byte aligned");
+        if ((J.shots + 63) / 64 > (uint64_t(1) << 32)) return fail(TMCS_E_INVALID, at + "too many shots");
+        const Program &P = J.c->prog;
+        if (batch_smem_bytes(P.n_slots, P.max_window_segs, 1) > lim.smem_optin)
+            return fail(TMCS_E_INVALID, at + "one 64-shot chunk of this circuit does not fit in shared memory");
+        const DeviceProgram *dp = nullptr;
+        if ((rc = device_program(J.c, &dp))) return rc;
+        if (P.layers.empty()) continue;
+        order.push_back({j, dp, double(P.args.size() + 64 * P.layers.size()) * double((J.shots + 63) / 64)});
+    }
+    std::stable_sort(order.begin(), order.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Size classes: jobs whose single 64-shot chunk needs more than 24 KB of
+    // shared memory share one launch; smaller circuits get their own launch
+    // with a smaller budget (more CTAs per SM, larger tiles). The classes run
+    // concurrently on streams forked from `stream` and joined back to it.
+    std::vector<Item> cls[2];
+    for (const Item &it : order) {
+        const Program &P = jobs[it.j].c->prog;
+        cls[batch_smem_bytes(P.n_slots, P.max_window_segs, 1) > (size_t(24) << 10) + 16384 + 128 ? 0 : 1].push_back(it);
+    }
+    const bool fork = !cls[0].empty() && !cls[1].empty();
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    if (fork) {
+        if ((e = batch_side_stream(dev, &side, &ev_fork, &ev_join)) != cudaSuccess) return cuda_fail(e, "batch stream");
+        if ((e = cudaEventRecord(ev_fork, st)) != cudaSuccess) return cuda_fail(e, "batch fork");
+        if ((e = cudaStreamWaitEvent(side, ev_fork, 0)) != cudaSuccess) return cuda_fail(e, "batch fork");
+    }
+    for (int ci = 0; ci < 2; ci++) {
+        const std::vector<Item> &ord = cls[ci];
+        cudaStream_t cs = (fork && ci == 1) ? side : st;
+        unsigned long long *ctr = counter + (ci == 1 ? 16 : 0);
+        for (size_t base = 0; base < ord.size(); base += kMaxBatch) {
+            const size_t nb = std::min<size_t>(kMaxBatch, ord.size() - base);
+            // one shared-memory budget per launch: its largest job at K = 1;
+            // each job then takes the largest tile (K <= 4) that fits it
+            size_t budget = 0;
+            for (size_t i = 0; i < nb; i++) {
+                const Program &P = jobs[ord[base + i].j].c->prog;
+                budget = std::max(budget, batch_smem_bytes(P.n_slots, P.max_window_segs, 1));
+            }
+            budget = std::max(budget, size_t(40) << 10);
+            budget = std::min(budget, lim.smem_optin);
+            BatchArgs B;
+            std::memset(&B, 0, sizeof(B));
+            uint64_t items = 0;
+            for (size_t i = 0; i < nb; i++) {
+                const tmcs_job &J = jobs[ord[base + i].j];
+                const Program &P = J.c->prog;
+                const DeviceProgram *dp = ord[base + i].dp;
+                const uint64_t n_cols = (J.shots + 63) / 64;
+                int K = ci == 0 ? 1 : 4;  // batch tiles: K = 1 for large circuits, up to 4 for small ones
+                while (K > 1 && batch_smem_bytes(P.n_slots, P.max_window_segs, K) > budget) K >>= 1;
+                while (K > 1 && (n_cols + K - 1) / K < 8) K >>= 1;
+                BatchJob &bj = B.jobs[i];
+                bj.layers = dp->layers;
+                bj.args = dp->args;
+                bj.noise = dp->noise;
+                bj.tables = dp->tables;
+                bj.det = J.det;
+                bj.obs = J.obs;
+                bj.n_cols = n_cols;
+                bj.last_mask = (J.shots % 64) ? ((uint64_t(1) << (J.shots % 64)) - 1) : ~uint64_t(0);
+                bj.item_begin = items;
+                bj.n_layers = uint32_t(P.layers.size());
+                bj.n_slots = P.n_slots;
+                bj.max_window_segs = P.max_window_segs;
+                bj.key0 = uint32_t(J.seed);
+                bj.key1 = uint32_t(J.seed >> 32);
+                bj.K = uint32_t(K);
+                items += (n_cols + K - 1) / K;
+            }
+            B.n_jobs = uint32_t(nb);
+            B.total_items = items;
+            B.counter = ctr;
+            B.status = status;
+            const int per_sm = std::max(1, std::min(ci == 0 ? 4 : 3, int(lim.smem_per_sm / (budget + 1024))));
+            const uint64_t grid = std::min<uint64_t>(items, uint64_t(lim.sms) * per_sm);
+            if ((e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), cs)) != cudaSuccess)
+                return cuda_fail(e, "batch queue reset");
+            auto kern = ci == 0 ? batch_kernel<1> : batch_kernel<4>;
+            if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(budget))) != cudaSuccess)
+                return cuda_fail(e, "batch kernel attribute");
+            kern<<<unsigned(grid), 256, budget, cs>>>(B);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+        }
+    }
+    if (fork) {
+        if ((e = cudaEventRecord(ev_join, side)) != cudaSuccess) return cuda_fail(e, "batch join");
+        if ((e = cudaStreamWaitEvent(st, ev_join, 0)) != cudaSuccess) return cuda_fail(e, "batch join");
+    }
+    return TMCS_OK;
+}
+
 // ---- allocation-free sampling
 //
 // Some callers cannot allocate device memory once they are running: a
@@ -1247,12 +1510,7 @@ int tmcs_check_device(void) {
 }
 
 int tmcs_batch_sample(const tmcs_job *jobs, size_t n_jobs, void *stream) {
-    if (n_jobs && !jobs) return fail(TMCS_E_INVALID, "jobs is NULL");
-    for (size_t j = 0; j < n_jobs; j++) {
-        int rc = sample_range(jobs[j].c, 0, jobs[j].shots, jobs[j].seed, jobs[j].det, jobs[j].obs, stream);
-        if (rc) return rc;
-    }
-    return TMCS_OK;
+    return batch_sample(jobs, n_jobs, stream);
 }
 
 }  // extern "C"

@@ -51,6 +51,24 @@ class _Stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in STATS_FIELDS]
 
 
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_uint32), ("slice_chunks", ctypes.c_uint32), ("arena_bytes", ctypes.c_uint64)]
+
+
+SERVER_STATS_FIELDS = (("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                       ("queued", ctypes.c_uint64), ("running", ctypes.c_uint64), ("arena_bytes", ctypes.c_uint64),
+                       ("arena_in_use", ctypes.c_uint64), ("latency_p50_s", ctypes.c_double),
+                       ("latency_p99_s", ctypes.c_double), ("latency_mean_s", ctypes.c_double),
+                       ("busy_seconds", ctypes.c_double), ("shots_done", ctypes.c_uint64))
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = list(SERVER_STATS_FIELDS)
+
+
+REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+
+
 _lib: Optional[ctypes.CDLL] = None
 
 
@@ -74,11 +92,20 @@ def lib() -> ctypes.CDLL:
         L.tmcs_debug_gap_table.argtypes = [ctypes.c_double, P]
         L.tmcs_sample_noalloc.argtypes = [P, U64, U64, U64, P, P, P]
         L.tmcs_check_device.argtypes = []
+        L.tmcs_server_open.argtypes = [P, ctypes.POINTER(P)]
+        L.tmcs_server_submit.argtypes = [P, P, U64, U64, ctypes.POINTER(ctypes.c_uint64)]
+        L.tmcs_server_poll.argtypes = [P, U64, ctypes.POINTER(ctypes.c_int)]
+        L.tmcs_server_fetch.argtypes = [P, U64, P, P]
+        L.tmcs_server_release.argtypes = [P, U64]
+        L.tmcs_server_get_stats.argtypes = [P, P]
+        L.tmcs_server_close.argtypes = [P]
         L.tmcs_last_error.argtypes = []
         L.tmcs_last_error.restype = ctypes.c_char_p
         for f in ("tmcs_circuit_build", "tmcs_circuit_free", "tmcs_circuit_info", "tmcs_circuit_stats",
                   "tmcs_reference_sample", "tmcs_sample", "tmcs_sample_range", "tmcs_batch_sample",
-                  "tmcs_debug_gap_table", "tmcs_check_device", "tmcs_sample_noalloc"):
+                  "tmcs_debug_gap_table", "tmcs_check_device", "tmcs_sample_noalloc", "tmcs_server_open",
+                  "tmcs_server_submit", "tmcs_server_poll", "tmcs_server_fetch", "tmcs_server_release",
+                  "tmcs_server_get_stats", "tmcs_server_close"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -262,6 +289,63 @@ class Sampler:
         if self.handle:
             tmcs_circuit_free(self.handle)
             self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching sampling server (``tmcs_server_*``) on the current
+    CUDA device. Circuits passed to ``submit`` are compiled handles (ints) or
+    ``Sampler`` objects; they must outlive their requests."""
+
+    def __init__(self, arena_bytes: int = 0, n_streams: int = 0, slice_chunks: int = 0):
+        cfg = _ServerConfig(n_streams, slice_chunks, arena_bytes)
+        out = ctypes.c_void_p()
+        _check(lib().tmcs_server_open(ctypes.byref(cfg), ctypes.byref(out)))
+        self.handle = out.value
+        self._shape: Dict[int, Tuple[int, int, int]] = {}
+
+    def submit(self, circuit, shots: int, seed: int) -> int:
+        h = circuit.handle if isinstance(circuit, Sampler) else int(circuit)
+        rid = ctypes.c_uint64()
+        _check(lib().tmcs_server_submit(ctypes.c_void_p(self.handle), ctypes.c_void_p(h), shots,
+                                        seed & (2 ** 64 - 1), ctypes.byref(rid)))
+        info = tmcs_circuit_info(h)
+        self._shape[rid.value] = (info["n_det"], info["n_obs"], (shots + 63) // 64)
+        return rid.value
+
+    def poll(self, request_id: int) -> str:
+        st = ctypes.c_int()
+        _check(lib().tmcs_server_poll(ctypes.c_void_p(self.handle), request_id, ctypes.byref(st)))
+        return REQ_STATES[st.value]
+
+    def fetch(self, request_id: int) -> Tuple[np.ndarray, np.ndarray]:
+        """Wait for the request and return (det, obs) as uint64 arrays in the
+        tmcs_sample layout; releases its device space."""
+        n_det, n_obs, cols = self._shape.pop(request_id)
+        det = np.zeros((n_det, cols), dtype=np.uint64)
+        obs = np.zeros((n_obs, cols), dtype=np.uint64)
+        _check(lib().tmcs_server_fetch(ctypes.c_void_p(self.handle), request_id,
+                                       det.ctypes.data if det.size else None, obs.ctypes.data if obs.size else None))
+        return det, obs
+
+    def release(self, request_id: int) -> None:
+        self._shape.pop(request_id, None)
+        _check(lib().tmcs_server_release(ctypes.c_void_p(self.handle), request_id))
+
+    def stats(self) -> Dict[str, float]:
+        st = _ServerStats()
+        _check(lib().tmcs_server_get_stats(ctypes.c_void_p(self.handle), ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in SERVER_STATS_FIELDS}
+
+    def close(self) -> None:
+        if self.handle:
+            _check(lib().tmcs_server_close(ctypes.c_void_p(self.handle)))
+            self.handle = None
 
     def __del__(self):
         try:

@@ -198,3 +198,62 @@ def test_autotuned_large_call_matches_forced_shape(monkeypatch):
     monkeypatch.setenv("TMCS_THREADS", "128")
     b = gpu_sample(circ, shots, 77)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def _batch_case(n_jobs, seed):
+    """Uneven jobs: SC d = 3..9 NL/teleport/memory and BB[[18,4,4]], varied
+    noise and shot counts (ragged tails included)."""
+    rng = np.random.default_rng(seed)
+    circs, shots = [], []
+    for j in range(n_jobs):
+        code = C.code_by_name(["sc3", "sc5", "sc7", "sc9", "bb18"][int(rng.integers(5))])
+        nz = C.NoiseModel(p=float(rng.choice([3e-3, 1e-2])), p_ebit=float(rng.choice([1e-2, 3e-2])))
+        kind = int(rng.integers(3))
+        r = int(rng.integers(1, 4))
+        circs.append(C.nonlocal_cnot_circuit(code, r, r, nz) if kind == 0 else
+                     C.teleport_circuit(code, r, r, nz) if kind == 1 else C.memory_circuit(code, r + 1, nz))
+        shots.append(int(rng.integers(1, 64 * 400)))
+    return circs, shots
+
+
+def test_batch_many_uneven_jobs_two_launches():
+    """More jobs than one launch holds (96): every job still equals its solo run."""
+    circs, shots = _batch_case(110, 5)
+    samplers = [tmcs.Sampler(c) for c in circs]
+    outs = [s.alloc(n) for s, n in zip(samplers, shots)]
+    jobs = [(s.handle, n, 1000 + i, d, o) for i, (s, n, (d, o)) in enumerate(zip(samplers, shots, outs))]
+    tmcs.tmcs_batch_sample(jobs)
+    torch.cuda.synchronize()
+    for i in range(0, len(circs), 7):
+        sd, so = gpu_sample(circs[i], shots[i], 1000 + i)
+        d, o = outs[i]
+        assert np.array_equal(d.cpu().numpy().view(np.uint64), sd)
+        assert np.array_equal(o[: circs[i].n_obs].cpu().numpy().view(np.uint64), so)
+    for s in samplers:
+        s.close()
+
+
+def test_batch_replays_under_cuda_graph():
+    """A batched launch captured in a CUDA graph replays to the same bits."""
+    circs, shots = _batch_case(12, 9)
+    samplers = [tmcs.Sampler(c) for c in circs]
+    outs = [s.alloc(n) for s, n in zip(samplers, shots)]
+    jobs = [(s.handle, n, 77 + i, d, o) for i, (s, n, (d, o)) in enumerate(zip(samplers, shots, outs))]
+    tmcs.tmcs_batch_sample(jobs)          # first call: uploads programs, allocates the queue
+    torch.cuda.synchronize()
+    ref = [(d.clone(), o.clone()) for d, o in outs]
+    for d, o in outs:
+        d.zero_()
+        o.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        tmcs.tmcs_batch_sample(jobs)
+    for _ in range(2):
+        for d, o in outs:
+            d.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for (d, o), (rd, ro) in zip(outs, ref):
+            assert torch.equal(d, rd) and torch.equal(o, ro)
+    for s in samplers:
+        s.close()
