@@ -155,6 +155,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=120, help="serve: number of requests")
+    ap.add_argument("--batch-mix", default="config", choices=["config", "small"], help="batch64: job mix")
     ap.add_argument("--load", type=float, default=0.7, help="serve: offered load / solo capacity")
     args = ap.parse_args()
 
@@ -359,7 +360,17 @@ def batch_bench(args):
     lib_build.build()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    jobs = circuits.batch_mix(64, seed=1)
+    if args.batch_mix == "small":
+        # many small jobs (SC d = 3..9, 1e4..1e5 shots): solo launches underfill the GPU
+        rng = __import__("numpy").random.default_rng(3)
+        jobs = []
+        for j in range(64):
+            d = int(rng.choice([3, 5, 7, 9]))
+            p = float(rng.choice([1e-4, 3e-4, 1e-3]))
+            jobs.append(circuits.Workload(f"small{j}", f"sc{d}", ("nl", "teleport")[j % 2], d, d, p, 10 * p,
+                                          int(round(10 ** rng.uniform(4, 5))), seed=j + 1))
+    else:
+        jobs = circuits.batch_mix(64, seed=1)
     cache = {}
     samplers, outs, total_det_bits, total_shots = [], [], 0, 0
     for w in jobs:
@@ -422,7 +433,9 @@ def batch_bench(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "shots_per_s": total_shots / (min(ms_batch, ms_graph) / 1e3),
         "config": {"workload": "batch64", "jobs": len(jobs), "distinct_circuits": len(cache),
-                   "total_shots": total_shots, "mix": "circuits.batch_mix(64, seed=1)"},
+                   "total_shots": total_shots,
+                   "mix": "circuits.batch_mix(64, seed=1)" if args.batch_mix != "small" else
+                          "64 SC d=3..9 NL/teleport jobs, 1e4..1e5 shots (seed 3)"},
         "batched_ms": ms_batch, "graph_replay_ms": ms_graph, "solo_calls_ms": ms_solo,
         "batched_vs_solo": ms_solo / min(ms_batch, ms_graph), "clocks": clk,
         "gpu_launches": 1,

@@ -56,22 +56,28 @@ typedef enum {
  *   DETECTOR       XOR of the listed absolute record indices
  *   OBSERVABLE     XOR of the listed records into observable `arg`
  *   TICK           layer hint, no effect
+ *   PAULI_CHANNEL_1 X, Y or Z with probabilities px, py, pz (Methods
+ *                  "Decoherence"): p = px + py + pz; an event's Pauli is X if
+ *                  its 32-bit Pauli word w < arg, Y if w < arg2, else Z, with
+ *                  arg = floor(2^32 px / p), arg2 = floor(2^32 (px+py) / p)
  */
 typedef enum {
     TMCS_R = 0, TMCS_RX, TMCS_H, TMCS_S, TMCS_CX, TMCS_M, TMCS_MX,
     TMCS_X_ERROR, TMCS_Z_ERROR, TMCS_DEPOLARIZE1, TMCS_DEPOLARIZE2,
-    TMCS_XFEED, TMCS_ZFEED, TMCS_DETECTOR, TMCS_OBSERVABLE, TMCS_TICK
+    TMCS_XFEED, TMCS_ZFEED, TMCS_DETECTOR, TMCS_OBSERVABLE, TMCS_TICK,
+    TMCS_PAULI_CHANNEL_1
 } tmcs_opcode;
 
 /* One instruction. `targets` points at n_targets uint32 (host memory, read
- * during tmcs_circuit_build only). `p` is used by the four noise opcodes,
- * `arg` by OBSERVABLE (observable id). 32 bytes on LP64. */
+ * during tmcs_circuit_build only). `p` is used by the noise opcodes, `arg` by
+ * OBSERVABLE (observable id) and PAULI_CHANNEL_1, `arg2` by PAULI_CHANNEL_1
+ * only (must be 0 for every other opcode). 32 bytes on LP64. */
 typedef struct {
     uint32_t code;
     uint32_t n_targets;
     double p;
     uint32_t arg;
-    uint32_t reserved; /* must be 0 */
+    uint32_t arg2;
     const uint32_t *targets;
 } tmcs_op;
 
@@ -91,7 +97,8 @@ typedef struct tmcs_circuit tmcs_circuit; /* opaque; owned by the library */
  * observable is deterministic (TMCS_E_NONDETERMINISTIC otherwise).
  * On success *out owns the compiled circuit; free it with tmcs_circuit_free.
  * Errors: TMCS_E_INVALID (bad opcode, odd pair list, qubit/record index out of
- * range, p outside [0,1] or in (0, 1e-12), reserved != 0), TMCS_E_OOM.
+ * range, p outside [0,1] or in (0, 1e-12), arg2 != 0 outside PAULI_CHANNEL_1,
+ * PAULI_CHANNEL_1 thresholds with arg > arg2), TMCS_E_OOM.
  */
 int tmcs_circuit_build(const tmcs_op *ops, size_t n_ops, uint32_t flags, tmcs_circuit **out);
 

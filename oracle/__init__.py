@@ -36,6 +36,7 @@ _CODES = {
     "R": 0, "RX": 1, "H": 2, "S": 3, "CX": 4, "M": 5, "MX": 6,
     "X_ERROR": 7, "Z_ERROR": 8, "DEPOLARIZE1": 9, "DEPOLARIZE2": 10,
     "XFEED": 11, "ZFEED": 12, "DETECTOR": 13, "OBSERVABLE": 14, "TICK": 15,
+    "PAULI_CHANNEL_1": 16,
 }
 
 _lib: Optional[ctypes.CDLL] = None
@@ -53,9 +54,9 @@ def lib() -> ctypes.CDLL:
         L.oracle_philox4x32_10.restype = None
         L.oracle_gap_table.argtypes = [ctypes.c_double, P]
         L.oracle_gap_table.restype = None
-        L.oracle_sample.argtypes = [I64, P, P, P, P, P, I64, I64, I64, I64, U64, U64, U64, P, P, ctypes.c_int]
+        L.oracle_sample.argtypes = [I64, P, P, P, P, P, P, I64, I64, I64, I64, U64, U64, U64, P, P, ctypes.c_int]
         L.oracle_sample.restype = ctypes.c_int
-        L.oracle_propagate64.argtypes = [I64, P, P, P, P, P, I64, I64, I64, I64, I64, P, P, P, P, U64, P, P]
+        L.oracle_propagate64.argtypes = [I64, P, P, P, P, P, P, I64, I64, I64, I64, I64, P, P, P, P, U64, P, P]
         L.oracle_propagate64.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -74,6 +75,7 @@ class Marshalled:
         self.codes = np.array([_CODES[o.name] for o in ops], dtype=np.int32)
         self.ps = np.array([o.p for o in ops], dtype=np.float64)
         self.args = np.array([o.arg for o in ops], dtype=np.uint32)
+        self.args2 = np.array([getattr(o, "arg2", 0) for o in ops], dtype=np.uint32)
         lens = np.array([o.targets.size for o in ops], dtype=np.int64)
         self.toff = np.zeros(self.n_ops + 1, dtype=np.int64)
         np.cumsum(lens, out=self.toff[1:])
@@ -87,7 +89,7 @@ class Marshalled:
         self.n_obs = circuit.n_obs
 
     def head(self):
-        return (self.n_ops, _ptr(self.codes), _ptr(self.ps), _ptr(self.args), _ptr(self.toff),
+        return (self.n_ops, _ptr(self.codes), _ptr(self.ps), _ptr(self.args), _ptr(self.args2), _ptr(self.toff),
                 _ptr(self.targets), self.n_qubits, self.n_meas, self.n_det, self.n_obs)
 
 

@@ -22,7 +22,7 @@ import numpy as np
 from . import Marshalled, propagate64
 
 # Pauli index -> (first, second) single-qubit Paulis; bit0 = X, bit1 = Z.
-_K = {"X_ERROR": 1, "Z_ERROR": 1, "DEPOLARIZE1": 3, "DEPOLARIZE2": 15}
+_K = {"X_ERROR": 1, "Z_ERROR": 1, "DEPOLARIZE1": 3, "DEPOLARIZE2": 15, "PAULI_CHANNEL_1": 3}
 
 
 def fault_list(circuit) -> List[Tuple[int, int, List[Tuple[int, int]], float]]:
@@ -38,6 +38,12 @@ def fault_list(circuit) -> List[Tuple[int, int, List[Tuple[int, int]], float]]:
         units = len(t) // 2 if op.name == "DEPOLARIZE2" else len(t)
         for u in range(units):
             for k in range(1, K + 1):
+                if op.name == "PAULI_CHANNEL_1":
+                    px, py, pz = op.channel
+                    pk = {1: px, 2: pz, 3: py}[k]
+                    if pk > 0.0:
+                        out.append((i, ch, [(t[u], k)], pk))
+                    continue
                 if op.name == "X_ERROR":
                     inj = [(t[u], 1)]
                 elif op.name == "Z_ERROR":

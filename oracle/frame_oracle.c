@@ -31,7 +31,10 @@
  *   probability p on every position a segment can reach (G is capped at
  *   4096, the trial count of a full segment).
  *   Pauli index bits: x = bit 0, z = bit 1 (X=1, Z=2, Y=3); DEPOLARIZE2 puts
- *   k>>2 on the first target and k&3 on the second.
+ *   k>>2 on the first target and k&3 on the second. PAULI_CHANNEL_1 (event
+ *   probability p = px + py + pz, Methods "Decoherence") picks X if
+ *   w_pauli < t1, Y if w_pauli < t2, else Z, with the op's thresholds
+ *   t1 = floor(2^32 px / p), t2 = floor(2^32 (px + py) / p).
  *
  * Build: gcc -O2 -ffp-contract=off -shared -fPIC -pthread (see oracle/build.py).
  */
@@ -46,6 +49,7 @@ enum {
     OR_R = 0, OR_RX, OR_H, OR_S, OR_CX, OR_M, OR_MX,
     OR_X_ERROR, OR_Z_ERROR, OR_DEP1, OR_DEP2,
     OR_XFEED, OR_ZFEED, OR_DETECTOR, OR_OBSERVABLE, OR_TICK,
+    OR_PC1, /* PAULI_CHANNEL_1 */
     OR_N_CODES
 };
 
@@ -106,6 +110,7 @@ typedef struct {
     const int32_t *codes;
     const double *ps;
     const uint32_t *args;
+    const uint32_t *args2; /* PAULI_CHANNEL_1 second threshold */
     const int64_t *toff; /* n_ops + 1 */
     const uint32_t *targets;
     int64_t n_qubits, n_meas, n_det, n_obs;
@@ -117,7 +122,7 @@ typedef struct {
 
 static int is_noise(int code)
 {
-    return code == OR_X_ERROR || code == OR_Z_ERROR || code == OR_DEP1 || code == OR_DEP2;
+    return code == OR_X_ERROR || code == OR_Z_ERROR || code == OR_DEP1 || code == OR_DEP2 || code == OR_PC1;
 }
 
 /* #{i : w < t[i]} for a non-increasing table (checked when it is built):
@@ -189,6 +194,11 @@ static void noise_op_one_lane(const oracle_circuit *c, const gap_table *tab, int
                 apply_pauli(x, z, t[2 * u], k >> 2);
                 apply_pauli(x, z, t[2 * u + 1], k & 3u);
                 break;
+            case OR_PC1: {
+                uint32_t pauli = (w_pauli < c->args[i]) ? 1u : (w_pauli < c->args2[i]) ? 3u : 2u;
+                apply_pauli(x, z, t[u], pauli);
+                break;
+            }
             }
         }
     }
@@ -248,6 +258,7 @@ static void *shot_worker(void *arg)
                 case OR_Z_ERROR:
                 case OR_DEP1:
                 case OR_DEP2:
+                case OR_PC1:
                     if (c->ps[i] > 0.0)
                         noise_op_one_lane(c, job->tables[i], i, job->seed, chunk, lane, x, z);
                     break;
@@ -291,6 +302,7 @@ static int validate(const oracle_circuit *c)
         int64_t nt = c->toff[i + 1] - c->toff[i];
         const uint32_t *t = c->targets + c->toff[i];
         if (is_noise(code) && !(c->ps[i] >= 0.0 && c->ps[i] <= 1.0)) return -1;
+        if (code == OR_PC1 && c->args[i] > c->args2[i]) return -1;
         if ((code == OR_CX || code == OR_DEP2 || code == OR_XFEED || code == OR_ZFEED) && (nt & 1)) return -1;
         if (code == OR_XFEED || code == OR_ZFEED) {
             for (int64_t a = 0; a < nt; a += 2)
@@ -317,12 +329,12 @@ static int validate(const oracle_circuit *c)
  * 64*col + lane. Returns 0, -1 on an invalid circuit, -2 on allocation failure.
  */
 int oracle_sample(int64_t n_ops, const int32_t *codes, const double *ps, const uint32_t *args,
-                  const int64_t *toff, const uint32_t *targets,
+                  const uint32_t *args2, const int64_t *toff, const uint32_t *targets,
                   int64_t n_qubits, int64_t n_meas, int64_t n_det, int64_t n_obs,
                   uint64_t seed, uint64_t first_chunk, uint64_t shots,
                   uint64_t *det, uint64_t *obs, int threads)
 {
-    oracle_circuit c = {n_ops, codes, ps, args, toff, targets, n_qubits, n_meas, n_det, n_obs};
+    oracle_circuit c = {n_ops, codes, ps, args, args2, toff, targets, n_qubits, n_meas, n_det, n_obs};
     if (validate(&c) != 0) return -1;
     uint64_t n_cols = (shots + 63) / 64;
     if (first_chunk + n_cols > 0x100000000ull) return -1;
@@ -393,13 +405,13 @@ static uint64_t splitmix64(uint64_t *s)
 }
 
 int oracle_propagate64(int64_t n_ops, const int32_t *codes, const double *ps, const uint32_t *args,
-                       const int64_t *toff, const uint32_t *targets,
+                       const uint32_t *args2, const int64_t *toff, const uint32_t *targets,
                        int64_t n_qubits, int64_t n_meas, int64_t n_det, int64_t n_obs,
                        int64_t n_inj, const int64_t *inj_op, const uint32_t *inj_target,
                        const uint32_t *inj_pauli, const uint32_t *inj_lane,
                        uint64_t gauge_seed, uint64_t *det_words, uint64_t *obs_words)
 {
-    oracle_circuit c = {n_ops, codes, ps, args, toff, targets, n_qubits, n_meas, n_det, n_obs};
+    oracle_circuit c = {n_ops, codes, ps, args, args2, toff, targets, n_qubits, n_meas, n_det, n_obs};
     if (validate(&c) != 0) return -1;
     uint64_t *x = calloc((size_t)n_qubits + 1, 8);
     uint64_t *z = calloc((size_t)n_qubits + 1, 8);

@@ -42,12 +42,34 @@ OPCODES: Tuple[str, ...] = (
     "R", "RX", "H", "S", "CX", "M", "MX",
     "X_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2",
     "XFEED", "ZFEED", "DETECTOR", "OBSERVABLE", "TICK",
+    "PAULI_CHANNEL_1",
 )
 OPCODE_ID: Dict[str, int] = {name: i for i, name in enumerate(OPCODES)}
-NOISE_OPS = frozenset({"X_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2"})
+NOISE_OPS = frozenset({"X_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2", "PAULI_CHANNEL_1"})
 PAIR_OPS = frozenset({"CX", "DEPOLARIZE2", "XFEED", "ZFEED"})
 QUBIT_OPS = frozenset({"R", "RX", "H", "S", "CX", "M", "MX",
-                       "X_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2"})
+                       "X_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2", "PAULI_CHANNEL_1"})
+
+
+def pauli_channel_thresholds(px: float, py: float, pz: float) -> Tuple[float, int, int]:
+    """PAULI_CHANNEL_1(px, py, pz) as (p, t1, t2): an event happens with
+    probability p = px + py + pz; its Pauli is X if w < t1, Y if w < t2, else
+    Z, for a uniform 32-bit word w, with t1 = floor(2^32 px / p) and
+    t2 = floor(2^32 (px + py) / p) (both capped at 2^32 - 1), i.e. the
+    conditional split is quantised to 2^-32."""
+    for v in (px, py, pz):
+        if not (0.0 <= v <= 1.0):
+            raise ValueError("PAULI_CHANNEL_1 probabilities must lie in [0, 1]")
+    p = px + py + pz
+    if p > 1.0 + 1e-12:
+        raise ValueError("PAULI_CHANNEL_1 probabilities sum above 1")
+    p = min(p, 1.0)
+    if p == 0.0:
+        return 0.0, 0, 0
+    cap = 2 ** 32 - 1
+    t1 = min(cap, int(math.floor(2.0 ** 32 * px / p)))
+    t2 = min(cap, int(math.floor(2.0 ** 32 * (px + py) / p)))
+    return p, t1, t2
 
 
 @dataclasses.dataclass
@@ -64,6 +86,8 @@ class Op:
     p: float = 0.0
     arg: int = 0
     tag: str = ""
+    arg2: int = 0
+    channel: Optional[Tuple[float, float, float]] = None  # PAULI_CHANNEL_1 (px, py, pz)
 
 
 class Circuit:
@@ -79,12 +103,19 @@ class Circuit:
         self.meta: Dict[str, object] = {}
 
     # -- construction -------------------------------------------------------
-    def append(self, name: str, targets: Iterable[int] = (), p: float = 0.0,
+    def append(self, name: str, targets: Iterable[int] = (), p=0.0,
                arg: int = 0, tag: str = "") -> np.ndarray:
         """Append one op; returns the record indices an M/MX op creates
-        (empty otherwise)."""
+        (empty otherwise). PAULI_CHANNEL_1 takes p = (px, py, pz)."""
         if name not in OPCODE_ID:
             raise ValueError(f"unknown op {name!r}")
+        channel = None
+        arg2 = 0
+        if name == "PAULI_CHANNEL_1":
+            channel = tuple(float(v) for v in p)
+            if len(channel) != 3:
+                raise ValueError("PAULI_CHANNEL_1 needs (px, py, pz)")
+            p, arg, arg2 = pauli_channel_thresholds(*channel)
         t = np.asarray(list(targets) if not isinstance(targets, np.ndarray) else targets,
                        dtype=np.int64).ravel()
         if t.size and t.min() < 0:
@@ -98,7 +129,7 @@ class Circuit:
         if name in ("XFEED", "ZFEED") and t.size and t[0::2].max() >= self.n_meas:
             raise ValueError(f"{name}: record index beyond {self.n_meas}")
         t = t.astype(np.uint32)
-        self.ops.append(Op(name, t, float(p), int(arg), tag))
+        self.ops.append(Op(name, t, float(p), int(arg), tag, int(arg2), channel))
         if name in QUBIT_OPS and t.size:
             self.n_qubits = max(self.n_qubits, int(t.max()) + 1)
         if name in ("XFEED", "ZFEED") and t.size:
@@ -120,7 +151,9 @@ class Circuit:
         lines = []
         for op in self.ops:
             head = op.name
-            if op.name in NOISE_OPS:
+            if op.name == "PAULI_CHANNEL_1":
+                head += "(" + ",".join(repr(v) for v in op.channel) + ")"
+            elif op.name in NOISE_OPS:
                 head += f"({op.p!r})"
             elif op.name == "OBSERVABLE":
                 head += f"({op.arg})"
@@ -145,6 +178,8 @@ class Circuit:
             if par is not None:
                 if name == "OBSERVABLE":
                     arg = int(par)
+                elif name == "PAULI_CHANNEL_1":
+                    p = tuple(float(v) for v in par.split(","))
                 else:
                     p = float(par)
             c.append(name, targets, p=p, arg=arg)
@@ -410,6 +445,58 @@ class Block:
 
 
 @dataclasses.dataclass
+class Decoherence:
+    """Ebit decoherence while ebits wait for use (Methods "Decoherence").
+
+    Each ebit is aged by the time between its generation and the end of
+    generation of all n ebits, and both of its halves get
+    PAULI_CHANNEL_1(p_X, p_Y, p_Z) with p_X = p_Y = (1 - e^{-t/T1}) / 4 and
+    p_Z = (1 - e^{-t/T2}) / 2 - (1 - e^{-t/T1}) / 4 (the paper takes
+    T1 = T2). Schedules:
+      * "serial": one ebit per time step t_gen; ebit j (1..n) has age
+        (n - j) t_gen;
+      * "lines": ``lines`` ebits per time step (default: d for surface codes,
+        the divisor of n closest to d for BB codes); the L = ceil(n / f)
+        lines are generated in order and line l (1..L) has age (L - l) t_gen.
+        (The text's formula for this case repeats the serial one; this is the
+        reading used here.)
+    Ages are in units of T1 through ``t_gen_over_t1``.
+    """
+
+    t_gen_over_t1: float
+    t2_over_t1: float = 1.0
+    schedule: str = "serial"
+    lines: int = 0
+
+
+def decoherence_paulis(t_over_t1: float, t_over_t2: float) -> Tuple[float, float, float]:
+    """(p_X, p_Y, p_Z) of an idle period t (Methods "Decoherence")."""
+    a = -math.expm1(-t_over_t1)
+    b = -math.expm1(-t_over_t2)
+    return a / 4.0, a / 4.0, b / 2.0 - a / 4.0
+
+
+def line_width(code: "CSSCode", n: int) -> int:
+    """Ebits generated per time step in the line schedule: d for the surface
+    code; for BB codes the divisor of n closest to d (ties: the smaller)."""
+    if code.name.startswith("SC"):
+        return max(1, code.d)
+    divs = [f for f in range(1, n + 1) if n % f == 0]
+    return min(divs, key=lambda f: (abs(f - code.d), f))
+
+
+def ebit_ages(code: "CSSCode", n: int, dec: Decoherence) -> List[int]:
+    """Age of ebit j (index 0..n-1) in units of t_gen."""
+    if dec.schedule == "serial":
+        return [n - 1 - j for j in range(n)]
+    if dec.schedule == "lines":
+        f = dec.lines or line_width(code, n)
+        L = (n + f - 1) // f
+        return [L - 1 - j // f for j in range(n)]
+    raise ValueError(f"unknown ebit schedule {dec.schedule!r}")
+
+
+@dataclasses.dataclass
 class NoiseModel:
     """Methods "Simulation": p on gates, resets and measurements; p_ebit on
     freshly prepared ebit pairs.
@@ -430,6 +517,7 @@ class NoiseModel:
     p_ebit: float = 1e-2
     idle: bool = False
     feed_noise: bool = False
+    decoherence: Optional[Decoherence] = None
 
 
 class Builder:
@@ -564,6 +652,17 @@ class Builder:
         self.op("H", ea, tag="prep")
         self.op("CX", bell, tag="prep")
         self.err("DEPOLARIZE2", bell, nz.p_ebit, tag="ebit")
+        if nz.decoherence is not None:
+            dec = nz.decoherence
+            ages = ebit_ages(ctrl.code, n, dec)
+            for age in sorted(set(ages), reverse=True):
+                if age == 0:
+                    continue
+                t = age * dec.t_gen_over_t1
+                ch = decoherence_paulis(t, t / dec.t2_over_t1)
+                js = [j for j in range(n) if ages[j] == age]
+                qs = np.concatenate([ea[js], eb[js]])
+                self.c.append("PAULI_CHANNEL_1", qs, p=ch, tag="ebit")
         self.op("TICK", [], tag="tick")
         pairs1 = np.stack([ctrl.data, ea], axis=1).ravel()
         self.op("CX", pairs1, tag="gate")
@@ -692,6 +791,77 @@ def teleport_circuit(code: CSSCode, rounds_before: int = 4, rounds_after: int = 
     return b.c
 
 
+# Methods "Pauli string compute": local (0) / non-local (1) pattern of the
+# chain CX_{1->2}, ..., CX_{(w-1)->w} for each string weight w.
+CHAIN_PATTERNS: Dict[int, str] = {2: "1", 3: "10", 4: "101", 5: "1010", 6: "10101"}
+
+
+def pauli_string_circuit(code: CSSCode, w: int, pattern: Optional[str] = None, rounds_before: int = 4,
+                         noise: Optional[NoiseModel] = None) -> Circuit:
+    """Methods "Pauli string compute" (Eq. chain-compute): the parity of w
+    code blocks is computed onto an ancilla block by the chain
+    CX_{1->2}, ..., CX_{(w-1)->w}, CX_{w->a}.
+
+    w + 1 blocks are noisily initialised in |0_L>; ``rounds_before`` rounds
+    run on all of them; each chain CNOT is local (transversal CX with
+    DEPOLARIZE2(p) on every pair) or non-local (the gate-teleported CNOT of
+    ``Builder.nonlocal_cnot_core``) as ``pattern`` says (default: the
+    paper's pattern for w); the final CX_{w->a} is local. After each chain
+    CNOT between blocks m and m+1 one syndrome round runs on those two blocks
+    only; then every block, ancilla included, is measured in the Z basis.
+
+    Readings: the text sends non-local CNOTs through "Fig. 1(c)" with ebit
+    noise equal to the physical error rate; this uses the non-local CNOT of
+    Fig. 1(b) and leaves p_ebit to the noise model (set p_ebit = p to match).
+    The round after a CNOT also follows the final CX_{w->a}.
+
+    Detectors: as in the non-local CNOT, a target block's first check after
+    a CNOT also takes the control block's last record of the same check.
+    Observables: Z_L of every logical of every block, block order
+    1..w then the ancilla.
+    """
+    if w < 1:
+        raise ValueError("string weight must be >= 1")
+    pattern = pattern if pattern is not None else CHAIN_PATTERNS.get(w, "")
+    if len(pattern) != w - 1 or any(ch not in "01" for ch in pattern):
+        raise ValueError(f"pattern must have {w - 1} symbols in {{0, 1}}")
+    noise = noise or NoiseModel()
+    b = Builder(noise)
+    blocks = [b.block(code, f"CB{i + 1}") for i in range(w)] + [b.block(code, "ANC")]
+    b.reset_data(blocks)
+    prev: List[Optional[np.ndarray]] = [None] * len(blocks)
+    extra: List[Optional[List[List[int]]]] = [None] * len(blocks)
+    for _ in range(rounds_before):
+        recs = b.syndrome_round(blocks)
+        for i, blk in enumerate(blocks):
+            b.round_detectors(blk, recs[i], prev[i], extra[i])
+            prev[i], extra[i] = recs[i], None
+    links = [(m, m + 1, pattern[m] == "1") for m in range(w - 1)] + [(w - 1, w, False)]
+    for m, t, nonlocal_ in links:
+        if nonlocal_:
+            b.nonlocal_cnot_core(blocks[m], blocks[t])
+        else:
+            pairs = np.stack([blocks[m].data, blocks[t].data], axis=1).ravel()
+            b.op("CX", pairs, tag="gate")
+            b.err("DEPOLARIZE2", pairs, noise.p)
+            b.op("TICK", [], tag="tick")
+        if prev[m] is not None:
+            extra[t] = [[int(prev[m][i])] + (extra[t][i] if extra[t] else []) for i in range(code.n_zchecks)]
+        recs = b.syndrome_round([blocks[m], blocks[t]])
+        for j, bi in enumerate((m, t)):
+            b.round_detectors(blocks[bi], recs[j], prev[bi], extra[bi])
+            prev[bi], extra[bi] = recs[j], None
+    data_recs = b.measure_data(blocks, tag="readout")
+    nxt = 0
+    for i, blk in enumerate(blocks):
+        b.final_detectors(blk, data_recs[i], prev[i], extra[i])
+    for i, blk in enumerate(blocks):
+        nxt = b.observables(blk, data_recs[i], nxt)
+    b.c.meta.update(op="pauli_string", code=code.name, w=w, pattern=pattern, rounds=(rounds_before, 1),
+                    p=noise.p, p_ebit=noise.p_ebit, n=code.n, k=code.k)
+    return b.c
+
+
 def memory_circuit(code: CSSCode, rounds: int, noise: Optional[NoiseModel] = None) -> Circuit:
     """Single-block Z-basis memory experiment (test fixture; not a paper
     workload): |0_L> init, ``rounds`` rounds, readout, Z detectors,
@@ -752,14 +922,17 @@ class Workload:
     p_ebit: float
     shots: int
     seed: int = 1
+    decoherence: Optional[Decoherence] = None
 
     def circuit(self) -> Circuit:
         code = code_by_name(self.code)
-        nz = NoiseModel(p=self.p, p_ebit=self.p_ebit)
+        nz = NoiseModel(p=self.p, p_ebit=self.p_ebit, decoherence=self.decoherence)
         if self.op == "nl":
             return nonlocal_cnot_circuit(code, self.rounds_before, self.rounds_after, nz)
         if self.op == "teleport":
             return teleport_circuit(code, self.rounds_before, self.rounds_after, nz)
+        if self.op.startswith("pauli"):
+            return pauli_string_circuit(code, int(self.op[5:]), rounds_before=self.rounds_before, noise=nz)
         raise ValueError(self.op)
 
 
@@ -773,6 +946,12 @@ WORKLOADS: Dict[str, Workload] = {
     # distance-29 SC non-local CNOT, 29 rounds before/after, 1e7 shots
     "nl_sc29": Workload("nl_sc29", "sc29", "nl", 29, 29, 1e-3, 1e-2, 10_000_000),
     "nl_sc29_p1e-4": Workload("nl_sc29_p1e-4", "sc29", "nl", 29, 29, 1e-4, 1e-3, 10_000_000),
+    # Pauli-string compute, weight 4 (pattern 101), BB[[144,12,12]], p = p_ebit
+    "ps4_bb144": Workload("ps4_bb144", "bb144", "pauli4", 4, 1, 5e-4, 5e-4, 1_000_000),
+    # distance-11 SC non-local CNOT with line-generated ebits decohering
+    # (t_gen / T1 = 1e-4, T1 = T2), p = p_ebit = 1e-3
+    "nl_sc11_deco": Workload("nl_sc11_deco", "sc11", "nl", 11, 11, 1e-3, 1e-3, 10_000_000,
+                             decoherence=Decoherence(1e-4, schedule="lines")),
 }
 
 

@@ -25,7 +25,7 @@ int fail(int code, const std::string &msg) {
 
 static bool is_noise(uint32_t code) {
     return code == TMCS_X_ERROR || code == TMCS_Z_ERROR || code == TMCS_DEPOLARIZE1 ||
-           code == TMCS_DEPOLARIZE2;
+           code == TMCS_DEPOLARIZE2 || code == TMCS_PAULI_CHANNEL_1;
 }
 
 static bool is_pair(uint32_t code) {
@@ -78,6 +78,7 @@ struct IRNoise {
     uint32_t op;
     uint32_t kind;
     double p;
+    uint32_t t1 = 0, t2 = 0;
     std::vector<uint32_t> comp;  // (xv, zv) per target qubit
     std::vector<uint8_t> live;   // per comp entry
 };
@@ -155,7 +156,7 @@ static int validate_program(const Program &P, uint64_t n_det, uint64_t n_obs) {
     for (size_t i = 0; i < P.noise.size(); i++) {
         const NoiseDesc &nd = P.noise[i];
         const uint64_t words = uint64_t(nd.kind == N_DEP2 ? 2 : 1) * nd.n_units;
-        if (nd.kind > N_DEP2 || nd.table >= P.table_p.size() || nd.n_seg != (nd.n_units + kSegUnits - 1) / kSegUnits ||
+        if (nd.kind > N_PC1 || (nd.kind == N_PC1 && nd.t1 > nd.t2) || nd.table >= P.table_p.size() || nd.n_seg != (nd.n_units + kSegUnits - 1) / kSegUnits ||
             uint64_t(nd.tgt_off) + words > P.args.size())
             return bad("noise descriptor " + std::to_string(i));
         for (uint64_t w = 0; w < words; w++) {
@@ -229,13 +230,18 @@ int compile(tmcs_circuit *c, uint32_t flags) {
         case TMCS_X_ERROR:
         case TMCS_Z_ERROR:
         case TMCS_DEPOLARIZE1:
-        case TMCS_DEPOLARIZE2: {
+        case TMCS_DEPOLARIZE2:
+        case TMCS_PAULI_CHANNEL_1: {
             if (!(op.p > 0.0) || op.nt == 0) break;
             IRNoise nz;
             nz.op = uint32_t(i);
             nz.kind = op.code == TMCS_X_ERROR ? N_XERR : op.code == TMCS_Z_ERROR ? N_ZERR
-                      : op.code == TMCS_DEPOLARIZE1 ? N_DEP1 : N_DEP2;
+                      : op.code == TMCS_DEPOLARIZE1 ? N_DEP1 : op.code == TMCS_DEPOLARIZE2 ? N_DEP2 : N_PC1;
             nz.p = op.p;
+            if (nz.kind == N_PC1) {
+                nz.t1 = op.arg;
+                nz.t2 = op.arg2;
+            }
             nz.comp.reserve(2 * op.nt);
             for (uint32_t a = 0; a < op.nt; a++) {
                 nz.comp.push_back(X[t[a]]);
@@ -538,6 +544,8 @@ int compile(tmcs_circuit *c, uint32_t flags) {
         NoiseDesc nd{};
         nd.op_index = nz.op;
         nd.kind = nz.kind;
+        nd.t1 = nz.t1;
+        nd.t2 = nz.t2;
         int rc = table_for(nz.p, &nd.table);
         if (rc) return rc;
         const uint32_t nq = uint32_t(nz.comp.size() / 2);
@@ -870,8 +878,12 @@ int tmcs_circuit_build(const tmcs_op *ops, size_t n_ops, uint32_t flags, tmcs_ci
         for (size_t i = 0; i < n_ops; i++) {
             const tmcs_op &op = ops[i];
             const std::string where = "op " + std::to_string(i) + ": ";
-            if (op.code > TMCS_TICK) { delete c; return fail(TMCS_E_INVALID, where + "unknown opcode"); }
-            if (op.reserved) { delete c; return fail(TMCS_E_INVALID, where + "reserved field must be 0"); }
+            if (op.code > TMCS_PAULI_CHANNEL_1) { delete c; return fail(TMCS_E_INVALID, where + "unknown opcode"); }
+            if (op.arg2 && op.code != TMCS_PAULI_CHANNEL_1) { delete c; return fail(TMCS_E_INVALID, where + "arg2 must be 0"); }
+            if (op.code == TMCS_PAULI_CHANNEL_1 && op.arg > op.arg2) {
+                delete c;
+                return fail(TMCS_E_INVALID, where + "PAULI_CHANNEL_1 thresholds must satisfy arg <= arg2");
+            }
             if (op.n_targets && !op.targets) { delete c; return fail(TMCS_E_INVALID, where + "targets is NULL"); }
             if (is_pair(op.code) && (op.n_targets & 1)) { delete c; return fail(TMCS_E_INVALID, where + "odd target count"); }
             if (is_noise(op.code)) {
@@ -879,7 +891,7 @@ int tmcs_circuit_build(const tmcs_op *ops, size_t n_ops, uint32_t flags, tmcs_ci
                 if (op.p > 0.0 && op.p < 1e-12) { delete c; return fail(TMCS_E_INVALID, where + "probability below 1e-12"); }
             }
             if (c->targets.size() + op.n_targets > 0xFFFFFFFFull) { delete c; return fail(TMCS_E_INVALID, "too many targets"); }
-            HostOp h{op.code, op.p, op.arg, uint32_t(c->targets.size()), op.n_targets};
+            HostOp h{op.code, op.p, op.arg, uint32_t(c->targets.size()), op.n_targets, op.arg2};
             const uint32_t *t = op.targets;
             if (op.code == TMCS_DETECTOR || op.code == TMCS_OBSERVABLE) {
                 for (uint32_t a = 0; a < op.n_targets; a++)

@@ -57,7 +57,7 @@ constexpr uint32_t kEvCap = 8;          // events buffered per (segment, chunk)
 constexpr uint32_t kWindowSegs = 192;   // noise segments per generation window
 constexpr uint32_t kWindowOps = 16;     // noise ops per generation window
 
-enum NoiseKind : uint32_t { N_XERR = 0, N_ZERR = 1, N_DEP1 = 2, N_DEP2 = 3 };
+enum NoiseKind : uint32_t { N_XERR = 0, N_ZERR = 1, N_DEP1 = 2, N_DEP2 = 3, N_PC1 = 4 };
 
 // Targets of a noise op live at args[tgt_off ...]: one word per qubit,
 // x slot in the low 16 bits, z slot in the high 16 bits, 0xFFFF = component
@@ -69,7 +69,7 @@ struct NoiseDesc {
     uint32_t n_units;   // targets (pairs for DEPOLARIZE2)
     uint32_t n_seg;     // ceil(n_units / 64)
     uint32_t tgt_off;   // offset into args
-    uint32_t pad0, pad1;
+    uint32_t t1, t2;    // PAULI_CHANNEL_1: X if w < t1, Y if w < t2, else Z
 };
 
 constexpr uint32_t kSegUnits = 64;     // units per noise segment
@@ -118,6 +118,7 @@ struct HostOp {
     double p;
     uint32_t arg;
     uint32_t toff, nt;
+    uint32_t arg2;
 };
 
 }  // namespace tmcs

@@ -171,7 +171,7 @@ __device__ __forceinline__ void apply_event(uint64_t *F, const uint32_t *__restr
         if (pb & 2u) xor_bit(F, c1 >> 16, K, k, bit);
     } else {
         const uint32_t c0 = __ldg(tg + unit);
-        const uint32_t pa = kind == N_XERR ? 1u : kind == N_ZERR ? 2u : pk;
+        const uint32_t pa = kind == N_XERR ? 1u : kind == N_ZERR ? 2u : pk;  // DEPOLARIZE1, PAULI_CHANNEL_1: pk
         if (pa & 1u) xor_bit(F, c0 & 0xFFFFu, K, k, bit);
         if (pa & 2u) xor_bit(F, c0 >> 16, K, k, bit);
     }
@@ -179,6 +179,12 @@ __device__ __forceinline__ void apply_event(uint64_t *F, const uint32_t *__restr
 
 __device__ __forceinline__ uint32_t npauli_of(uint32_t kind) {
     return kind == N_DEP2 ? 15u : kind == N_DEP1 ? 3u : 1u;
+}
+
+// Pauli index (x = bit 0, z = bit 1) of an event from its Pauli word.
+__device__ __forceinline__ uint32_t pauli_index(const NoiseDesc &nd, uint32_t npauli, uint32_t wp) {
+    if (nd.kind == N_PC1) return wp < nd.t1 ? 1u : wp < nd.t2 ? 3u : 2u;
+    return 1u + __umulhi(wp, npauli);
 }
 
 // Walks draws d = d0, d0+1, ... of one (segment, chunk) stream from position
@@ -200,7 +206,7 @@ __device__ __forceinline__ void walk_segment(const NoiseDesc &nd, const uint32_t
         const int prev = pos;
         pos += 1 + gap_count(T, inv, wg);
         if (pos >= n_trials) break;
-        const uint32_t pk = 1u + __umulhi(wp, npauli);
+        const uint32_t pk = pauli_index(nd, npauli, wp);
         if (buf) {
             if (n == kEvCap) {
                 buf->cont_d = uint16_t(d);

@@ -29,7 +29,7 @@ TMCS_FLAG_NO_AUDIT = 0x1
 TMCS_FLAG_NO_PRUNE = 0x2
 
 OP_DTYPE = np.dtype([("code", "<u4"), ("n_targets", "<u4"), ("p", "<f8"), ("arg", "<u4"),
-                     ("reserved", "<u4"), ("targets", "<u8")])
+                     ("arg2", "<u4"), ("targets", "<u8")])
 assert OP_DTYPE.itemsize == 32
 
 STATS_FIELDS = ("n_layers", "n_slots", "n_xor", "n_zero", "n_copy", "n_noise_ops", "n_noise_units",
@@ -135,6 +135,7 @@ def marshal_ops(circuit: Circuit) -> Tuple[np.ndarray, np.ndarray]:
     arr["n_targets"] = lens
     arr["p"] = [o.p for o in ops]
     arr["arg"] = [o.arg for o in ops]
+    arr["arg2"] = [getattr(o, "arg2", 0) for o in ops]
     arr["targets"] = flat.ctypes.data + 4 * offs
     return arr, flat
 

@@ -29,8 +29,11 @@ def random_noisy_circuit(rng, n, depth):
     for i, (name, t) in enumerate(body + inv):
         c.append(name, t)
         if rng.random() < 0.3:
-            kind = ["X_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2"][int(rng.integers(4))]
-            if kind == "DEPOLARIZE2":
+            kind = ["X_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2", "PAULI_CHANNEL_1"][int(rng.integers(5))]
+            if kind == "PAULI_CHANNEL_1":
+                qs = sorted(set(int(v) for v in rng.integers(0, n, 2)))
+                c.append(kind, qs, p=tuple(float(v) for v in rng.uniform(0.0, 0.1, 3)))
+            elif kind == "DEPOLARIZE2":
                 a, b = rng.choice(n, 2, replace=False)
                 c.append(kind, [int(a), int(b)], p=float(rng.uniform(0.01, 0.3)))
             else:

@@ -102,6 +102,17 @@ def test_rejects_invalid_ops(tmcs):
         tmcs.tmcs_circuit_build(c)
     with pytest.raises(tmcs.TmcsError):
         tmcs.tmcs_circuit_build(C.Circuit(), flags=0x80)
+    # arg2 is only meaningful for PAULI_CHANNEL_1, whose thresholds must be ordered
+    c = C.Circuit()
+    c.append("R", [0])
+    arr, flat = tmcs.marshal_ops(c)
+    arr["arg2"] = 5
+    assert tmcs.lib().tmcs_circuit_build(arr.ctypes.data, 1, 0, ctypes.byref(out)) == 1
+    c = C.Circuit()
+    c.append("PAULI_CHANNEL_1", [0], p=(0.1, 0.1, 0.1))
+    arr, flat = tmcs.marshal_ops(c)
+    arr["arg"], arr["arg2"] = arr["arg2"][0], arr["arg"][0]
+    assert tmcs.lib().tmcs_circuit_build(arr.ctypes.data, 1, 0, ctypes.byref(out)) == 1
 
 
 @pytest.mark.parametrize("trial", range(40))

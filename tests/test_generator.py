@@ -125,3 +125,73 @@ def test_invalid_ops_rejected():
         c.append("DETECTOR", [0])
     with pytest.raises(ValueError):
         c.append("FOO", [0])
+
+
+@pytest.mark.parametrize("key", ["sc3", "bb18"])
+@pytest.mark.parametrize("w", [1, 2, 3, 4, 5, 6])
+def test_pauli_string_chain_deterministic(key, w):
+    """Methods "Pauli string compute": w+1 blocks, the chain pattern of the
+    text (w=2: 1, 3: 10, 4: 101, 5: 1010, 6: 10101), all detectors and
+    observables deterministic, one ebit pair per data qubit per non-local link."""
+    import oracle
+    code = C.code_by_name(key)
+    c = C.pauli_string_circuit(code, w, rounds_before=2, noise=C.NoiseModel(1e-3, 1e-3))
+    bad_d, bad_o = oracle.gauge_audit(c)
+    assert bad_d.size == 0 and bad_o.size == 0
+    nonlocal_links = C.CHAIN_PATTERNS.get(w, "").count("1")
+    # qubits: (w+1) blocks of data + check ancillas, plus 2n ebits per non-local link
+    per_block = code.n + code.n_xchecks + code.n_zchecks
+    assert c.n_qubits == (w + 1) * per_block + nonlocal_links * 2 * code.n
+    assert c.n_obs == (w + 1) * code.k
+
+
+def test_pauli_string_distance_sc3():
+    """The chained compute on distance-3 surface-code blocks keeps circuit
+    distance 3 (same check as Table I's for the paper's primitives)."""
+    from oracle import dem
+    c = C.pauli_string_circuit(C.code_by_name("sc3"), 3, rounds_before=2, noise=C.NoiseModel(1e-3, 1e-3))
+    assert dem.circuit_distance(c, max_weight=3) == 3
+
+
+def test_pauli_string_pattern_validation():
+    with pytest.raises(ValueError):
+        C.pauli_string_circuit(C.code_by_name("sc3"), 3, pattern="1")
+    with pytest.raises(ValueError):
+        C.pauli_string_circuit(C.code_by_name("sc3"), 3, pattern="12")
+
+
+def test_decoherence_channel_limits():
+    """Methods "Decoherence": no idling gives no noise; an ebit idle for many
+    T1 = T2 is fully depolarised (X, Y, Z each 1/4); short idling costs
+    t / (4 T1) per Pauli."""
+    assert C.decoherence_paulis(0.0, 0.0) == (0.0, 0.0, 0.0)
+    px, py, pz = C.decoherence_paulis(60.0, 60.0)
+    assert abs(px - 0.25) < 1e-12 and abs(py - 0.25) < 1e-12 and abs(pz - 0.25) < 1e-12
+    px, py, pz = C.decoherence_paulis(1e-6, 1e-6)
+    assert abs(px / 2.5e-7 - 1) < 1e-5 and abs(pz / 2.5e-7 - 1) < 1e-5
+
+
+@pytest.mark.parametrize("schedule", ["serial", "lines"])
+def test_decoherence_ebit_ages(schedule):
+    """Serial generation ages ebit j by (n - j) t_gen; line generation (f = d
+    per step for the surface code) ages line l by (L - l) t_gen; every ebit
+    half gets its channel and the circuit stays deterministic."""
+    import oracle
+    code = C.code_by_name("sc5")
+    dec = C.Decoherence(1e-3, schedule=schedule)
+    c = C.nonlocal_cnot_circuit(code, 2, 2, C.NoiseModel(1e-3, 1e-2, decoherence=dec))
+    pcs = [op for op in c.ops if op.name == "PAULI_CHANNEL_1"]
+    ages = sorted(round(-4 * __import__("math").log1p(-4 * op.channel[0]) / 1e-3 / 4) for op in pcs)
+    if schedule == "serial":
+        assert ages == list(range(1, 25)) and all(op.targets.size == 2 for op in pcs)
+    else:
+        assert ages == [1, 2, 3, 4] and all(op.targets.size == 10 for op in pcs)
+    bad_d, bad_o = oracle.gauge_audit(c)
+    assert bad_d.size == 0 and bad_o.size == 0
+
+
+def test_line_width_bb():
+    """BB codes use the divisor of n closest to d (Methods "Decoherence")."""
+    assert C.line_width(C.code_by_name("bb144"), 144) == 12
+    assert C.line_width(C.code_by_name("bb18"), 18) == 3
+    assert C.line_width(C.code_by_name("bb90"), 90) == 10

@@ -257,3 +257,48 @@ def test_batch_replays_under_cuda_graph():
             assert torch.equal(d, rd) and torch.equal(o, ro)
     for s in samplers:
         s.close()
+
+
+@pytest.mark.parametrize("code,w", [("sc3", 2), ("sc3", 4), ("sc3", 6), ("bb18", 3), ("sc5", 5)])
+def test_pauli_string_chain(code, w):
+    circ = C.pauli_string_circuit(C.code_by_name(code), w, rounds_before=2, noise=C.NoiseModel(0.01, 0.01))
+    assert_parity(circ, 64 * 29 + 11, seed=31)
+
+
+def test_pauli_string_bb144_full_size_sampled_chunks():
+    """Weight-4 chain on BB[[144,12,12]] blocks at its bench size (1e6 shots):
+    sampled chunks against the oracle."""
+    w = C.WORKLOADS["ps4_bb144"]
+    circ = w.circuit()
+    s = tmcs.Sampler(circ)
+    det, obs = s.sample(w.shots, w.seed)
+    torch.cuda.synchronize()
+    cols = (w.shots + 63) // 64
+    for col in (0, cols // 3, cols - 1):
+        n = min(64, w.shots - 64 * col)
+        od, oo = oracle.sample(circ, n, w.seed, first_chunk=col, threads=8)
+        assert np.array_equal(det[:, col].cpu().numpy().view(np.uint64), od[:, 0])
+        assert np.array_equal(obs[:, col].cpu().numpy().view(np.uint64), oo[:, 0])
+    s.close()
+
+
+@pytest.mark.parametrize("code,schedule", [("sc5", "serial"), ("sc5", "lines"), ("bb18", "lines")])
+def test_ebit_decoherence(code, schedule):
+    """Methods "Decoherence": aged ebits get PAULI_CHANNEL_1 noise."""
+    nz = C.NoiseModel(0.003, 0.01, decoherence=C.Decoherence(2e-3, schedule=schedule))
+    circ = C.nonlocal_cnot_circuit(C.code_by_name(code), 2, 2, nz)
+    assert_parity(circ, 64 * 41 + 3, seed=8)
+
+
+def test_ebit_decoherence_workload_sampled_chunks():
+    w = C.WORKLOADS["nl_sc11_deco"]
+    circ = w.circuit()
+    s = tmcs.Sampler(circ)
+    shots = 64 * 152 * 20
+    det, obs = s.sample(shots, w.seed)
+    torch.cuda.synchronize()
+    for col in (0, 777, shots // 64 - 1):
+        od, oo = oracle.sample(circ, 64, w.seed, first_chunk=col, threads=8)
+        assert np.array_equal(det[:, col].cpu().numpy().view(np.uint64), od[:, 0])
+        assert np.array_equal(obs[:, col].cpu().numpy().view(np.uint64), oo[:, 0])
+    s.close()

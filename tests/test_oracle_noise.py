@@ -154,3 +154,36 @@ def test_probability_zero_and_one():
     c.append("DETECTOR", [1])
     b = bits(c, 1000)
     assert not b[0].any() and b[1].all()
+
+
+def test_pauli_channel_1_distribution():
+    """PAULI_CHANNEL_1(px, py, pz) (Methods "Decoherence"): X, Y, Z with the
+    given probabilities, read out through x/z copy CNOTs."""
+    px, py, pz = 0.05, 0.12, 0.2
+    c = Circuit()
+    c.append("R", [0, 1])
+    c.append("RX", [2])
+    c.append("PAULI_CHANNEL_1", [0], p=(px, py, pz))
+    readout_xz(c, 0, 1, 2)
+    c.append("M", [1])
+    c.append("MX", [2])
+    c.append("DETECTOR", [0])
+    c.append("DETECTOR", [1])
+    n = 300_000
+    b = bits(c, n)
+    h = np.bincount(b[0] + 2 * b[1], minlength=4)
+    assert close(h[1], n, px) and close(h[3], n, py) and close(h[2], n, pz)
+    assert close(h[0], n, 1 - px - py - pz)
+
+
+def test_pauli_channel_1_edges():
+    c = Circuit()
+    c.append("R", [0, 1, 2])
+    c.append("PAULI_CHANNEL_1", [0], p=(0.0, 0.0, 0.0))
+    c.append("PAULI_CHANNEL_1", [1], p=(1.0, 0.0, 0.0))
+    c.append("PAULI_CHANNEL_1", [2], p=(0.0, 0.0, 1.0))
+    c.append("M", [0, 1, 2])
+    for r in range(3):
+        c.append("DETECTOR", [r])
+    b = bits(c, 640)
+    assert not b[0].any() and b[1].sum() >= 639 and not b[2].any()
