@@ -184,6 +184,25 @@ int tmcs_sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shot
 int tmcs_sample_noalloc(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
                         uint64_t *detector_bits, uint64_t *observable_bits, void *stream);
 
+/*
+ * Detector error model by single-fault injection (Methods "Decoding": one
+ * detector-error-model column per distinct error mechanism). Faults are
+ * enumerated over the op list: every noise op with p > 0 in order, every
+ * target unit (pair for DEPOLARIZE2), Pauli index k = 1..K (K = 1 for
+ * X_ERROR/Z_ERROR, 3 for DEPOLARIZE1/PAULI_CHANNEL_1 with 1=X, 2=Z, 3=Y, 15
+ * for DEPOLARIZE2 with k>>2 on the first and k&3 on the second target).
+ * tmcs_fault_count gives the number of faults.
+ * tmcs_fault_signatures propagates faults first_fault .. first_fault+n_faults-1
+ * through the noiseless circuit, one fault per lane, with the sampling
+ * kernels: lane l of word c of detector j (layout of tmcs_sample with
+ * ceil(n_faults/64) words per detector) says whether fault first_fault+64c+l
+ * flips detector j; observables likewise. first_fault must be a multiple of
+ * 64. Errors: TMCS_E_INVALID (range), as tmcs_sample otherwise.
+ */
+int tmcs_fault_count(const tmcs_circuit *c, uint64_t *n_faults);
+int tmcs_fault_signatures(const tmcs_circuit *c, uint64_t first_fault, uint64_t n_faults, uint64_t *detector_bits,
+                          uint64_t *observable_bits, void *stream);
+
 /* One job of a batched launch: circuit, shots (from chunk 0), seed, outputs. */
 typedef struct {
     const tmcs_circuit *c;

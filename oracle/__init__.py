@@ -56,6 +56,9 @@ def lib() -> ctypes.CDLL:
         L.oracle_gap_table.restype = None
         L.oracle_sample.argtypes = [I64, P, P, P, P, P, P, I64, I64, I64, I64, U64, U64, U64, P, P, ctypes.c_int]
         L.oracle_sample.restype = ctypes.c_int
+        L.oracle_sample_measurements.argtypes = [I64, P, P, P, P, P, P, I64, I64, I64, I64, P, U64, U64, U64, P,
+                                                 ctypes.c_int]
+        L.oracle_sample_measurements.restype = ctypes.c_int
         L.oracle_propagate64.argtypes = [I64, P, P, P, P, P, P, I64, I64, I64, I64, I64, P, P, P, P, U64, P, P]
         L.oracle_propagate64.restype = ctypes.c_int
         _lib = L
@@ -122,6 +125,28 @@ def sample(circuit, shots: int, seed: int, first_chunk: int = 0, threads: int = 
     if rc != 0:
         raise ValueError(f"oracle_sample failed with {rc}")
     return det[:m.n_det, :cols], obs[:m.n_obs, :cols]
+
+
+def sample_measurements(circuit, shots: int, seed: int, first_chunk: int = 0, threads: int = 1,
+                        reference: Optional[np.ndarray] = None) -> np.ndarray:
+    """Raw measurement records, [n_meas][ceil(shots/64)] uint64 (bit l of
+    column c = shot 64c + l): reference XOR flip with gauge-randomised
+    frames, so random outcomes are fair coins. The reference record comes
+    from the oracle tableau unless given."""
+    m = Marshalled(circuit)
+    if reference is None:
+        from .tableau import reference_sample
+        reference = reference_sample(circuit)["rec"]
+    ref = np.ascontiguousarray(np.asarray(reference, dtype=np.uint8))
+    if ref.size == 0:
+        ref = np.zeros(1, np.uint8)
+    cols = (shots + 63) // 64
+    meas = np.zeros((max(m.n_meas, 1), max(cols, 1)), dtype=np.uint64)
+    rc = lib().oracle_sample_measurements(*m.head(), _ptr(ref), seed & 0xFFFFFFFFFFFFFFFF, first_chunk, shots,
+                                          _ptr(meas), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle_sample_measurements failed with {rc}")
+    return meas[:m.n_meas, :cols]
 
 
 def propagate64(circuit, inj_op, inj_target, inj_pauli, inj_lane, gauge_seed: int = 0,

@@ -27,7 +27,8 @@ _K = {"X_ERROR": 1, "Z_ERROR": 1, "DEPOLARIZE1": 3, "DEPOLARIZE2": 15, "PAULI_CH
 
 def fault_list(circuit) -> List[Tuple[int, int, List[Tuple[int, int]], float]]:
     """(op index, channel id, [(qubit, pauli), ...], probability) for every
-    elementary fault of every noise channel with p > 0."""
+    elementary fault of every noise channel with p > 0, in the order noise op,
+    target unit, Pauli index k = 1..K."""
     out = []
     ch = 0
     for i, op in enumerate(circuit.ops):
@@ -40,9 +41,7 @@ def fault_list(circuit) -> List[Tuple[int, int, List[Tuple[int, int]], float]]:
             for k in range(1, K + 1):
                 if op.name == "PAULI_CHANNEL_1":
                     px, py, pz = op.channel
-                    pk = {1: px, 2: pz, 3: py}[k]
-                    if pk > 0.0:
-                        out.append((i, ch, [(t[u], k)], pk))
+                    out.append((i, ch, [(t[u], k)], {1: px, 2: pz, 3: py}[k]))
                     continue
                 if op.name == "X_ERROR":
                     inj = [(t[u], 1)]

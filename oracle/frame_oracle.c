@@ -381,6 +381,168 @@ int oracle_sample(int64_t n_ops, const int32_t *codes, const double *ps, const u
     return rc;
 }
 
+/* ---------------------------------------- raw measurement sampling */
+
+/*
+ * Measurement records of every shot (not only detector parities): the frame
+ * additionally gets a random gauge Pauli wherever it is free to -- Z after R
+ * and M, X after RX and MX, Z on every qubit at the start (an implicit R) --
+ * which leaves the state unchanged but makes every non-deterministic outcome
+ * a fair coin, and each record is reported as reference XOR flip.
+ * Gauge word of (op i, target u, chunk c): Philox4x32-10 at counter
+ * (u / 2, c, i, 2^31) with the sampling key; (w0 | w1 << 32) for even u,
+ * (w2 | w3 << 32) for odd u; bit `lane` applies to shot 64 c + lane. The
+ * implicit initial R uses op index n_ops and target u = qubit.
+ */
+static uint32_t gauge_bit(uint64_t seed, uint32_t op, uint32_t u, uint32_t chunk, uint32_t lane)
+{
+    uint32_t ctr[4] = {u / 2u, chunk, op, 0x80000000u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    oracle_philox4x32_10(ctr, key, w);
+    uint64_t word = (u & 1u) ? ((uint64_t)w[2] | ((uint64_t)w[3] << 32)) : ((uint64_t)w[0] | ((uint64_t)w[1] << 32));
+    return (uint32_t)((word >> lane) & 1u);
+}
+
+typedef struct {
+    const oracle_circuit *c;
+    const gap_table *const *tables;
+    const uint8_t *ref;
+    uint64_t seed, first_chunk, shots, col_begin, col_end, n_cols;
+    uint64_t *meas;
+    int status;
+} meas_job;
+
+static void *meas_worker(void *arg)
+{
+    meas_job *job = (meas_job *)arg;
+    const oracle_circuit *c = job->c;
+    uint8_t *x = calloc((size_t)c->n_qubits + 1, 1);
+    uint8_t *z = calloc((size_t)c->n_qubits + 1, 1);
+    uint8_t *rec = calloc((size_t)c->n_meas + 1, 1);
+    if (!x || !z || !rec) {
+        job->status = -2;
+        free(x); free(z); free(rec);
+        return NULL;
+    }
+    for (uint64_t col = job->col_begin; col < job->col_end; col++) {
+        uint32_t chunk = (uint32_t)(job->first_chunk + col);
+        for (uint32_t lane = 0; lane < 64; lane++) {
+            uint64_t shot = col * 64 + lane;
+            if (shot >= job->shots) break;
+            for (int64_t q = 0; q < c->n_qubits; q++) {
+                x[q] = 0;
+                z[q] = (uint8_t)gauge_bit(job->seed, (uint32_t)c->n_ops, (uint32_t)q, chunk, lane);
+            }
+            int64_t m = 0;
+            for (int64_t i = 0; i < c->n_ops; i++) {
+                int code = c->codes[i];
+                const uint32_t *t = c->targets + c->toff[i];
+                int64_t nt = c->toff[i + 1] - c->toff[i];
+                switch (code) {
+                case OR_R:
+                    for (int64_t a = 0; a < nt; a++) {
+                        x[t[a]] = 0;
+                        z[t[a]] = (uint8_t)gauge_bit(job->seed, (uint32_t)i, (uint32_t)a, chunk, lane);
+                    }
+                    break;
+                case OR_RX:
+                    for (int64_t a = 0; a < nt; a++) {
+                        z[t[a]] = 0;
+                        x[t[a]] = (uint8_t)gauge_bit(job->seed, (uint32_t)i, (uint32_t)a, chunk, lane);
+                    }
+                    break;
+                case OR_H:
+                    for (int64_t a = 0; a < nt; a++) { uint8_t v = x[t[a]]; x[t[a]] = z[t[a]]; z[t[a]] = v; }
+                    break;
+                case OR_S:
+                    for (int64_t a = 0; a < nt; a++) z[t[a]] ^= x[t[a]];
+                    break;
+                case OR_CX:
+                    for (int64_t a = 0; a + 1 < nt; a += 2) { x[t[a + 1]] ^= x[t[a]]; z[t[a]] ^= z[t[a + 1]]; }
+                    break;
+                case OR_M:
+                    for (int64_t a = 0; a < nt; a++) {
+                        rec[m++] = x[t[a]];
+                        z[t[a]] ^= (uint8_t)gauge_bit(job->seed, (uint32_t)i, (uint32_t)a, chunk, lane);
+                    }
+                    break;
+                case OR_MX:
+                    for (int64_t a = 0; a < nt; a++) {
+                        rec[m++] = z[t[a]];
+                        x[t[a]] ^= (uint8_t)gauge_bit(job->seed, (uint32_t)i, (uint32_t)a, chunk, lane);
+                    }
+                    break;
+                case OR_X_ERROR:
+                case OR_Z_ERROR:
+                case OR_DEP1:
+                case OR_DEP2:
+                case OR_PC1:
+                    if (c->ps[i] > 0.0) noise_op_one_lane(c, job->tables[i], i, job->seed, chunk, lane, x, z);
+                    break;
+                case OR_XFEED:
+                    for (int64_t a = 0; a + 1 < nt; a += 2) x[t[a + 1]] ^= rec[t[a]];
+                    break;
+                case OR_ZFEED:
+                    for (int64_t a = 0; a + 1 < nt; a += 2) z[t[a + 1]] ^= rec[t[a]];
+                    break;
+                default:
+                    break;
+                }
+            }
+            for (int64_t r = 0; r < c->n_meas; r++)
+                if (rec[r] ^ job->ref[r]) job->meas[(uint64_t)r * job->n_cols + col] |= (uint64_t)1 << lane;
+        }
+    }
+    free(x); free(z); free(rec);
+    return NULL;
+}
+
+/* meas: [n_meas][ceil(shots/64)] zero-filled; ref: n_meas reference bits. */
+int oracle_sample_measurements(int64_t n_ops, const int32_t *codes, const double *ps, const uint32_t *args,
+                               const uint32_t *args2, const int64_t *toff, const uint32_t *targets,
+                               int64_t n_qubits, int64_t n_meas, int64_t n_det, int64_t n_obs,
+                               const uint8_t *ref, uint64_t seed, uint64_t first_chunk, uint64_t shots,
+                               uint64_t *meas, int threads)
+{
+    oracle_circuit c = {n_ops, codes, ps, args, args2, toff, targets, n_qubits, n_meas, n_det, n_obs};
+    if (validate(&c) != 0) return -1;
+    uint64_t n_cols = (shots + 63) / 64;
+    if (first_chunk + n_cols > 0x100000000ull) return -1;
+    const gap_table **tables = calloc((size_t)n_ops + 1, sizeof(gap_table *));
+    gap_table *distinct = calloc((size_t)n_ops + 1, sizeof(gap_table));
+    double *distinct_p = calloc((size_t)n_ops + 1, sizeof(double));
+    int64_t n_distinct = 0;
+    if (!tables || !distinct || !distinct_p) { free(tables); free(distinct); free(distinct_p); return -2; }
+    for (int64_t i = 0; i < n_ops; i++) {
+        if (!is_noise(codes[i]) || !(ps[i] > 0.0)) continue;
+        int64_t k = 0;
+        while (k < n_distinct && distinct_p[k] != ps[i]) k++;
+        if (k == n_distinct) {
+            distinct_p[k] = ps[i];
+            oracle_gap_table(ps[i], distinct[k].t);
+            n_distinct++;
+        }
+        tables[i] = &distinct[k];
+    }
+    if (threads < 1) threads = 1;
+    if ((uint64_t)threads > n_cols) threads = (int)(n_cols ? n_cols : 1);
+    meas_job *jobs = calloc((size_t)threads, sizeof(meas_job));
+    pthread_t *tid = calloc((size_t)threads, sizeof(pthread_t));
+    if (!jobs || !tid) { free(tables); free(distinct); free(distinct_p); free(jobs); free(tid); return -2; }
+    for (int w = 0; w < threads; w++)
+        jobs[w] = (meas_job){&c, tables, ref, seed, first_chunk, shots,
+                             n_cols * (uint64_t)w / (uint64_t)threads, n_cols * (uint64_t)(w + 1) / (uint64_t)threads,
+                             n_cols, meas, 0};
+    for (int w = 0; w < threads; w++) pthread_create(&tid[w], NULL, meas_worker, &jobs[w]);
+    for (int w = 0; w < threads; w++) pthread_join(tid[w], NULL);
+    int rc = 0;
+    for (int w = 0; w < threads; w++)
+        if (jobs[w].status) rc = jobs[w].status;
+    free(tables); free(distinct); free(distinct_p); free(jobs); free(tid);
+    return rc;
+}
+
 /* ------------------------------------- bit-parallel fault propagation */
 
 /*

@@ -130,3 +130,70 @@ def run(circuit, faults: Sequence[Tuple[int, int, int]] = ()) -> Dict[str, np.nd
         for q, p in by_op.get(i, ()):
             sv.pauli(q, p)
     return {"rec": np.array(rec, dtype=np.uint8), "det": np.array(det, dtype=np.uint8), "obs": obs}
+
+
+def outcome_distribution(circuit) -> Dict[Tuple[int, ...], float]:
+    """Exact probability of every measurement-record string of a noiseless
+    circuit (Born rule), by branching the state vector at every measurement
+    and reset; conditioned Paulis follow each branch's outcomes."""
+    out: Dict[Tuple[int, ...], float] = {}
+
+    def measure_branch(sv: StateVector, q: int, outcome: int):
+        keep = sv._bit(q) == outcome
+        psi = np.where(keep, sv.psi, 0.0)
+        p = float(np.sum(np.abs(psi) ** 2))
+        if p < 1e-12:
+            return None, 0.0
+        nsv = StateVector(sv.n)
+        nsv.psi = psi / np.sqrt(p)
+        return nsv, p
+
+    def run_from(sv: StateVector, op_i: int, t_i: int, rec: Tuple[int, ...], prob: float):
+        ops = circuit.ops
+        while op_i < len(ops):
+            op = ops[op_i]
+            t = [int(v) for v in op.targets]
+            name = op.name
+            if name in ("M", "MX", "R", "RX") and t_i < len(t):
+                q = t[t_i]
+                if name == "MX":
+                    sv.h(q)
+                for outcome in (0, 1):
+                    nsv, p = measure_branch(sv, q, outcome)
+                    if nsv is None:
+                        continue
+                    nrec = rec
+                    if name in ("M", "MX"):
+                        nrec = rec + (outcome,)
+                        if name == "MX":
+                            nsv.h(q)
+                    else:
+                        if outcome:
+                            nsv.x(q)
+                        if name == "RX":
+                            nsv.h(q)
+                    run_from(nsv, op_i, t_i + 1, nrec, prob * p)
+                return
+            if name not in ("M", "MX", "R", "RX"):
+                if name == "H":
+                    for q in t:
+                        sv.h(q)
+                elif name == "S":
+                    for q in t:
+                        sv.s(q)
+                elif name == "CX":
+                    for a in range(0, len(t), 2):
+                        sv.cx(t[a], t[a + 1])
+                elif name == "XFEED":
+                    for a in range(0, len(t), 2):
+                        if rec[t[a]]:
+                            sv.x(t[a + 1])
+                elif name == "ZFEED":
+                    for a in range(0, len(t), 2):
+                        if rec[t[a]]:
+                            sv.z(t[a + 1])
+            op_i, t_i = op_i + 1, 0
+        out[rec] = out.get(rec, 0.0) + prob
+
+    run_from(StateVector(circuit.n_qubits), 0, 0, (), 1.0)
+    return out

@@ -60,14 +60,14 @@ int gap_table(double p, uint32_t *t) {
 size_t program_bytes(const Program &p) {
     auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
     return al(p.layers.size() * sizeof(Layer)) + al(p.args.size() * 4) +
-           al(p.noise.size() * sizeof(NoiseDesc)) + al(p.tables.size() * 4);
+           al(p.noise.size() * sizeof(NoiseDesc)) + al(p.tables.size() * 4) + al(p.fault_base.size() * 8);
 }
 
 // -------------------------------------------------------------- compiler
 
 namespace {
 
-enum IRKind : uint8_t { I_ZERO, I_XOR, I_COPY, I_NOISE, I_DET, I_OBS };
+enum IRKind : uint8_t { I_ZERO, I_XOR, I_COPY, I_NOISE, I_DET, I_OBS, I_GAUGE, I_REC };
 
 struct IRInst {
     uint8_t kind;
@@ -94,7 +94,7 @@ struct IRParity {
 // blocks 16-byte aligned and at most kStageWords words, every slot index
 // below n_slots, list bounds inside their block, detector and observable ids
 // in range, noise windows inside the event buffer. Runs after every compile.
-static int validate_program(const Program &P, uint64_t n_det, uint64_t n_obs) {
+static int validate_program(const Program &P, uint64_t n_det, uint64_t n_obs, uint64_t n_meas) {
     auto bad = [](const std::string &m) { return fail(TMCS_E_INVALID, "internal: program check failed: " + m); };
     if (P.args.size() % 4) return bad("args not padded");
     uint32_t staged = 0;
@@ -144,6 +144,16 @@ static int validate_program(const Program &P, uint64_t n_det, uint64_t n_obs) {
             if (segs != ly.aux2 || ly.aux2 > P.max_window_segs) return bad(at + ": window size");
             break;
         }
+        case L_GAUGE:
+            if (!ly.nwords || 3ull * ly.count > ly.nwords) return bad(at + ": block too small");
+            for (uint32_t i = 0; i < ly.count; i++)
+                if (b[3 * i] >= P.n_slots) return bad(at + ": slot out of range");
+            break;
+        case L_RECOUT:
+            if (!ly.nwords || 2ull * ly.count > ly.nwords) return bad(at + ": block too small");
+            for (uint32_t i = 0; i < ly.count; i++)
+                if ((b[2 * i] & 0x7FFFFFFFu) >= P.n_slots || b[2 * i + 1] >= n_meas) return bad(at + ": record out of range");
+            break;
         case L_NAPPLY: {
             if (ly.nwords || ly.aux >= P.noise.size()) return bad(at + ": apply layer");
             if (uint64_t(ly.aux2) + P.noise[ly.aux].n_seg > P.max_window_segs) return bad(at + ": window base");
@@ -170,8 +180,17 @@ static int validate_program(const Program &P, uint64_t n_det, uint64_t n_obs) {
     return TMCS_OK;
 }
 
-int compile(tmcs_circuit *c, uint32_t flags) {
+// meas = false: detector/observable program (c->prog). meas = true: raw
+// measurement program (c->prog_meas): gauge Paulis XORed in after every reset
+// and measurement (and on z at the start), every record emitted as
+// reference XOR flip, detectors and observables left out.
+int compile(tmcs_circuit *c, uint32_t flags, bool meas) {
     const bool prune = !(flags & TMCS_FLAG_NO_PRUNE);
+    std::vector<std::pair<uint32_t, uint32_t>> gauges;  // (op index, target index) per I_GAUGE
+    auto gauge = [&](uint32_t vreg, uint32_t op, uint32_t u, std::vector<IRInst> &irv) {
+        irv.push_back({I_GAUGE, vreg, uint32_t(gauges.size())});
+        gauges.push_back({op, u});
+    };
     const uint64_t Q = c->n_qubits;
     uint32_t V = 0;
     std::vector<IRInst> ir;
@@ -187,7 +206,9 @@ int compile(tmcs_circuit *c, uint32_t flags) {
         Z[q] = newv();
         ir.push_back({I_ZERO, Z[q], 0});
     }
-    for (uint64_t o = 0; o < c->n_obs; o++) {
+    if (meas)
+        for (uint64_t q = 0; q < Q; q++) gauge(Z[q], uint32_t(c->ops.size()), uint32_t(q), ir);
+    for (uint64_t o = 0; o < c->n_obs && !meas; o++) {
         acc[o] = newv();
         ir.push_back({I_ZERO, acc[o], 0});
     }
@@ -203,6 +224,7 @@ int compile(tmcs_circuit *c, uint32_t flags) {
                 ir.push_back({I_ZERO, X[t[a]], 0});
                 Z[t[a]] = newv();
                 ir.push_back({I_ZERO, Z[t[a]], 0});
+                if (meas) gauge(op.code == TMCS_R ? Z[t[a]] : X[t[a]], uint32_t(i), a, ir);
             }
             break;
         case TMCS_H:
@@ -221,10 +243,15 @@ int compile(tmcs_circuit *c, uint32_t flags) {
         case TMCS_MX:
             for (uint32_t a = 0; a < op.nt; a++) {
                 std::vector<uint32_t> &P = (op.code == TMCS_M) ? X : Z;
-                rec[m++] = P[t[a]];
+                rec[m] = P[t[a]];
                 uint32_t nv = newv();
                 ir.push_back({I_COPY, nv, P[t[a]]});
                 P[t[a]] = nv;
+                if (meas) {
+                    ir.push_back({I_REC, rec[m], uint32_t(m)});
+                    gauge(op.code == TMCS_M ? Z[t[a]] : X[t[a]], uint32_t(i), a, ir);
+                }
+                m++;
             }
             break;
         case TMCS_X_ERROR:
@@ -259,6 +286,7 @@ int compile(tmcs_circuit *c, uint32_t flags) {
             for (uint32_t a = 0; a + 1 < op.nt; a += 2) ir.push_back({I_XOR, Z[t[a + 1]], rec[t[a]]});
             break;
         case TMCS_DETECTOR: {
+            if (meas) break;
             IRParity p;
             p.acc = uint32_t(d++);
             for (uint32_t a = 0; a < op.nt; a++) p.recs.push_back(rec[t[a]]);
@@ -267,6 +295,7 @@ int compile(tmcs_circuit *c, uint32_t flags) {
             break;
         }
         case TMCS_OBSERVABLE: {
+            if (meas) break;
             IRParity p;
             p.acc = acc[op.arg];
             for (uint32_t a = 0; a < op.nt; a++) p.recs.push_back(rec[t[a]]);
@@ -281,7 +310,7 @@ int compile(tmcs_circuit *c, uint32_t flags) {
 
     // ---- backward liveness: keep only updates that can reach an output
     std::vector<uint8_t> live(V, 0), keep(ir.size(), 0);
-    for (uint64_t o = 0; o < c->n_obs; o++) live[acc[o]] = 1;
+    for (uint64_t o = 0; o < c->n_obs && !meas; o++) live[acc[o]] = 1;
     uint64_t pruned = 0;
     for (size_t k = ir.size(); k-- > 0;) {
         const IRInst &in = ir[k];
@@ -331,6 +360,16 @@ int compile(tmcs_circuit *c, uint32_t flags) {
             for (uint32_t r : pars[in.a].recs) live[r] = 1;
             if (in.kind == I_OBS) live[pars[in.a].acc] = 1;
             break;
+        case I_GAUGE:
+            if (live[in.a] || !prune) {
+                keep[k] = 1;
+                live[in.a] = 1;
+            }
+            break;
+        case I_REC:
+            keep[k] = 1;
+            live[in.a] = 1;
+            break;
         }
     }
 
@@ -359,6 +398,12 @@ int compile(tmcs_circuit *c, uint32_t flags) {
             case I_XOR:
             case I_COPY:
                 ok = wstamp[in.a] != L && rstamp[in.a] != L && wstamp[in.b] != L;
+                break;
+            case I_GAUGE:
+                ok = wstamp[in.a] != L && rstamp[in.a] != L;
+                break;
+            case I_REC:
+                ok = wstamp[in.a] != L;
                 break;
             case I_DET:
                 for (uint32_t r : pars[in.a].recs) ok = ok && wstamp[r] != L;
@@ -390,6 +435,12 @@ int compile(tmcs_circuit *c, uint32_t flags) {
             break;
         case I_NOISE:
             cur_kind = -1;  // noise layers hold one op
+            break;
+        case I_GAUGE:
+            wstamp[in.a] = L;
+            break;
+        case I_REC:
+            rstamp[in.a] = L;
             break;
         }
     }
@@ -432,9 +483,13 @@ int compile(tmcs_circuit *c, uint32_t flags) {
             for (uint32_t r : pars[in.a].recs) touch(r, l);
             if (in.kind == I_OBS) touch(pars[in.a].acc, l);
             break;
+        case I_GAUGE:
+        case I_REC:
+            touch(in.a, l);
+            break;
         }
     }
-    for (uint64_t o = 0; o < c->n_obs; o++) touch(acc[o], obsout_layer);
+    for (uint64_t o = 0; o < c->n_obs && !meas; o++) touch(acc[o], obsout_layer);
     for (uint32_t v = 0; v < V; v++) {
         if (used[v] && def_layer[v] == 0xFFFFFFFFu)
             return fail(TMCS_E_INVALID, "internal: frame value used without definition");
@@ -463,7 +518,7 @@ int compile(tmcs_circuit *c, uint32_t flags) {
                                         " frame slots; at most 65534 are supported");
 
     // ---- gap tables
-    Program &P = c->prog;
+    Program &P = meas ? c->prog_meas : c->prog;
     P = Program();
     std::unordered_map<uint64_t, uint32_t> table_id;
     auto table_for = [&](double p, uint32_t *out) -> int {
@@ -494,7 +549,8 @@ int compile(tmcs_circuit *c, uint32_t flags) {
     // independent). Item order inside update layers cycles through the 16
     // residues of the destination slot, so the lanes of a warp tend to hit
     // distinct shared-memory banks.
-    tmcs_stats &S = c->stats;
+    tmcs_stats S_meas{};
+    tmcs_stats &S = meas ? S_meas : c->stats;
     S = tmcs_stats{};
     auto pad4 = [&]() {
         while (P.args.size() % 4) P.args.push_back(0u);
@@ -535,6 +591,23 @@ int compile(tmcs_circuit *c, uint32_t flags) {
             push_layer(kind, uint32_t(e - b), off, 0, 0, true);
         }
     };
+    // single-fault enumeration over the whole op list: noise ops with p > 0
+    // in order, each target unit, Pauli index 1..K (K = 1, 1, 3, 15, 3 for
+    // X_ERROR, Z_ERROR, DEPOLARIZE1, DEPOLARIZE2, PAULI_CHANNEL_1)
+    std::vector<uint64_t> op_fault_base(c->ops.size(), 0);
+    {
+        uint64_t f = 0;
+        for (size_t i = 0; i < c->ops.size(); i++) {
+            const HostOp &op = c->ops[i];
+            op_fault_base[i] = f;
+            if (!is_noise(op.code) || !(op.p > 0.0)) continue;
+            const uint64_t units = op.code == TMCS_DEPOLARIZE2 ? op.nt / 2 : op.nt;
+            const uint64_t K = op.code == TMCS_DEPOLARIZE2 ? 15 : (op.code == TMCS_DEPOLARIZE1 ||
+                                                                   op.code == TMCS_PAULI_CHANNEL_1) ? 3 : 1;
+            f += units * K;
+        }
+        P.n_faults = f;
+    }
     // noise descriptors (program order) and their generation windows
     std::vector<uint32_t> noise_layer_desc(n_layers_body, 0xFFFFFFFFu);
     std::vector<uint32_t> desc_win_first, desc_win_count, desc_win_segs, desc_win_base;
@@ -560,6 +633,7 @@ int compile(tmcs_circuit *c, uint32_t flags) {
         }
         noise_layer_desc[l] = uint32_t(P.noise.size());
         P.noise.push_back(nd);
+        P.fault_base.push_back(op_fault_base[nz.op]);
         S.n_noise_ops++;
         S.n_noise_units += nd.n_units;
         S.n_noise_segments += nd.n_seg;
@@ -613,6 +687,39 @@ int compile(tmcs_circuit *c, uint32_t flags) {
             push_layer(L_NAPPLY, 1, 0, d, desc_win_base[d], false);
             break;
         }
+        case I_GAUGE: {
+            // 3 words per item: slot, op index, target index
+            const size_t per = kStageWords / 3;
+            for (size_t b0 = 0; b0 < ins.size(); b0 += per) {
+                const size_t e0 = std::min(ins.size(), b0 + per);
+                pad4();
+                const size_t off = P.args.size();
+                for (size_t e = b0; e < e0; e++) {
+                    const auto &g = gauges[ir[ins[e]].b];
+                    P.args.push_back(slot[ir[ins[e]].a]);
+                    P.args.push_back(g.first);
+                    P.args.push_back(g.second);
+                }
+                push_layer(L_GAUGE, uint32_t(e0 - b0), off, 0, 0, true);
+            }
+            break;
+        }
+        case I_REC: {
+            // 2 words per item: slot | reference bit << 31, record index
+            const size_t per = kStageWords / 2;
+            for (size_t b0 = 0; b0 < ins.size(); b0 += per) {
+                const size_t e0 = std::min(ins.size(), b0 + per);
+                pad4();
+                const size_t off = P.args.size();
+                for (size_t e = b0; e < e0; e++) {
+                    const uint32_t r = ir[ins[e]].b;
+                    P.args.push_back(slot[ir[ins[e]].a] | (uint32_t(c->ref_bits[r] & 1u) << 31));
+                    P.args.push_back(r);
+                }
+                push_layer(L_RECOUT, uint32_t(e0 - b0), off, 0, 0, true);
+            }
+            break;
+        }
         case I_DET:
         case I_OBS: {
             const bool det = layer_kind[l] == I_DET;
@@ -648,7 +755,7 @@ int compile(tmcs_circuit *c, uint32_t flags) {
         }
         }
     }
-    if (c->n_obs) {
+    if (c->n_obs && !meas) {
         std::vector<uint32_t> w;
         for (uint64_t o = 0; o < c->n_obs; o++) w.push_back(slot[acc[o]]);
         if (w.size() > kStageWords) return fail(TMCS_E_INVALID, "too many observables");
@@ -665,7 +772,7 @@ int compile(tmcs_circuit *c, uint32_t flags) {
     S.n_layers = P.layers.size();
     S.n_slots = n_slots;
     S.pruned_updates = pruned;
-    return validate_program(P, c->n_det, c->n_obs);
+    return validate_program(P, c->n_det, c->n_obs, c->n_meas);
 }
 
 // ------------------------------------------------------------- audit
@@ -851,6 +958,81 @@ struct Tableau {
 
 }  // namespace
 
+// Noiseless run of the circuit on the stabilizer tableau: the reference
+// measurement record (one byte per record, 0 or 1).
+int reference_record(const tmcs_circuit *c, std::vector<uint8_t> *out) {
+    try {
+        Tableau T(c->n_qubits);
+        std::vector<uint8_t> &rec = *out;
+        rec.clear();
+        rec.reserve(c->n_meas);
+        for (const HostOp &op : c->ops) {
+            const uint32_t *t = c->targets.data() + op.toff;
+            switch (op.code) {
+            case TMCS_R:
+                for (uint32_t a = 0; a < op.nt; a++)
+                    if (T.measure(t[a])) T.pauli_x(t[a]);
+                break;
+            case TMCS_RX:
+                for (uint32_t a = 0; a < op.nt; a++) {
+                    if (T.measure(t[a])) T.pauli_x(t[a]);
+                    T.h(t[a]);
+                }
+                break;
+            case TMCS_H:
+                for (uint32_t a = 0; a < op.nt; a++) T.h(t[a]);
+                break;
+            case TMCS_S:
+                for (uint32_t a = 0; a < op.nt; a++) T.s(t[a]);
+                break;
+            case TMCS_CX:
+                for (uint32_t a = 0; a + 1 < op.nt; a += 2) T.cx(t[a], t[a + 1]);
+                break;
+            case TMCS_M:
+                for (uint32_t a = 0; a < op.nt; a++) rec.push_back(uint8_t(T.measure(t[a])));
+                break;
+            case TMCS_MX:
+                for (uint32_t a = 0; a < op.nt; a++) {
+                    T.h(t[a]);
+                    rec.push_back(uint8_t(T.measure(t[a])));
+                    T.h(t[a]);
+                }
+                break;
+            case TMCS_XFEED:
+                for (uint32_t a = 0; a + 1 < op.nt; a += 2)
+                    if (rec[t[a]]) T.pauli_x(t[a + 1]);
+                break;
+            case TMCS_ZFEED:
+                for (uint32_t a = 0; a + 1 < op.nt; a += 2)
+                    if (rec[t[a]]) T.pauli_z(t[a + 1]);
+                break;
+            default:
+                break;
+            }
+        }
+    } catch (const std::bad_alloc &) {
+        return fail(TMCS_E_OOM, "out of host memory for the tableau");
+    }
+    return TMCS_OK;
+}
+
+// Builds, once, the program that emits raw measurement records: the
+// reference record is XORed into the sampled frame bits, and every reset and
+// measurement re-randomises the anticommuting frame component (gauge).
+int build_measurement_program(tmcs_circuit *c) {
+    if (c->meas_built) return TMCS_OK;
+    try {
+        int rc = reference_record(c, &c->ref_bits);
+        if (rc) return rc;
+        rc = compile(c, c->flags, true);
+        if (rc) return rc;
+    } catch (const std::bad_alloc &) {
+        return fail(TMCS_E_OOM, "out of host memory while compiling");
+    }
+    c->meas_built = true;
+    return TMCS_OK;
+}
+
 }  // namespace tmcs
 
 using namespace tmcs;
@@ -942,7 +1124,8 @@ int tmcs_circuit_build(const tmcs_op *ops, size_t n_ops, uint32_t flags, tmcs_ci
             int rc = audit(c);
             if (rc) { delete c; return rc; }
         }
-        int rc = compile(c, flags);
+        c->flags = flags;
+        int rc = compile(c, flags, false);
         if (rc) { delete c; return rc; }
     } catch (const std::bad_alloc &) {
         delete c;
@@ -971,6 +1154,12 @@ int tmcs_circuit_info(const tmcs_circuit *c, uint64_t *n_qubits, uint64_t *n_mea
     return TMCS_OK;
 }
 
+int tmcs_fault_count(const tmcs_circuit *c, uint64_t *n_faults) {
+    if (!c || !n_faults) return fail(TMCS_E_INVALID, "NULL argument");
+    *n_faults = c->prog.n_faults;
+    return TMCS_OK;
+}
+
 int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out) {
     if (!c || !out) return fail(TMCS_E_INVALID, "NULL argument");
     *out = c->stats;
@@ -979,60 +1168,12 @@ int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out) {
 
 int tmcs_reference_sample(const tmcs_circuit *c, uint8_t *meas_bits) {
     if (!c || (!meas_bits && c->n_meas)) return fail(TMCS_E_INVALID, "NULL argument");
-    try {
-        Tableau T(c->n_qubits);
-        std::vector<uint8_t> rec;
-        rec.reserve(c->n_meas);
-        for (const HostOp &op : c->ops) {
-            const uint32_t *t = c->targets.data() + op.toff;
-            switch (op.code) {
-            case TMCS_R:
-                for (uint32_t a = 0; a < op.nt; a++)
-                    if (T.measure(t[a])) T.pauli_x(t[a]);
-                break;
-            case TMCS_RX:
-                for (uint32_t a = 0; a < op.nt; a++) {
-                    if (T.measure(t[a])) T.pauli_x(t[a]);
-                    T.h(t[a]);
-                }
-                break;
-            case TMCS_H:
-                for (uint32_t a = 0; a < op.nt; a++) T.h(t[a]);
-                break;
-            case TMCS_S:
-                for (uint32_t a = 0; a < op.nt; a++) T.s(t[a]);
-                break;
-            case TMCS_CX:
-                for (uint32_t a = 0; a + 1 < op.nt; a += 2) T.cx(t[a], t[a + 1]);
-                break;
-            case TMCS_M:
-                for (uint32_t a = 0; a < op.nt; a++) rec.push_back(uint8_t(T.measure(t[a])));
-                break;
-            case TMCS_MX:
-                for (uint32_t a = 0; a < op.nt; a++) {
-                    T.h(t[a]);
-                    rec.push_back(uint8_t(T.measure(t[a])));
-                    T.h(t[a]);
-                }
-                break;
-            case TMCS_XFEED:
-                for (uint32_t a = 0; a + 1 < op.nt; a += 2)
-                    if (rec[t[a]]) T.pauli_x(t[a + 1]);
-                break;
-            case TMCS_ZFEED:
-                for (uint32_t a = 0; a + 1 < op.nt; a += 2)
-                    if (rec[t[a]]) T.pauli_z(t[a + 1]);
-                break;
-            default:
-                break;
-            }
-        }
-        std::memset(meas_bits, 0, (c->n_meas + 7) / 8);
-        for (size_t i = 0; i < rec.size(); i++)
-            if (rec[i]) meas_bits[i / 8] |= uint8_t(1u << (i % 8));
-    } catch (const std::bad_alloc &) {
-        return fail(TMCS_E_OOM, "out of host memory for the tableau");
-    }
+    std::vector<uint8_t> rec;
+    int rc = reference_record(c, &rec);
+    if (rc) return rc;
+    if (c->n_meas) std::memset(meas_bits, 0, (c->n_meas + 7) / 8);
+    for (size_t i = 0; i < rec.size(); i++)
+        if (rec[i]) meas_bits[i / 8] |= uint8_t(1u << (i % 8));
     return TMCS_OK;
 }
 

@@ -35,6 +35,8 @@ enum LayerKind : uint32_t {
                    // of record slots; detector ids aux .. aux+count-1
     L_OBS = 6,     // as L_DET; list[0] = accumulator slot, rest = record slots
     L_OBSOUT = 7,  // block[i] = accumulator slot of observable i (count = n_obs)
+    L_GAUGE = 8,   // block[3i..3i+2] = slot, op index, target: slot ^= gauge word
+    L_RECOUT = 9,  // block[2i..2i+1] = slot | reference bit << 31, record index
 };
 
 // A layer's arguments are one contiguous block args[off, off + nwords) that
@@ -86,9 +88,11 @@ struct Program {
     std::vector<uint32_t> args;
     std::vector<NoiseDesc> noise;
     std::vector<uint32_t> tables;   // kTableWords per distinct p (gap table + estimate constant)
+    std::vector<uint64_t> fault_base;  // per noise descriptor: index of its first single fault
     std::vector<double> table_p;
     uint32_t n_slots = 0;
     uint32_t max_window_segs = 0;  // event-buffer size in segments
+    uint64_t n_faults = 0;         // single faults of the whole op list (see tmcs_fault_count)
     uint64_t n_det = 0, n_obs = 0;
 };
 
@@ -101,6 +105,7 @@ struct DeviceProgram {
     const uint32_t *args = nullptr;
     const NoiseDesc *noise = nullptr;
     const uint32_t *tables = nullptr;
+    const uint64_t *fault_base = nullptr;
     int tuned_mode = 0;     // launch shape chosen by the autotuner (0: not tuned)
     int tuned_K = 0;
     int tuned_warps = 0;
@@ -129,6 +134,12 @@ struct tmcs_circuit {
     std::vector<uint32_t> targets;
     tmcs::Program prog;
     tmcs_stats stats{};
+    // raw-measurement program, built on first use (tmcs_sample_measurements)
+    tmcs::Program prog_meas;
+    std::vector<uint8_t> ref_bits;
+    bool meas_built = false;
+    uint32_t flags = 0;
+    mutable std::map<int, tmcs::DeviceProgram> dev_meas;
     mutable std::mutex mu;
     mutable std::map<int, tmcs::DeviceProgram> dev;
 };
@@ -138,7 +149,9 @@ namespace tmcs {
 // Host side (tmcs_host.cpp)
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
-int compile(tmcs_circuit *c, uint32_t flags);
+int compile(tmcs_circuit *c, uint32_t flags, bool meas);
+int reference_record(const tmcs_circuit *c, std::vector<uint8_t> *rec);
+int build_measurement_program(tmcs_circuit *c);
 int gap_table(double p, uint32_t *t);
 int audit(const tmcs_circuit *c);
 size_t program_bytes(const Program &p);

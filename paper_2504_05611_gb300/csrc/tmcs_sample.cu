@@ -82,6 +82,12 @@ struct KernelArgs {
     uint64_t last_mask;    // valid-shot mask of the last column
     uint64_t *det;
     uint64_t *obs;
+    // single-fault mode (tmcs_fault_signatures): noise ops inject one fault
+    // per lane instead of sampling; lane l of output column c carries fault
+    // fault_first + 64 c + l
+    const uint64_t *fault_base;
+    uint64_t fault_first;
+    uint32_t fault_mode;
 };
 
 // Buffered events of one (segment, chunk) of a noise op: up to kEvCap events
@@ -226,6 +232,27 @@ __device__ __forceinline__ void walk_segment(const NoiseDesc &nd, const uint32_t
     }
 }
 
+// Single-fault mode: every lane of the tile whose fault index falls in this
+// noise op's range gets exactly that fault (target unit, Pauli index 1..KP).
+template <int K>
+__device__ __forceinline__ void inject_faults(uint64_t *F, const KernelArgs &P, uint32_t desc, uint64_t col0,
+                                              int nvalid, uint32_t tid, uint32_t nthreads) {
+    const NoiseDesc nd = P.noise[desc];
+    const uint64_t fb = P.fault_base[desc];
+    const uint32_t KP = nd.kind == N_DEP2 ? 15u : (nd.kind == N_DEP1 || nd.kind == N_PC1) ? 3u : 1u;
+    const uint64_t fe = fb + uint64_t(nd.n_units) * KP;
+    const uint32_t *tg = P.args + nd.tgt_off;
+    for (uint32_t i = tid; i < uint32_t(nvalid) * 64u; i += nthreads) {
+        const int k = int(i / 64u);
+        const uint32_t lane = i % 64u;
+        const uint64_t f = P.fault_first + 64ull * (col0 + uint64_t(k)) + lane;
+        if (f < fb || f >= fe) continue;
+        const uint64_t idx = f - fb;
+        const uint32_t unit = uint32_t(idx / KP), pk = uint32_t(idx % KP) + 1u;
+        apply_event<K>(F, tg, nd.kind, unit / kSegUnits, int((unit % kSegUnits) * 64u + lane), pk, k);
+    }
+}
+
 // Runs the whole program for one tile of K chunks starting at output column col0.
 //
 // Update layers give each thread whole ops: an op's K chunk words of a slot
@@ -321,7 +348,7 @@ __device__ __forceinline__ void run_tile(const KernelArgs P, uint64_t *F, uint32
                 break;
             }
             case L_NGEN: {
-                const uint32_t units = ly.aux2 * K;
+                const uint32_t units = P.fault_mode ? 0u : ly.aux2 * K;
                 for (uint32_t u = tid; u < units; u += T_) {
                     const uint32_t ws = u / K;
                     const int k = int(u % K);
@@ -346,6 +373,10 @@ __device__ __forceinline__ void run_tile(const KernelArgs P, uint64_t *F, uint32
                 break;
             }
             case L_NAPPLY: {
+                if (P.fault_mode) {
+                    inject_faults<K>(F, P, ly.aux, col0, nvalid, tid, T_);
+                    break;
+                }
                 const NoiseDesc nd = P.noise[ly.aux];
                 const uint32_t *tg = P.args + nd.tgt_off;
                 const uint32_t items = nd.n_seg * K * kEvCap;
@@ -660,7 +691,7 @@ __device__ __forceinline__ void consumer_group(const KernelArgs &P, uint64_t *Fw
         case L_NGEN: {
             // walk the event streams of a window of upcoming noise ops into
             // the group's event buffer (one thread per (segment, chunk))
-            const uint32_t units = cur.aux2 * KW;
+            const uint32_t units = P.fault_mode ? 0u : cur.aux2 * KW;
             for (uint32_t u = gtid; u < units; u += GT) {
                 const uint32_t ws = u / KW;
                 const int k = int(u % KW);
@@ -687,6 +718,10 @@ __device__ __forceinline__ void consumer_group(const KernelArgs &P, uint64_t *Fw
         case L_NAPPLY: {
             // apply the buffered events of one op (one thread per event slot);
             // a walk that overflowed its buffer resumes here
+            if (P.fault_mode) {
+                inject_faults<KW>(Fw, P, cur.aux, col0, nvalid, gtid, GT);
+                break;
+            }
             const NoiseDesc nd = P.noise[cur.aux];
             const uint32_t *tg = P.args + nd.tgt_off;
             const uint32_t items = nd.n_seg * KW * kEvCap;
@@ -868,12 +903,14 @@ static int device_program(const tmcs_circuit *c, const DeviceProgram **out) {
     const size_t b_args = align256(P.args.size() * 4);
     const size_t b_noise = align256(P.noise.size() * sizeof(NoiseDesc));
     const size_t b_tables = align256(P.tables.size() * 4);
-    const size_t total = std::max<size_t>(b_layers + b_args + b_noise + b_tables, 256);
+    const size_t b_fault = align256(P.fault_base.size() * 8);
+    const size_t total = std::max<size_t>(b_layers + b_args + b_noise + b_tables + b_fault, 256);
     std::vector<uint8_t> host(total, 0);
     std::memcpy(host.data(), P.layers.data(), P.layers.size() * sizeof(Layer));
     std::memcpy(host.data() + b_layers, P.args.data(), P.args.size() * 4);
     std::memcpy(host.data() + b_layers + b_args, P.noise.data(), P.noise.size() * sizeof(NoiseDesc));
     std::memcpy(host.data() + b_layers + b_args + b_noise, P.tables.data(), P.tables.size() * 4);
+    std::memcpy(host.data() + b_layers + b_args + b_noise + b_tables, P.fault_base.data(), P.fault_base.size() * 8);
     void *base = nullptr;
     e = cudaMalloc(&base, total);
     if (e != cudaSuccess) {
@@ -894,6 +931,7 @@ static int device_program(const tmcs_circuit *c, const DeviceProgram **out) {
     dp.args = reinterpret_cast<const uint32_t *>(b + b_layers);
     dp.noise = reinterpret_cast<const NoiseDesc *>(b + b_layers + b_args);
     dp.tables = reinterpret_cast<const uint32_t *>(b + b_layers + b_args + b_noise);
+    dp.fault_base = reinterpret_cast<const uint64_t *>(b + b_layers + b_args + b_noise + b_tables);
     auto ins = c->dev.emplace(dev, dp);
     *out = &ins.first->second;
     return TMCS_OK;
@@ -1140,7 +1178,8 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
 }
 
 static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
-                        uint64_t *det, uint64_t *obs, void *stream) {
+                        uint64_t *det, uint64_t *obs, void *stream, bool fault_mode = false,
+                        uint64_t fault_first = 0) {
     if (!c) return fail(TMCS_E_INVALID, "circuit is NULL");
     if (shots == 0) return fail(TMCS_E_INVALID, "shots must be positive");
     if ((c->n_det && !det) || (c->n_obs && !obs)) return fail(TMCS_E_INVALID, "output buffer is NULL");
@@ -1187,7 +1226,10 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
     a.last_mask = (shots % 64) ? ((uint64_t(1) << (shots % 64)) - 1) : ~uint64_t(0);
     a.det = det;
     a.obs = obs;
-    if (!forced && env_int("TMCS_AUTOTUNE", 1) != 0) {
+    a.fault_base = dp->fault_base;
+    a.fault_first = fault_first;
+    a.fault_mode = fault_mode ? 1u : 0u;
+    if (!fault_mode && !forced && env_int("TMCS_AUTOTUNE", 1) != 0) {
         bool tuned;
         {
             std::lock_guard<std::mutex> lock(c->mu);
@@ -1498,6 +1540,15 @@ int tmcs_sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shot
 int tmcs_sample_noalloc(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
                         uint64_t *detector_bits, uint64_t *observable_bits, void *stream) {
     return sample_noalloc(c, first_chunk, shots, seed, detector_bits, observable_bits, stream);
+}
+
+int tmcs_fault_signatures(const tmcs_circuit *c, uint64_t first_fault, uint64_t n_faults, uint64_t *detector_bits,
+                          uint64_t *observable_bits, void *stream) {
+    if (!c) return fail(TMCS_E_INVALID, "circuit is NULL");
+    if (first_fault % 64) return fail(TMCS_E_INVALID, "first_fault must be a multiple of 64");
+    if (n_faults == 0 || first_fault + n_faults > c->prog.n_faults)
+        return fail(TMCS_E_INVALID, "fault range outside [0, tmcs_fault_count)");
+    return sample_range(c, 0, n_faults, 0, detector_bits, observable_bits, stream, true, first_fault);
 }
 
 int tmcs_check_device(void) {

@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
         L.tmcs_debug_gap_table.argtypes = [ctypes.c_double, P]
         L.tmcs_sample_noalloc.argtypes = [P, U64, U64, U64, P, P, P]
         L.tmcs_check_device.argtypes = []
+        L.tmcs_fault_count.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
+        L.tmcs_fault_signatures.argtypes = [P, U64, U64, P, P, P]
         L.tmcs_server_open.argtypes = [P, ctypes.POINTER(P)]
         L.tmcs_server_submit.argtypes = [P, P, U64, U64, ctypes.POINTER(ctypes.c_uint64)]
         L.tmcs_server_poll.argtypes = [P, U64, ctypes.POINTER(ctypes.c_int)]
@@ -105,7 +107,7 @@ def lib() -> ctypes.CDLL:
                   "tmcs_reference_sample", "tmcs_sample", "tmcs_sample_range", "tmcs_batch_sample",
                   "tmcs_debug_gap_table", "tmcs_check_device", "tmcs_sample_noalloc", "tmcs_server_open",
                   "tmcs_server_submit", "tmcs_server_poll", "tmcs_server_fetch", "tmcs_server_release",
-                  "tmcs_server_get_stats", "tmcs_server_close"):
+                  "tmcs_server_get_stats", "tmcs_server_close", "tmcs_fault_count", "tmcs_fault_signatures"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -172,6 +174,50 @@ def tmcs_reference_sample(handle: int) -> np.ndarray:
     buf = np.zeros(max((n + 7) // 8, 1), dtype=np.uint8)
     _check(lib().tmcs_reference_sample(ctypes.c_void_p(handle), buf.ctypes.data))
     return np.unpackbits(buf, bitorder="little")[:n]
+
+
+def tmcs_fault_count(handle: int) -> int:
+    n = ctypes.c_uint64()
+    _check(lib().tmcs_fault_count(ctypes.c_void_p(handle), ctypes.byref(n)))
+    return n.value
+
+
+def tmcs_fault_signatures(handle: int, first_fault: int, n_faults: int, det, obs, stream=None) -> None:
+    info = tmcs_circuit_info(handle)
+    cols = (n_faults + 63) // 64
+    _check_size(det, info["n_det"], cols, "detector")
+    _check_size(obs, info["n_obs"], cols, "observable")
+    _check(lib().tmcs_fault_signatures(ctypes.c_void_p(handle), first_fault, n_faults, _dev_ptr(det),
+                                       _dev_ptr(obs), _stream_ptr(stream)))
+
+
+def dem_columns(sampler: "Sampler", slice_faults: int = 1 << 20):
+    """Distinct non-empty (detector set, observable set) signatures of all
+    single faults, from tmcs_fault_signatures on the GPU; returns them as a
+    set of (detector bytes, observable bytes) keys."""
+    import torch
+    n = tmcs_fault_count(sampler.handle)
+    info = sampler.info
+    out = set()
+    zero_d = bytes((info["n_det"] + 7) // 8)
+    zero_o = bytes((info["n_obs"] + 7) // 8)
+    for f0 in range(0, n, slice_faults):
+        m = min(slice_faults, n - f0)
+        cols = (m + 63) // 64
+        det = torch.empty((info["n_det"], cols), dtype=torch.int64, device="cuda")
+        obs = torch.empty((max(info["n_obs"], 1), cols), dtype=torch.int64, device="cuda")
+        tmcs_fault_signatures(sampler.handle, f0, m, det, obs if info["n_obs"] else None)
+        d = np.unpackbits(det.cpu().numpy().view(np.uint8).reshape(info["n_det"], -1), axis=1,
+                          bitorder="little")[:, :m]
+        o = np.unpackbits(obs.cpu().numpy().view(np.uint8).reshape(max(info["n_obs"], 1), -1), axis=1,
+                          bitorder="little")[: info["n_obs"], :m]
+        dp = np.packbits(d.T, axis=1, bitorder="little")
+        op = np.packbits(o.T, axis=1, bitorder="little") if info["n_obs"] else np.zeros((m, 0), np.uint8)
+        for a, b in zip(dp, op):
+            ka, kb = a.tobytes(), b.tobytes()
+            if ka != zero_d or kb != zero_o:
+                out.add((ka, kb))
+    return out
 
 
 def tmcs_check_device() -> None:

@@ -125,3 +125,17 @@ def test_random_circuits_compile_and_validate(tmcs, trial):
     for flags in (0, tmcs.TMCS_FLAG_NO_PRUNE):
         h = tmcs.tmcs_circuit_build(c, flags)
         tmcs.tmcs_circuit_free(h)
+
+
+@pytest.mark.parametrize("kind", ["nl", "teleport"])
+def test_fault_count_matches_oracle_enumeration(tmcs, kind):
+    """The library's single-fault enumeration has the oracle DEM's length."""
+    from oracle import dem
+    nz = C.NoiseModel(1e-3, 1e-2, decoherence=C.Decoherence(1e-3, schedule="lines"))
+    fn = C.nonlocal_cnot_circuit if kind == "nl" else C.teleport_circuit
+    c = fn(C.code_by_name("sc3"), 2, 2, nz)
+    h = tmcs.tmcs_circuit_build(c)
+    try:
+        assert tmcs.tmcs_fault_count(h) == len(dem.fault_list(c))
+    finally:
+        tmcs.tmcs_circuit_free(h)
