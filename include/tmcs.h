@@ -200,6 +200,29 @@ int tmcs_sample_noalloc(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
  * 64. Errors: TMCS_E_INVALID (range), as tmcs_sample otherwise.
  */
 int tmcs_fault_count(const tmcs_circuit *c, uint64_t *n_faults);
+
+/*
+ * Raw measurement records of noisy executions (Methods "Decoding": detector
+ * values are parities of the measurement outcomes of one noisy run; this
+ * returns the outcomes themselves). Shots 64*first_chunk .. +shots-1 of the
+ * stream `seed`: the noise draws are those of tmcs_sample_range with the same
+ * arguments, so every detector parity of these records, XORed with its value
+ * on the reference record (tmcs_reference_sample), equals that call's
+ * detector bit. Record i of a shot is reference bit XOR frame flip, where the
+ * frame also carries a random gauge Pauli after every reset and measurement
+ * (Z after R/M, X after RX/MX, Z on every qubit at the start): that leaves
+ * the state unchanged but turns each non-deterministic outcome into a fair
+ * coin. Gauge word of (op i, target u, chunk c): Philox4x32-10 with the
+ * sampling key at counter (u/2, c, i, 2^31), words 0|1<<32 for even u, 2|3<<32
+ * for odd u; the start uses op index n_ops and u = qubit.
+ * meas_bits: device, n_meas * ceil(shots/64) uint64, 8-byte aligned; word j of
+ * row i holds record i of shots 64(first_chunk+j) .. +63, bits past `shots` 0.
+ * The first call per circuit builds a second compiled program on the host
+ * (reference tableau run plus compile) and uploads it; asynchronous after
+ * that. Errors: as tmcs_sample_range.
+ */
+int tmcs_sample_measurements(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
+                             uint64_t *meas_bits, void *stream);
 int tmcs_fault_signatures(const tmcs_circuit *c, uint64_t first_fault, uint64_t n_faults, uint64_t *detector_bits,
                           uint64_t *observable_bits, void *stream);
 

@@ -466,6 +466,39 @@ __device__ __forceinline__ void run_tile(const KernelArgs P, uint64_t *F, uint32
                 }
                 break;
             }
+            case L_GAUGE: {
+                // slot ^= gauge word of (op, target u, chunk): Philox at
+                // counter (u / 2, chunk, op, 2^31); even u takes w0 | w1 << 32,
+                // odd u takes w2 | w3 << 32
+                const uint32_t n = ly.count * K;
+                for (uint32_t i = tid; i < n; i += T_) {
+                    const uint32_t g = i / K;
+                    const int k = int(i % K);
+                    if (k >= nvalid) continue;
+                    const uint32_t slot = st[3 * g], op = st[3 * g + 1], u = st[3 * g + 2];
+                    const uint4 w = philox4x32_10(u >> 1, chunk0 + uint32_t(k), op, 0x80000000u, P.key0, P.key1);
+                    const uint64_t word = (u & 1u) ? (uint64_t(w.z) | (uint64_t(w.w) << 32))
+                                                   : (uint64_t(w.x) | (uint64_t(w.y) << 32));
+                    F[slot * K + k] ^= word;
+                }
+                break;
+            }
+            case L_RECOUT: {
+                // record r = reference bit XOR frame bit, one row per record
+                const uint32_t n = ly.count * K;
+                for (uint32_t i = tid; i < n; i += T_) {
+                    const uint32_t g = i / K;
+                    const int k = int(i % K);
+                    if (k >= nvalid) continue;
+                    const uint32_t w0 = st[2 * g], r = st[2 * g + 1];
+                    uint64_t v = F[(w0 & 0x7FFFFFFFu) * K + k];
+                    if (w0 >> 31) v = ~v;
+                    const uint64_t col = col0 + uint64_t(k);
+                    if (col == P.n_cols - 1) v &= P.last_mask;
+                    P.det[uint64_t(r) * P.n_cols + col] = v;
+                }
+                break;
+            }
             default:
                 break;
             }
@@ -887,18 +920,19 @@ static int cuda_fail(cudaError_t e, const char *what) {
 
 static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
-// Upload (once per device) and return the device copy of a program.
-static int device_program(const tmcs_circuit *c, const DeviceProgram **out) {
+// Upload (once per device) and return the device copy of a program; map is
+// the circuit's per-device copies of that program.
+static int upload_program(const tmcs_circuit *c, const Program &P, std::map<int, DeviceProgram> &map,
+                          const DeviceProgram **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     std::lock_guard<std::mutex> lock(c->mu);
-    auto it = c->dev.find(dev);
-    if (it != c->dev.end()) {
+    auto it = map.find(dev);
+    if (it != map.end()) {
         *out = &it->second;
         return TMCS_OK;
     }
-    const Program &P = c->prog;
     const size_t b_layers = align256(P.layers.size() * sizeof(Layer));
     const size_t b_args = align256(P.args.size() * 4);
     const size_t b_noise = align256(P.noise.size() * sizeof(NoiseDesc));
@@ -932,21 +966,27 @@ static int device_program(const tmcs_circuit *c, const DeviceProgram **out) {
     dp.noise = reinterpret_cast<const NoiseDesc *>(b + b_layers + b_args);
     dp.tables = reinterpret_cast<const uint32_t *>(b + b_layers + b_args + b_noise);
     dp.fault_base = reinterpret_cast<const uint64_t *>(b + b_layers + b_args + b_noise + b_tables);
-    auto ins = c->dev.emplace(dev, dp);
+    auto ins = map.emplace(dev, dp);
     *out = &ins.first->second;
     return TMCS_OK;
+}
+
+static int device_program(const tmcs_circuit *c, const DeviceProgram **out) {
+    return upload_program(c, c->prog, c->dev, out);
 }
 
 void free_device_programs(tmcs_circuit *c) {
     std::lock_guard<std::mutex> lock(c->mu);
     int cur = 0;
     cudaGetDevice(&cur);
-    for (auto &kv : c->dev) {
-        cudaSetDevice(kv.first);
-        cudaFree(kv.second.base);
+    for (auto *m : {&c->dev, &c->dev_meas}) {
+        for (auto &kv : *m) {
+            cudaSetDevice(kv.first);
+            cudaFree(kv.second.base);
+        }
+        m->clear();
     }
     cudaSetDevice(cur);
-    c->dev.clear();
     cudaGetLastError();
 }
 
@@ -1030,6 +1070,8 @@ static LaunchShape make_shape_w(const Program &P, uint64_t n_cols, int KW, int W
     return s;
 }
 
+static LaunchShape choose_shape_cta(const Program &P, uint64_t n_cols, const DeviceLimits &lim);
+
 static LaunchShape choose_shape(const Program &P, uint64_t n_cols, const DeviceLimits &lim) {
     const int mode = env_int("TMCS_KERNEL", 0);
     const int kcap = env_int("TMCS_TILE_K", 0);
@@ -1043,6 +1085,12 @@ static LaunchShape choose_shape(const Program &P, uint64_t n_cols, const DeviceL
         if (W >= 1) return make_shape_w(P, n_cols, KW, W, G);
         // frames of even one group do not fit next to the ring: use mode 3
     }
+    return choose_shape_cta(P, n_cols, lim);
+}
+
+// CTA-wide kernel shape (mode 3) from the shared-memory and grid heuristics.
+static LaunchShape choose_shape_cta(const Program &P, uint64_t n_cols, const DeviceLimits &lim) {
+    const int kcap = env_int("TMCS_TILE_K", 0);
     int K = 16;
     if (kcap > 0)
         while (K > 1 && K > kcap) K >>= 1;
@@ -1243,6 +1291,58 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
         }
     }
     cudaError_t e = launch(a, s, st);
+    if (e != cudaSuccess) return cuda_fail(e, "frame kernel launch");
+    return TMCS_OK;
+}
+
+// ---- raw measurement records
+
+// Same noise draws as sample_range (noise ops keep their op indices), plus the
+// gauge words; records land in meas (n_meas rows of n_cols words). Always the
+// CTA-wide kernel: the warp-owned kernel does not run gauge/record layers.
+static int sample_measurements(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
+                               uint64_t *meas, void *stream) {
+    if (!c) return fail(TMCS_E_INVALID, "circuit is NULL");
+    if (shots == 0) return fail(TMCS_E_INVALID, "shots must be positive");
+    if (c->n_meas && !meas) return fail(TMCS_E_INVALID, "output buffer is NULL");
+    if (reinterpret_cast<uintptr_t>(meas) & 7) return fail(TMCS_E_BUFFER, "output buffer must be 8-byte aligned");
+    const uint64_t n_cols = (shots + 63) / 64;
+    if (first_chunk + n_cols > (uint64_t(1) << 32)) return fail(TMCS_E_INVALID, "chunk range beyond 2^32");
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        int rc = build_measurement_program(const_cast<tmcs_circuit *>(c));
+        if (rc) return rc;
+    }
+    const Program &P = c->prog_meas;
+    const DeviceProgram *dp = nullptr;
+    int rc = upload_program(c, P, c->dev_meas, &dp);
+    if (rc) return rc;
+    DeviceLimits lim;
+    if ((rc = device_limits(&lim))) return rc;
+    if (kernel_smem_bytes(P.n_slots, P.max_window_segs, 1) > lim.smem_optin)
+        return fail(TMCS_E_INVALID, "circuit needs " + std::to_string(P.n_slots) +
+                                        " frame slots; one 64-shot chunk does not fit in shared memory");
+    if (P.layers.empty()) return TMCS_OK;
+    uint32_t *status = device_status_word(dp->device);
+    if (!status) return fail(TMCS_E_OOM, "cannot allocate the device status word");
+    KernelArgs a{};
+    a.layers = dp->layers;
+    a.args = dp->args;
+    a.noise = dp->noise;
+    a.tables = dp->tables;
+    a.status = status;
+    a.n_layers = uint32_t(P.layers.size());
+    a.n_slots = P.n_slots;
+    a.max_window_segs = P.max_window_segs;
+    a.key0 = uint32_t(seed);
+    a.key1 = uint32_t(seed >> 32);
+    a.first_chunk = uint32_t(first_chunk);
+    a.n_cols = n_cols;
+    a.last_mask = (shots % 64) ? ((uint64_t(1) << (shots % 64)) - 1) : ~uint64_t(0);
+    a.det = meas;
+    a.obs = nullptr;
+    a.fault_base = dp->fault_base;
+    cudaError_t e = launch(a, choose_shape_cta(P, n_cols, lim), static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "frame kernel launch");
     return TMCS_OK;
 }
@@ -1540,6 +1640,11 @@ int tmcs_sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shot
 int tmcs_sample_noalloc(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
                         uint64_t *detector_bits, uint64_t *observable_bits, void *stream) {
     return sample_noalloc(c, first_chunk, shots, seed, detector_bits, observable_bits, stream);
+}
+
+int tmcs_sample_measurements(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
+                             uint64_t *meas_bits, void *stream) {
+    return sample_measurements(c, first_chunk, shots, seed, meas_bits, stream);
 }
 
 int tmcs_fault_signatures(const tmcs_circuit *c, uint64_t first_fault, uint64_t n_faults, uint64_t *detector_bits,

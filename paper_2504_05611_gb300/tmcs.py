@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
         L.tmcs_check_device.argtypes = []
         L.tmcs_fault_count.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
         L.tmcs_fault_signatures.argtypes = [P, U64, U64, P, P, P]
+        L.tmcs_sample_measurements.argtypes = [P, U64, U64, U64, P, P]
         L.tmcs_server_open.argtypes = [P, ctypes.POINTER(P)]
         L.tmcs_server_submit.argtypes = [P, P, U64, U64, ctypes.POINTER(ctypes.c_uint64)]
         L.tmcs_server_poll.argtypes = [P, U64, ctypes.POINTER(ctypes.c_int)]
@@ -107,7 +108,8 @@ def lib() -> ctypes.CDLL:
                   "tmcs_reference_sample", "tmcs_sample", "tmcs_sample_range", "tmcs_batch_sample",
                   "tmcs_debug_gap_table", "tmcs_check_device", "tmcs_sample_noalloc", "tmcs_server_open",
                   "tmcs_server_submit", "tmcs_server_poll", "tmcs_server_fetch", "tmcs_server_release",
-                  "tmcs_server_get_stats", "tmcs_server_close", "tmcs_fault_count", "tmcs_fault_signatures"):
+                  "tmcs_server_get_stats", "tmcs_server_close", "tmcs_fault_count", "tmcs_fault_signatures",
+                  "tmcs_sample_measurements"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -291,6 +293,17 @@ def tmcs_sample_noalloc(handle: int, first_chunk: int, shots: int, seed: int, de
     _check_size(obs, info["n_obs"], cols, "observable")
     _check(lib().tmcs_sample_noalloc(ctypes.c_void_p(handle), first_chunk, shots, seed & (2 ** 64 - 1),
                                      _dev_ptr(det), _dev_ptr(obs), _stream_ptr(stream)))
+
+
+def tmcs_sample_measurements(handle: int, first_chunk: int, shots: int, seed: int, meas, stream=None) -> None:
+    """Raw measurement records (n_meas rows of ceil(shots/64) words), same
+    noise draws as tmcs_sample_range with these arguments plus gauge Paulis
+    that make non-deterministic outcomes fair coins (see include/tmcs.h)."""
+    info = tmcs_circuit_info(handle)
+    cols = (shots + 63) // 64
+    _check_size(meas, info["n_meas"], cols, "measurement")
+    _check(lib().tmcs_sample_measurements(ctypes.c_void_p(handle), first_chunk, shots, seed & (2 ** 64 - 1),
+                                          _dev_ptr(meas), _stream_ptr(stream)))
 
 
 def tmcs_batch_sample(jobs: Sequence[Tuple[int, int, int, object, object]], stream=None) -> None:

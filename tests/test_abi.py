@@ -139,3 +139,29 @@ def test_fault_count_matches_oracle_enumeration(tmcs, kind):
         assert tmcs.tmcs_fault_count(h) == len(dem.fault_list(c))
     finally:
         tmcs.tmcs_circuit_free(h)
+
+
+@pytest.mark.parametrize("kind", ["nl_sc5", "tp_bb18", "ps4_sc3", "random"])
+def test_measurement_program_compiles_and_validates(tmcs, kind):
+    """tmcs_sample_measurements builds its gauge/record program on the host
+    (reference tableau, compile, program check) before any CUDA call; without
+    a GPU it must then stop at the first CUDA call, not in the program check."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only check")
+    if kind == "nl_sc5":
+        c = C.nonlocal_cnot_circuit(C.code_by_name("sc5"), 2, 2, C.NoiseModel(0.001, 0.01))
+    elif kind == "tp_bb18":
+        c = C.teleport_circuit(C.code_by_name("bb18"), 1, 1, C.NoiseModel(0.001, 0.01))
+    elif kind == "ps4_sc3":
+        c = C.pauli_string_circuit(C.code_by_name("sc3"), 4, rounds_before=1, noise=C.NoiseModel(0.003, 0.02))
+    else:
+        from circuit_gen import random_noisy_circuit
+        c = random_noisy_circuit(np.random.default_rng(5), 6, 30)
+    h = tmcs.tmcs_circuit_build(c)
+    try:
+        rc = tmcs.lib().tmcs_sample_measurements(h, 0, 64, 1, 4096, None)
+        assert rc == 4, tmcs.tmcs_last_error()
+        assert "program check" not in tmcs.tmcs_last_error()
+    finally:
+        tmcs.tmcs_circuit_free(h)
