@@ -124,6 +124,14 @@ typedef struct {
     uint64_t n_parity_terms;  /* record reads of detectors and observables */
     uint64_t live_components; /* x/z components kept by pruning (of 2 * updates) */
     uint64_t pruned_updates;  /* slot updates removed by pruning */
+    /* event-signature program (see tmcs_fault_outputs) */
+    uint64_t sig_ok;          /* 1 if the signature sampler can run this circuit */
+    uint64_t sig_window;      /* detector ring size (words per chunk) */
+    uint64_t sig_steps;       /* flush steps */
+    uint64_t sig_items;       /* noise segments walked per chunk */
+    uint64_t sig_generators;  /* X/Z generators of all noise units */
+    uint64_t sig_entries;     /* (generator, output) pairs */
+    uint64_t sig_build_us;    /* host time to build it, microseconds */
 } tmcs_stats;
 int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out);
 
@@ -200,6 +208,19 @@ int tmcs_sample_noalloc(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
  * 64. Errors: TMCS_E_INVALID (range), as tmcs_sample otherwise.
  */
 int tmcs_fault_count(const tmcs_circuit *c, uint64_t *n_faults);
+
+/*
+ * Outputs flipped by elementary fault `fault` (enumeration of
+ * tmcs_fault_count), from the host event-signature table: detector indices,
+ * then 0x80000000 | observable index, ascending. The table holds, per noise
+ * unit, the outputs flipped by X and by Z on each of its qubits (DEM columns,
+ * Methods "Decoding"), found by running the transposed frame maps backwards
+ * over the op list; the signature sampler XORs these lists per event.
+ * out: host, cap entries; *n_out = number of outputs (may exceed cap, then
+ * only cap are written). Errors: TMCS_E_INVALID (fault out of range, no
+ * table: sig_ok = 0 in tmcs_circuit_stats).
+ */
+int tmcs_fault_outputs(const tmcs_circuit *c, uint64_t fault, uint32_t *out, uint32_t cap, uint32_t *n_out);
 
 /*
  * Raw measurement records of noisy executions (Methods "Decoding": detector

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -1127,6 +1128,10 @@ int tmcs_circuit_build(const tmcs_op *ops, size_t n_ops, uint32_t flags, tmcs_ci
         c->flags = flags;
         int rc = compile(c, flags, false);
         if (rc) { delete c; return rc; }
+        const char *wenv = std::getenv("TMCS_SIG_WINDOW");
+        const uint32_t max_window = (wenv && *wenv) ? uint32_t(std::atoi(wenv)) : 8192u;
+        rc = build_signature_program(c, max_window);
+        if (rc) { delete c; return rc; }
     } catch (const std::bad_alloc &) {
         delete c;
         return fail(TMCS_E_OOM, "out of host memory while compiling");
@@ -1163,7 +1168,50 @@ int tmcs_fault_count(const tmcs_circuit *c, uint64_t *n_faults) {
 int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out) {
     if (!c || !out) return fail(TMCS_E_INVALID, "NULL argument");
     *out = c->stats;
+    const SigProgram &G = c->sig;
+    out->sig_ok = G.ok ? 1 : 0;
+    out->sig_window = G.window;
+    out->sig_steps = G.steps.size();
+    out->sig_items = G.items.size() / 2;
+    out->sig_generators = G.gen_off.empty() ? 0 : G.gen_off.size() - 1;
+    out->sig_entries = G.gen_ent.size();
+    out->sig_build_us = uint64_t(G.build_seconds * 1e6);
     return TMCS_OK;
+}
+
+int tmcs_fault_outputs(const tmcs_circuit *c, uint64_t fault, uint32_t *out, uint32_t cap, uint32_t *n_out) {
+    if (!c || !n_out || (cap && !out)) return fail(TMCS_E_INVALID, "NULL argument");
+    const SigProgram &G = c->sig;
+    if (!G.ok) return fail(TMCS_E_INVALID, "no event-signature table: " + G.why);
+    uint64_t f = fault;
+    for (const NoiseDesc &nd : G.noise) {
+        const uint64_t KP = nd.kind == N_DEP2 ? 15 : (nd.kind == N_DEP1 || nd.kind == N_PC1) ? 3 : 1;
+        const uint64_t nf = uint64_t(nd.n_units) * KP;
+        if (f >= nf) {
+            f -= nf;
+            continue;
+        }
+        const uint32_t unit = uint32_t(f / KP), pk = uint32_t(f % KP) + 1u;
+        const uint32_t mask = sig_mask(nd.kind, pk), ng = sig_gens(nd.kind);
+        std::vector<uint32_t> v;
+        for (uint32_t g = 0; g < ng; g++)
+            if (mask >> g & 1u) {
+                const uint32_t id = nd.tgt_off + unit * ng + g;
+                v.insert(v.end(), G.gen_ent.begin() + G.gen_off[id], G.gen_ent.begin() + G.gen_off[id + 1]);
+            }
+        std::sort(v.begin(), v.end());
+        std::vector<uint32_t> w;  // XOR: drop pairs
+        for (size_t i = 0; i < v.size();) {
+            size_t j = i;
+            while (j < v.size() && v[j] == v[i]) j++;
+            if ((j - i) & 1) w.push_back(v[i]);
+            i = j;
+        }
+        *n_out = uint32_t(w.size());
+        for (size_t i = 0; i < w.size() && i < cap; i++) out[i] = w[i];
+        return TMCS_OK;
+    }
+    return fail(TMCS_E_INVALID, "fault index out of range");
 }
 
 int tmcs_reference_sample(const tmcs_circuit *c, uint8_t *meas_bits) {

@@ -96,6 +96,8 @@ struct Program {
     uint64_t n_det = 0, n_obs = 0;
 };
 
+struct SigStep;
+
 // One device copy of a program.
 struct DeviceProgram {
     int device = -1;
@@ -113,9 +115,78 @@ struct DeviceProgram {
     int tuned_threads = 0;
 };
 
+// One device copy of an event-signature program.
+struct DeviceSig {
+    int device = -1;
+    void *base = nullptr;
+    size_t bytes = 0;
+    const NoiseDesc *noise = nullptr;
+    const uint32_t *tables = nullptr;
+    const uint32_t *items = nullptr;
+    const SigStep *steps = nullptr;
+    const uint32_t *unit_ent = nullptr;
+};
+
 // Per-device scratch of the library: a status word that kernels set when a
 // bounded wait expires (read and cleared by tmcs_check_device).
 uint32_t *device_status_word(int device);
+
+// ------------------------------------------------- event-signature program
+//
+// Detector and observable flips are GF(2)-linear in the noise events, so a
+// fixed circuit can also be sampled without running its Clifford layers per
+// shot: every noise unit has up to four generators (X and Z on each of its
+// qubits), each with the list of outputs it flips (its signature); an event
+// with Pauli index k flips the XOR of the lists of the generators in k. The
+// lists come from one transposed frame pass per group of 64 outputs (host),
+// and the kernel walks the same noise streams as the frame program and XORs
+// each event's lists into a shared-memory ring of detector words.
+//
+// Items are the noise segments that flip anything, in op order; steps are
+// runs of items whose detectors fit in the ring (window) above the step's
+// flush point. After step s, detectors [flush_lo, flush_hi) are final and are
+// written out; every detector is written by exactly one step.
+struct SigStep {
+    uint32_t item_begin, item_end;
+    uint32_t flush_lo, flush_hi;
+};
+
+constexpr uint32_t kSigObsFlag = 0x80000000u;  // entry = observable index | flag
+
+struct SigProgram {
+    bool ok = false;
+    std::string why;                 // reason the program is unusable (ok = false)
+    uint32_t window = 0;             // ring size in detectors (power of two)
+    std::vector<NoiseDesc> noise;    // every noise op with p > 0; tgt_off = first generator id
+                                     // (host); the device copy carries unit_base there
+    std::vector<uint32_t> tables;    // kTableWords per distinct p
+    std::vector<uint32_t> items;     // (descriptor, segment) pairs, 2 words per item
+    std::vector<SigStep> steps;
+    std::vector<uint32_t> gen_off;   // CSR offsets per generator (n_gens + 1)
+    std::vector<uint32_t> gen_ent;   // detector index, or kSigObsFlag | observable index
+    // Device layout: a slot of slot_words (8 or 16) words per noise unit,
+    // global unit index = descriptor's unit_base + unit: word 0 = entry count
+    // n; n < slot_words: entries in words 1..n; else word 1 = offset of the n
+    // entries in the overflow area that follows the slots. An entry is
+    // generator << 30 | observable flag << 29 | output index.
+    std::vector<uint32_t> unit_base;  // per descriptor: first global unit index
+    std::vector<uint32_t> unit_ent;
+    uint32_t slot_words = 8;
+    double build_seconds = 0;
+};
+
+// Generators of a noise unit: DEPOLARIZE2 has X, Z on its first qubit then X,
+// Z on its second; the single-qubit kinds have X, Z.
+#ifdef __CUDACC__
+#define TMCS_HD __host__ __device__
+#else
+#define TMCS_HD
+#endif
+TMCS_HD inline uint32_t sig_gens(uint32_t kind) { return kind == 3u ? 4u : 2u; }
+// Generator mask of Pauli index pk (bit 0 = X part, bit 1 = Z part per qubit).
+TMCS_HD inline uint32_t sig_mask(uint32_t kind, uint32_t pk) {
+    return kind == 3u ? ((pk >> 2) | ((pk & 3u) << 2)) : kind == 0u ? 1u : kind == 1u ? 2u : pk;
+}
 
 // Host-side copy of one user op.
 struct HostOp {
@@ -140,6 +211,9 @@ struct tmcs_circuit {
     bool meas_built = false;
     uint32_t flags = 0;
     mutable std::map<int, tmcs::DeviceProgram> dev_meas;
+    // event-signature program (built with the circuit; ok = false if unusable)
+    tmcs::SigProgram sig;
+    mutable std::map<int, tmcs::DeviceSig> dev_sig;
     mutable std::mutex mu;
     mutable std::map<int, tmcs::DeviceProgram> dev;
 };
@@ -155,6 +229,8 @@ int build_measurement_program(tmcs_circuit *c);
 int gap_table(double p, uint32_t *t);
 int audit(const tmcs_circuit *c);
 size_t program_bytes(const Program &p);
+int build_signature_program(tmcs_circuit *c, uint32_t max_window);
+int table_for_p(std::vector<uint32_t> &tables, std::vector<double> &table_p, double p, uint32_t *out);
 
 // Device side (tmcs_sample.cu)
 void free_device_programs(tmcs_circuit *c);

@@ -66,6 +66,18 @@ __device__ __forceinline__ int gap_count(const uint32_t *__restrict__ T, float i
     return g;
 }
 
+// gap_count on a table in shared memory (SMT) or global memory.
+template <bool SMT>
+__device__ __forceinline__ int gap_count_t(const uint32_t *__restrict__ T, float inv_log2, uint32_t w) {
+    if constexpr (!SMT) return gap_count(T, inv_log2, w);
+    const float lg = __log2f(__uint2float_rn(w) + 1.0f) - 32.0f;
+    const float est = lg * inv_log2;
+    int g = est >= float(kGapLen) ? int(kGapLen) : (est > 0.0f ? int(est) : 0);
+    while (g < int(kGapLen) && w < T[g]) g++;
+    while (g > 0 && w >= T[g - 1]) g--;
+    return g;
+}
+
 struct KernelArgs {
     const Layer *layers;
     const uint32_t *args;
@@ -540,6 +552,301 @@ __global__ void __launch_bounds__(512) frame_kernel(const KernelArgs P) {
 }
 
 // ---------------------------------------------------------------------------
+// Event-signature kernel: samples the same noise streams as the frame kernels
+// and, instead of running the Clifford layers, XORs each event's precomputed
+// output list (the XOR of its generators' lists) into a shared-memory ring of
+// detector words. Bit-identical to the frame kernels because detector flips
+// are linear in the events (see tmcs_signature.cpp).
+//
+// A CTA owns K chunks at a time (persistent over tiles). Per step it walks
+// the step's (segment, chunk) streams, one per thread, applying events with
+// 32-bit shared atomics (lanes 0-31 in the low word, 32-63 in the high word),
+// then writes and clears the detectors that the step finalised. Observables
+// accumulate in a small array written once per tile.
+
+struct SigArgs {
+    const NoiseDesc *noise;   // tgt_off = first global unit index of the descriptor
+    const uint32_t *tables;
+    const uint2 *items;       // (descriptor, segment)
+    const uint4 *steps;       // SigStep: item_begin, item_end, flush_lo, flush_hi
+    const uint32_t *unit_ent; // slot_words words per global unit (count, entries), then overflow
+    uint32_t n_steps;
+    uint32_t window_mask;     // ring size - 1 (power of two)
+    uint32_t n_obs;
+    uint32_t queue_cap;       // events the shared queue holds
+    uint32_t smem_tables;     // gap tables copied to shared memory (0, or all of them)
+    uint32_t slot_words;      // 8 or 16
+    uint32_t key0, key1;
+    uint32_t first_chunk;
+    uint64_t n_cols, last_mask, n_tiles;
+    uint64_t *det;
+    uint64_t *obs;
+};
+
+// Draws of one (segment, chunk) stream from its start; sink(pos, pauli) per
+// event, in stream order (the sampling specification's walk).
+template <class Sink>
+__device__ __forceinline__ void walk_stream(const NoiseDesc &nd, const uint32_t *__restrict__ T, float inv,
+                                            uint32_t s, uint32_t chunk, uint32_t key0, uint32_t key1,
+                                            Sink &&sink) {
+    const int n_trials = 64 * int(min(kSegUnits, nd.n_units - s * kSegUnits));
+    const uint32_t npauli = npauli_of(nd.kind);
+    int pos = -1;
+    uint4 w = make_uint4(0, 0, 0, 0);
+    for (uint32_t d = 0;; d++) {
+        if ((d & 1u) == 0) w = philox4x32_10(d >> 1, chunk, nd.op_index, s, key0, key1);
+        const uint32_t wg = (d & 1u) ? w.z : w.x;
+        const uint32_t wp = (d & 1u) ? w.w : w.y;
+        pos += 1 + gap_count(T, inv, wg);
+        if (pos >= n_trials) break;
+        sink(pos, pauli_index(nd, npauli, wp));
+    }
+}
+
+// Queued events: global unit index (low word), and lane | chunk k << 6 |
+// Pauli index << 9 | noise kind << 13 (high word). A thread applies up to N
+// at once; each event's data is the first 32 bytes of its unit's slot (the
+// count and up to 7 entries), all N loaded before any is used so their
+// latencies overlap. Longer units read the rest of the slot (16-word slots)
+// or their overflow list.
+template <int N>
+__device__ __forceinline__ void sig_apply_events(const SigArgs &A, const uint64_t (&q)[N], int n, uint64_t *ring,
+                                                 uint64_t *oacc, int K) {
+    uint4 v0[N], v1[N];
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        if (j < n) {
+            const uint4 *sl = reinterpret_cast<const uint4 *>(A.unit_ent + size_t(uint32_t(q[j])) * A.slot_words);
+            v0[j] = __ldg(sl);
+            v1[j] = __ldg(sl + 1);
+        } else {
+            v0[j] = make_uint4(0u, 0u, 0u, 0u);
+            v1[j] = v0[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        const uint32_t cnt = v0[j].x;
+        if (cnt == 0) continue;
+        const uint32_t hi = uint32_t(q[j] >> 32);
+        const uint32_t lane = hi & 63u, k = (hi >> 6) & 7u;
+        const uint32_t m = sig_mask(hi >> 13, (hi >> 9) & 15u);
+        unsigned int *ring32 = reinterpret_cast<unsigned int *>(ring + k) + (lane >> 5);
+        unsigned int *obs32 = reinterpret_cast<unsigned int *>(oacc + k) + (lane >> 5);
+        const uint32_t bit = 1u << (lane & 31u);
+        auto put = [&](uint32_t w) {
+            if (!((m >> (w >> 30)) & 1u)) return;
+            const uint32_t idx = w & 0x1FFFFFFFu;
+            unsigned int *p = (w & (1u << 29)) ? obs32 + size_t(idx) * 2 * K
+                                                : ring32 + size_t(idx & A.window_mask) * 2 * K;
+            atomicXor(p, bit);
+        };
+        if (cnt < 8) {
+            const uint32_t w7[7] = {v0[j].y, v0[j].z, v0[j].w, v1[j].x, v1[j].y, v1[j].z, v1[j].w};
+#pragma unroll
+            for (uint32_t t = 0; t < 7; t++)
+                if (t < cnt) put(w7[t]);
+        } else if (cnt < A.slot_words) {
+            const uint4 *sl = reinterpret_cast<const uint4 *>(A.unit_ent + size_t(uint32_t(q[j])) * A.slot_words);
+            const uint4 v2 = __ldg(sl + 2), v3 = __ldg(sl + 3);
+            const uint32_t w15[15] = {v0[j].y, v0[j].z, v0[j].w, v1[j].x, v1[j].y, v1[j].z, v1[j].w,
+                                      v2.x, v2.y, v2.z, v2.w, v3.x, v3.y, v3.z, v3.w};
+#pragma unroll
+            for (uint32_t t = 0; t < 15; t++)
+                if (t < cnt) put(w15[t]);
+        } else {
+            const uint32_t *ov = A.unit_ent + v0[j].y;
+            for (uint32_t x = 0; x < cnt; x++) put(__ldg(ov + x));
+        }
+    }
+}
+
+__device__ __forceinline__ void sig_apply_event(const SigArgs &A, uint64_t q, uint64_t *ring, uint64_t *oacc,
+                                                int K) {
+    const uint64_t qq[1] = {q};
+    sig_apply_events<1>(A, qq, 1, ring, oacc, K);
+}
+
+// Warp-aggregated shared counter: the calling lane's index among all lanes
+// that call together (one atomic per warp).
+__device__ __forceinline__ uint32_t grab_index(uint32_t *ctr) {
+    const uint32_t mask = __activemask();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t leader = uint32_t(__ffs(mask)) - 1u;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(ctr, uint32_t(__popc(mask)));
+    base = __shfl_sync(mask, base, int(leader));
+    return base + uint32_t(__popc(mask & ((1u << lane) - 1u)));
+}
+
+// Walk phase of one step: every lane holds one (segment, chunk) stream and
+// runs one Philox call (two draws) of it per iteration; a lane whose stream
+// ends takes the next from the step's counter, so the warp stays converged on
+// the generator. Events go to the shared queue (or, when it is full, straight
+// to the ring). tabs: the gap tables, in shared memory when SMT.
+template <bool SMT>
+__device__ __forceinline__ void sig_walk(const SigArgs &A, const uint4 st, uint32_t n, uint32_t nvalid,
+                                         uint32_t chunk0, const uint32_t *tabs, uint64_t *queue, uint32_t qcap,
+                                         uint32_t *s_next, uint32_t *s_qn, uint64_t *ring, uint64_t *oacc, int K) {
+    bool have = false;
+    uint32_t call = 0, seg = 0, op = 0, kind = 0, chunk = 0, ubase = 0, tag = 0, t1 = 0, t2 = 0, npauli = 1;
+    int pos = -1, n_trials = 0;
+    const uint32_t *Tt = tabs;
+    float inv = 0.f;
+    for (;;) {
+        if (!have) {
+            const uint32_t i = grab_index(s_next);
+            if (i < n) {
+                const uint32_t it = st.x + i / uint32_t(nvalid);
+                const uint32_t k = i % uint32_t(nvalid);
+                const uint2 item = __ldg(A.items + it);
+                const NoiseDesc nd = A.noise[item.x];
+                Tt = tabs + size_t(nd.table) * kTableWords;
+                inv = __uint_as_float(Tt[kGapLen]);
+                seg = item.y;
+                op = nd.op_index;
+                kind = nd.kind;
+                t1 = nd.t1;
+                t2 = nd.t2;
+                npauli = npauli_of(nd.kind);
+                chunk = chunk0 + k;
+                ubase = nd.tgt_off + item.y * kSegUnits;
+                tag = (k << 6) | (nd.kind << 13);
+                n_trials = 64 * int(min(kSegUnits, nd.n_units - item.y * kSegUnits));
+                call = 0;
+                pos = -1;
+                have = true;
+            }
+        }
+        if (!__any_sync(0xFFFFFFFFu, have)) break;
+        if (!have) continue;
+        const uint4 w = philox4x32_10(call, chunk, op, seg, A.key0, A.key1);
+        call++;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            if (!have) break;
+            const uint32_t wg = h ? w.z : w.x, wp = h ? w.w : w.y;
+            pos += 1 + gap_count_t<SMT>(Tt, inv, wg);
+            if (pos >= n_trials) {
+                have = false;
+                break;
+            }
+            const uint32_t pk = kind == N_PC1 ? (wp < t1 ? 1u : wp < t2 ? 3u : 2u) : 1u + __umulhi(wp, npauli);
+            const uint64_t q = uint64_t(ubase + uint32_t(pos >> 6)) |
+                               (uint64_t(tag | uint32_t(pos & 63) | (pk << 9)) << 32);
+            const uint32_t slot = grab_index(s_qn);
+            if (slot < qcap) queue[slot] = q;
+            else sig_apply_event(A, q, ring, oacc, K);
+        }
+    }
+}
+
+// Per step: (1) threads take (segment, chunk) streams from a shared counter
+// and walk them, appending each event to a shared queue (an event that finds
+// the queue full is applied at once); (2) all threads apply the queued events,
+// one per thread, so the output lookups and ring updates run converged;
+// (3) the step's final detectors are written out and cleared.
+template <int K>
+__global__ void __launch_bounds__(1024) sig_kernel(const SigArgs A) {
+    extern __shared__ __align__(128) uint64_t smem[];
+    __shared__ uint32_t s_next, s_qn;
+    const uint32_t W = A.window_mask + 1u;
+    uint64_t *ring = smem;
+    uint64_t *oacc = smem + size_t(W) * K;
+    uint32_t *stab = reinterpret_cast<uint32_t *>(oacc + size_t(A.n_obs) * K);
+    uint64_t *queue = reinterpret_cast<uint64_t *>(stab + size_t(A.smem_tables) * kTableWords);
+    const uint32_t qcap = A.queue_cap;
+    const uint32_t T_ = blockDim.x, tid = threadIdx.x;
+    for (uint32_t i = tid; i < (W + A.n_obs) * K; i += T_) smem[i] = 0ull;
+    for (uint32_t i = tid; i < A.smem_tables * kTableWords; i += T_) stab[i] = __ldg(A.tables + i);
+    if (tid == 0) {
+        s_next = 0;
+        s_qn = 0;
+    }
+    __syncthreads();
+    for (uint64_t tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
+        const uint64_t col0 = tile * K;
+        const uint64_t rem = A.n_cols - col0;
+        const int nvalid = rem < uint64_t(K) ? int(rem) : K;
+        const uint32_t chunk0 = A.first_chunk + uint32_t(col0);
+        for (uint32_t si = 0; si < A.n_steps; si++) {
+            const uint4 st = __ldg(A.steps + si);
+            const uint32_t n = (st.y - st.x) * uint32_t(nvalid);
+            if (A.smem_tables)
+                sig_walk<true>(A, st, n, uint32_t(nvalid), chunk0, stab, queue, qcap, &s_next, &s_qn, ring, oacc, K);
+            else
+                sig_walk<false>(A, st, n, uint32_t(nvalid), chunk0, A.tables, queue, qcap, &s_next, &s_qn, ring, oacc, K);
+            __syncthreads();
+            const uint32_t nq = min(s_qn, qcap);
+            for (uint32_t e0 = tid; e0 < nq; e0 += 4 * T_) {
+                uint64_t qb[4];
+                int nb = 0;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const uint32_t e = e0 + uint32_t(j) * T_;
+                    qb[j] = e < nq ? queue[e] : 0ull;
+                    nb += e < nq ? 1 : 0;
+                }
+                sig_apply_events<4>(A, qb, nb, ring, oacc, K);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                s_next = 0;
+                s_qn = 0;
+            }
+            const uint32_t nf = (st.w - st.z) * K;
+            for (uint32_t i = tid; i < nf; i += T_) {
+                const uint32_t d = st.z + i / K;
+                const int k = int(i % K);
+                if (k >= nvalid) continue;
+                uint64_t v = 0ull;
+                if (d - st.z < W) {
+                    uint64_t *r = ring + size_t(d & A.window_mask) * K + k;
+                    v = *r;
+                    *r = 0ull;
+                }
+                const uint64_t col = col0 + uint64_t(k);
+                if (col == A.n_cols - 1) v &= A.last_mask;
+                A.det[uint64_t(d) * A.n_cols + col] = v;
+            }
+            __syncthreads();
+        }
+        for (uint32_t i = tid; i < A.n_obs * K; i += T_) {
+            const uint32_t o = i / K;
+            const int k = int(i % K);
+            uint64_t v = oacc[i];
+            oacc[i] = 0ull;
+            if (k >= nvalid) continue;
+            const uint64_t col = col0 + uint64_t(k);
+            if (col == A.n_cols - 1) v &= A.last_mask;
+            A.obs[uint64_t(o) * A.n_cols + col] = v;
+        }
+        __syncthreads();
+    }
+}
+
+constexpr uint32_t kSigQueueMax = 16384;  // events per shared queue (128 KB)
+constexpr uint32_t kSigQueueMin = 256;
+
+static size_t sig_table_bytes(const SigProgram &G) { return G.tables.size() * 4; }
+
+static size_t sig_ring_bytes(const SigProgram &G, uint64_t n_obs, int K) {
+    return (size_t(G.window) + size_t(n_obs)) * size_t(K) * 8;
+}
+
+// Ring + observables + event queue: the queue takes what is left of `budget`
+// (at least kSigQueueMin events, at most kSigQueueMax).
+static uint32_t sig_queue_cap(const SigProgram &G, uint64_t n_obs, int K, size_t budget, bool smem_tables) {
+    const size_t ring = sig_ring_bytes(G, n_obs, K) + (smem_tables ? sig_table_bytes(G) : 0);
+    const size_t left = budget > ring ? (budget - ring) / 8 : 0;
+    return uint32_t(std::min<size_t>(kSigQueueMax, std::max<size_t>(kSigQueueMin, left & ~size_t(255))));
+}
+
+static size_t sig_smem_bytes(const SigProgram &G, uint64_t n_obs, int K, uint32_t qcap, bool smem_tables) {
+    return sig_ring_bytes(G, n_obs, K) + (smem_tables ? sig_table_bytes(G) : 0) + size_t(qcap) * 8;
+}
+
+// ---------------------------------------------------------------------------
 // Batched persistent launch: resident CTAs pull work items (job, tile) from a
 // device counter until none are left; each item runs its job's program on
 // one tile with the CTA-wide layer loop above. Jobs may have different
@@ -975,6 +1282,65 @@ static int device_program(const tmcs_circuit *c, const DeviceProgram **out) {
     return upload_program(c, c->prog, c->dev, out);
 }
 
+// Upload (once per device) the event-signature program.
+static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(c->mu);
+    auto it = c->dev_sig.find(dev);
+    if (it != c->dev_sig.end()) {
+        *out = &it->second;
+        return TMCS_OK;
+    }
+    const SigProgram &G = c->sig;
+    const size_t b_noise = align256(G.noise.size() * sizeof(NoiseDesc));
+    const size_t b_tables = align256(G.tables.size() * 4);
+    const size_t b_items = align256(G.items.size() * 4);
+    const size_t b_steps = align256(G.steps.size() * sizeof(SigStep));
+    const size_t b_ent = align256(G.unit_ent.size() * 4);
+    const size_t total = std::max<size_t>(b_noise + b_tables + b_items + b_steps + b_ent, 256);
+    std::vector<uint8_t> host(total, 0);
+    size_t o = 0;
+    auto put = [&](const void *src, size_t n, size_t span) {
+        if (n) std::memcpy(host.data() + o, src, n);
+        const size_t at = o;
+        o += span;
+        return at;
+    };
+    std::vector<NoiseDesc> dn = G.noise;
+    for (size_t i = 0; i < dn.size(); i++) dn[i].tgt_off = G.unit_base[i];
+    const size_t o_noise = put(dn.data(), dn.size() * sizeof(NoiseDesc), b_noise);
+    const size_t o_tables = put(G.tables.data(), G.tables.size() * 4, b_tables);
+    const size_t o_items = put(G.items.data(), G.items.size() * 4, b_items);
+    const size_t o_steps = put(G.steps.data(), G.steps.size() * sizeof(SigStep), b_steps);
+    const size_t o_ent = put(G.unit_ent.data(), G.unit_ent.size() * 4, b_ent);
+    void *base = nullptr;
+    e = cudaMalloc(&base, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TMCS_E_OOM, std::string("cudaMalloc of the signature program: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(base, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(base);
+        return cuda_fail(e, "cudaMemcpy of the signature program");
+    }
+    DeviceSig ds;
+    ds.device = dev;
+    ds.base = base;
+    ds.bytes = total;
+    uint8_t *b = static_cast<uint8_t *>(base);
+    ds.noise = reinterpret_cast<const NoiseDesc *>(b + o_noise);
+    ds.tables = reinterpret_cast<const uint32_t *>(b + o_tables);
+    ds.items = reinterpret_cast<const uint32_t *>(b + o_items);
+    ds.steps = reinterpret_cast<const SigStep *>(b + o_steps);
+    ds.unit_ent = reinterpret_cast<const uint32_t *>(b + o_ent);
+    auto ins = c->dev_sig.emplace(dev, ds);
+    *out = &ins.first->second;
+    return TMCS_OK;
+}
+
 void free_device_programs(tmcs_circuit *c) {
     std::lock_guard<std::mutex> lock(c->mu);
     int cur = 0;
@@ -986,6 +1352,11 @@ void free_device_programs(tmcs_circuit *c) {
         }
         m->clear();
     }
+    for (auto &kv : c->dev_sig) {
+        cudaSetDevice(kv.first);
+        cudaFree(kv.second.base);
+    }
+    c->dev_sig.clear();
     cudaSetDevice(cur);
     cudaGetLastError();
 }
@@ -1013,13 +1384,17 @@ static int device_limits(DeviceLimits *lim) {
 }
 
 struct LaunchShape {
-    int mode = 3;      // 3: CTA-wide layers (frame_kernel), 4: warp-owned chunks (frame_kernel_w)
+    int mode = 3;      // 3: CTA-wide layers (frame_kernel), 4: warp-owned chunks (frame_kernel_w),
+                       // 5: event signatures (sig_kernel; tiles = resident CTAs)
     int K = 1;         // chunks per CTA (mode 3) or per consumer warp (mode 4)
     int warps = 0;     // chunk groups (mode 4)
     int group = 1;     // warps per chunk group (mode 4)
     int threads = 256;
     size_t smem = 0;
     uint64_t tiles = 0;
+    int sms = 0;       // mode 5: SM count (grid = SMs x resident CTAs per SM)
+    uint32_t qcap = 0; // mode 5: event-queue capacity
+    bool smem_tables = false;  // mode 5: gap tables staged in shared memory
 };
 
 static int env_int(const char *name, int dflt) {
@@ -1067,6 +1442,35 @@ static LaunchShape make_shape_w(const Program &P, uint64_t n_cols, int KW, int W
     s.threads = 32 * (W * G + 1);
     s.smem = kernel_w_smem_bytes(P.n_slots, P.max_window_segs, KW, W);
     s.tiles = (n_cols + uint64_t(W) * KW - 1) / (uint64_t(W) * KW);
+    return s;
+}
+
+// Event-signature kernel: K chunks per CTA, persistent grid of the CTAs that
+// fit on the device at once (shared memory and thread limits).
+static bool sig_fits(const tmcs_circuit *c, const DeviceLimits &lim, int K) {
+    return c->sig.ok && sig_smem_bytes(c->sig, c->n_obs, K, kSigQueueMin, false) <= lim.smem_optin;
+}
+
+// The queue gets the shared memory left once the CTAs that the register file
+// allows at this CTA size (64 registers per thread) each hold their ring.
+static LaunchShape make_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const DeviceLimits &lim, int K,
+                                  int threads) {
+    LaunchShape s;
+    s.mode = 5;
+    s.K = K;
+    s.threads = threads;
+    s.sms = lim.sms;
+    const size_t ctas = size_t(std::max(1, 1024 / threads));
+    const size_t budget = std::min(lim.smem_optin, lim.smem_per_sm / ctas - 1024);
+    // gap tables go to shared memory if they fit next to the ring and a
+    // queue of 2048 events
+    s.smem_tables = sig_smem_bytes(c->sig, c->n_obs, K, 2048, true) <= budget;
+    s.qcap = sig_queue_cap(c->sig, c->n_obs, K, budget, s.smem_tables);
+    const int qforce = env_int("TMCS_SIG_QUEUE", 0);  // tuning/testing knob: queue capacity
+    if (qforce > 0) s.qcap = uint32_t(std::min<int>(qforce, int(kSigQueueMax)));
+    s.smem = sig_smem_bytes(c->sig, c->n_obs, K, s.qcap, s.smem_tables);
+    const uint64_t n_tiles = (n_cols + K - 1) / K;
+    s.tiles = std::min<uint64_t>(n_tiles, uint64_t(lim.sms) * ctas);
     return s;
 }
 
@@ -1120,7 +1524,58 @@ static cudaError_t launch_w(const KernelArgs &a, const LaunchShape &s, cudaStrea
     return cudaGetLastError();
 }
 
-static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream_t st) {
+// Persistent grid: as many CTAs as are resident at once (occupancy query),
+// never more than there are tiles.
+template <int K>
+static cudaError_t launch_sig(const SigArgs &a, const LaunchShape &s, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(sig_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sig_kernel<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             int(cudaSharedmemCarveoutMaxShared));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sig_kernel<K>, s.threads, s.smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(a.n_tiles, uint64_t(s.sms) * uint64_t(std::max(per_sm, 1))));
+    sig_kernel<K><<<unsigned(grid), s.threads, s.smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Mode 5 takes the event-signature program (device copy ds, host G); its
+// output, seed and chunk range come from a0 like the frame kernels'.
+static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream_t st,
+                          const DeviceSig *ds = nullptr, const SigProgram *G = nullptr, uint32_t n_obs = 0) {
+    if (s.mode == 5) {
+        if (!ds || !G) return cudaErrorInvalidValue;
+        SigArgs a{};
+        a.noise = ds->noise;
+        a.tables = ds->tables;
+        a.items = reinterpret_cast<const uint2 *>(ds->items);
+        a.steps = reinterpret_cast<const uint4 *>(ds->steps);
+        a.unit_ent = ds->unit_ent;
+        a.n_steps = uint32_t(G->steps.size());
+        a.window_mask = G->window - 1u;
+        a.n_obs = n_obs;
+        a.queue_cap = s.qcap;
+        a.smem_tables = s.smem_tables ? uint32_t(G->tables.size() / kTableWords) : 0u;
+        a.slot_words = G->slot_words;
+        a.key0 = a0.key0;
+        a.key1 = a0.key1;
+        a.first_chunk = a0.first_chunk;
+        a.n_cols = a0.n_cols;
+        a.last_mask = a0.last_mask;
+        a.n_tiles = (a0.n_cols + uint64_t(s.K) - 1) / uint64_t(s.K);
+        a.det = a0.det;
+        a.obs = a0.obs;
+        LaunchShape t = s;
+        t.tiles = std::min<uint64_t>(s.tiles, a.n_tiles);
+        switch (s.K) {
+        case 8: return launch_sig<8>(a, t, st);
+        case 4: return launch_sig<4>(a, t, st);
+        case 2: return launch_sig<2>(a, t, st);
+        default: return launch_sig<1>(a, t, st);
+        }
+    }
     KernelArgs a = a0;
     a.group_warps = uint32_t(s.group);
     if (s.mode == 4) return s.K == 2 ? launch_w<2>(a, s, st) : launch_w<1>(a, s, st);
@@ -1161,9 +1616,14 @@ uint32_t *device_status_word(int device) {
 // chunk for the circuit on this device. Synchronous; runs once per circuit
 // and device.
 static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const DeviceLimits &lim, uint64_t n_cols,
-                    cudaStream_t st, LaunchShape *best) {
+                    cudaStream_t st, LaunchShape *best, const DeviceSig *ds) {
     const Program &P = c->prog;
     std::vector<LaunchShape> cands;
+    if (ds)
+        for (int K = 1; K <= 8; K *= 2) {
+            if (!sig_fits(c, lim, K)) break;
+            for (int threads : {256, 512, 1024}) cands.push_back(make_shape_sig(c, n_cols, lim, K, threads));
+        }
     for (int K = 1; K <= 16; K *= 2) {
         if (!shape_fits(P, lim, K)) break;
         for (int threads : {128, 256, 512}) cands.push_back(make_shape(P, n_cols, K, threads));
@@ -1189,14 +1649,14 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
         const uint64_t cols = std::min<uint64_t>(n_cols, uint64_t(4) * lim.sms * per_tile);
         if (cols / per_tile < uint64_t(lim.sms)) continue;
         LaunchShape s = full;
-        s.tiles = (cols + per_tile - 1) / per_tile;
+        if (s.mode != 5) s.tiles = (cols + per_tile - 1) / per_tile;
         KernelArgs t = a;
         t.n_cols = cols;
         t.last_mask = ~uint64_t(0);
         float ms = 0.f;
         for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
             if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
-            if ((e = launch(t, s, st)) != cudaSuccess) break;
+            if ((e = launch(t, s, st, ds, &c->sig, uint32_t(c->n_obs))) != cudaSuccess) break;
             if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
             if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
             e = cudaEventElapsedTime(&ms, e0, e1);
@@ -1225,6 +1685,23 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
     return TMCS_OK;
 }
 
+// Default shape of the event-signature kernel: the largest K (<= 4) that
+// leaves room for two CTAs per SM and still gives every SM two tiles.
+static LaunchShape choose_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const DeviceLimits &lim) {
+    const int kcap = env_int("TMCS_TILE_K", 0);
+    int K = kcap > 0 ? std::min(kcap, 8) : 4;
+    while (K > 1 && (K & (K - 1))) K--;
+    while (K > 1 && !sig_fits(c, lim, K)) K >>= 1;
+    if (kcap <= 0) {
+        while (K > 1 && 2 * (sig_smem_bytes(c->sig, c->n_obs, K, kSigQueueMin, false) + 1024) > lim.smem_per_sm) K >>= 1;
+        while (K > 1 && (n_cols + K - 1) / K < uint64_t(2 * lim.sms)) K >>= 1;
+    }
+    int threads = 512;
+    const int tforce = env_int("TMCS_THREADS", 0);
+    if (tforce >= 32 && tforce <= 1024 && tforce % 32 == 0) threads = tforce;
+    return make_shape_sig(c, n_cols, lim, K, threads);
+}
+
 static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
                         uint64_t *det, uint64_t *obs, void *stream, bool fault_mode = false,
                         uint64_t fault_first = 0) {
@@ -1248,16 +1725,25 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
     uint32_t *status = device_status_word(dp->device);
     if (!status) return fail(TMCS_E_OOM, "cannot allocate the device status word");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    LaunchShape s = choose_shape(P, n_cols, lim);
+    const int kmode = env_int("TMCS_KERNEL", 0);
+    const DeviceSig *ds = nullptr;
+    if (!fault_mode && c->sig.ok && sig_fits(c, lim, 1) && kmode != 3 && kmode != 4) {
+        if ((rc = device_sig(c, &ds))) return rc;
+    }
+    if (kmode == 5 && !ds && !fault_mode)
+        return fail(TMCS_E_INVALID, "TMCS_KERNEL=5: no event-signature program for this circuit (" +
+                                        (c->sig.ok ? std::string("ring does not fit") : c->sig.why) + ")");
+    LaunchShape s = ds ? choose_shape_sig(c, n_cols, lim) : choose_shape(P, n_cols, lim);
     const bool forced = env_int("TMCS_TILE_K", 0) > 0 || env_int("TMCS_THREADS", 0) > 0 ||
-                        env_int("TMCS_KERNEL", 0) > 0 || env_int("TMCS_WARPS", 0) > 0 ||
-                        env_int("TMCS_GROUP", 0) > 0;
-    if (!forced) {
+                        kmode > 0 || env_int("TMCS_WARPS", 0) > 0 || env_int("TMCS_GROUP", 0) > 0;
+    if (!forced && !fault_mode) {
         std::lock_guard<std::mutex> lock(c->mu);
         DeviceProgram &mdp = c->dev[dp->device];
         if (mdp.tuned_mode == 3) s = make_shape(P, n_cols, mdp.tuned_K, mdp.tuned_threads);
         if (mdp.tuned_mode == 4) s = make_shape_w(P, n_cols, mdp.tuned_K, mdp.tuned_warps, mdp.tuned_group);
+        if (mdp.tuned_mode == 5 && ds) s = make_shape_sig(c, n_cols, lim, mdp.tuned_K, mdp.tuned_threads);
     }
+    if (fault_mode) s = choose_shape(P, n_cols, lim);
     KernelArgs a{};
     a.layers = dp->layers;
     a.args = dp->args;
@@ -1286,11 +1772,11 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         cudaStreamIsCapturing(st, &cap);
         if (!tuned && cap == cudaStreamCaptureStatusNone && n_cols >= uint64_t(16 * lim.sms)) {
-            int rc2 = autotune(c, dp->device, a, lim, n_cols, st, &s);
+            int rc2 = autotune(c, dp->device, a, lim, n_cols, st, &s, ds);
             if (rc2) return rc2;
         }
     }
-    cudaError_t e = launch(a, s, st);
+    cudaError_t e = launch(a, s, st, ds, &c->sig, uint32_t(c->n_obs));
     if (e != cudaSuccess) return cuda_fail(e, "frame kernel launch");
     return TMCS_OK;
 }

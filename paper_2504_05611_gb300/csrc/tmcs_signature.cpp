@@ -1,0 +1,421 @@
+// Event-signature program: per-generator output lists by a transposed frame
+// pass, and the step schedule of the signature sampler.
+//
+// Why it is exact: with the noiseless reference fixed, each detector and
+// observable flip is a parity of record flips, and every record flip is a
+// GF(2)-linear function of the Pauli events of the shot (frames only ever
+// XOR; Methods "Simulation" noise channels are Pauli). So the flips of a shot
+// are the XOR over its events of each event's signature, the output of the
+// frame program with that one event injected -- the DEM columns of Methods
+// "Decoding". A Pauli event is the product of its X/Z generators, so its
+// signature is the XOR of theirs.
+//
+// Transposed pass: the frame maps (CX c->t: x_t ^= x_c, z_c ^= z_t; H swaps
+// x and z; S: z ^= x; R/RX clear both; M/MX record x/z; XFEED/ZFEED XOR a
+// record into x/z) are linear; running their transposes over the op list
+// from the end, on bit masks of a group of 64 outputs, gives at each point
+// the set of outputs an X (mask sx) or Z (mask sz) flip there would flip.
+// The pass for a group starts at the last op holding one of its records and
+// stops as soon as no mask and no pending record sensitivity is left.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <system_error>
+#include <thread>
+
+#include "tmcs_internal.h"
+
+namespace tmcs {
+
+int table_for_p(std::vector<uint32_t> &tables, std::vector<double> &table_p, double p, uint32_t *out) {
+    for (size_t i = 0; i < table_p.size(); i++)
+        if (table_p[i] == p) {
+            *out = uint32_t(i);
+            return TMCS_OK;
+        }
+    const uint32_t id = uint32_t(table_p.size());
+    table_p.push_back(p);
+    tables.resize(tables.size() + kTableWords, 0u);
+    uint32_t *tab = &tables[size_t(id) * kTableWords];
+    int rc = gap_table(p, tab);
+    if (rc) return rc;
+    const float inv = p >= 1.0 ? 0.0f : float(1.0 / std::log2(1.0 - p));
+    std::memcpy(tab + kGapLen, &inv, 4);
+    *out = id;
+    return TMCS_OK;
+}
+
+namespace {
+
+bool noise_code(uint32_t code) {
+    return code == TMCS_X_ERROR || code == TMCS_Z_ERROR || code == TMCS_DEPOLARIZE1 ||
+           code == TMCS_DEPOLARIZE2 || code == TMCS_PAULI_CHANNEL_1;
+}
+
+uint32_t kind_of(uint32_t code) {
+    return code == TMCS_X_ERROR ? N_XERR : code == TMCS_Z_ERROR ? N_ZERR : code == TMCS_DEPOLARIZE1 ? N_DEP1
+           : code == TMCS_DEPOLARIZE2 ? N_DEP2 : N_PC1;
+}
+
+struct Edge {
+    uint32_t gen;
+    uint32_t out;
+};
+
+// State of one transposed pass (reused across the passes of one thread).
+struct Pass {
+    std::vector<uint64_t> sx, sz, rs;  // per qubit / per record sensitivity masks
+    std::vector<uint32_t> rs_touched;
+    int64_t nz = 0;                    // nonzero entries among sx, sz, rs
+
+    void set(uint64_t &v, uint64_t nv) {
+        nz += int64_t(nv != 0) - int64_t(v != 0);
+        v = nv;
+    }
+};
+
+}  // namespace
+
+int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
+    const auto t_start = std::chrono::steady_clock::now();
+    SigProgram &G = c->sig;
+    G = SigProgram();
+    const size_t n_ops = c->ops.size();
+    const uint64_t Q = c->n_qubits, M = c->n_meas, D = c->n_det, O = c->n_obs;
+    if (D >= kSigObsFlag || O > 4096) {
+        G.why = "too many outputs";
+        return TMCS_OK;
+    }
+
+    // ---- noise descriptors and generator ids (every noise op with p > 0)
+    std::vector<uint32_t> op_desc(n_ops, 0xFFFFFFFFu);
+    std::vector<double> table_p;
+    uint64_t n_gens = 0;
+    for (size_t i = 0; i < n_ops; i++) {
+        const HostOp &op = c->ops[i];
+        if (!noise_code(op.code) || !(op.p > 0.0) || op.nt == 0) continue;
+        NoiseDesc nd{};
+        nd.op_index = uint32_t(i);
+        nd.kind = kind_of(op.code);
+        if (nd.kind == N_PC1) {
+            nd.t1 = op.arg;
+            nd.t2 = op.arg2;
+        }
+        int rc = table_for_p(G.tables, table_p, op.p, &nd.table);
+        if (rc) return rc;
+        nd.n_units = nd.kind == N_DEP2 ? op.nt / 2 : op.nt;
+        nd.n_seg = (nd.n_units + kSegUnits - 1) / kSegUnits;
+        if (n_gens + uint64_t(nd.n_units) * sig_gens(nd.kind) >= 0xFFFFFFFFull) {
+            G.why = "too many noise generators";
+            return TMCS_OK;
+        }
+        nd.tgt_off = uint32_t(n_gens);
+        n_gens += uint64_t(nd.n_units) * sig_gens(nd.kind);
+        op_desc[i] = uint32_t(G.noise.size());
+        G.noise.push_back(nd);
+    }
+
+    // ---- records: producing op, first record of each measuring op
+    std::vector<uint32_t> rec_op(M), rec_base(n_ops, 0);
+    {
+        uint64_t m = 0;
+        for (size_t i = 0; i < n_ops; i++) {
+            const HostOp &op = c->ops[i];
+            rec_base[i] = uint32_t(m);
+            if (op.code == TMCS_M || op.code == TMCS_MX)
+                for (uint32_t a = 0; a < op.nt; a++) rec_op[m++] = uint32_t(i);
+        }
+    }
+    // output record lists: detectors 0..D-1, then observables D..D+O-1
+    std::vector<uint32_t> out_off(D + O + 1, 0), out_rec;
+    {
+        std::vector<std::vector<uint32_t>> obs_recs(O);
+        uint64_t d = 0;
+        for (size_t i = 0; i < n_ops; i++) {
+            const HostOp &op = c->ops[i];
+            const uint32_t *t = c->targets.data() + op.toff;
+            if (op.code == TMCS_DETECTOR) {
+                out_rec.insert(out_rec.end(), t, t + op.nt);
+                out_off[++d] = uint32_t(out_rec.size());
+            } else if (op.code == TMCS_OBSERVABLE) {
+                obs_recs[op.arg].insert(obs_recs[op.arg].end(), t, t + op.nt);
+            }
+        }
+        for (uint64_t o = 0; o < O; o++) {
+            out_rec.insert(out_rec.end(), obs_recs[o].begin(), obs_recs[o].end());
+            out_off[D + o + 1] = uint32_t(out_rec.size());
+        }
+    }
+
+    // ---- transposed passes, one per group of 64 outputs (detector groups
+    // never mix with observables)
+    const uint64_t n_gd = (D + 63) / 64, n_go = (O + 63) / 64, n_groups = n_gd + n_go;
+    std::vector<std::vector<Edge>> edges(n_groups);
+    auto run_group = [&](uint64_t g, Pass &S) {
+        const bool obs = g >= n_gd;
+        const uint64_t b = obs ? D + 64 * (g - n_gd) : 64 * g;
+        const uint64_t e = obs ? std::min<uint64_t>(D + O, b + 64) : std::min<uint64_t>(D, b + 64);
+        const uint32_t tag = obs ? kSigObsFlag : 0u;
+        const uint64_t base_out = obs ? b - D : b;
+        int64_t start = -1;
+        for (uint64_t j = b; j < e; j++)
+            for (uint32_t k = out_off[j]; k < out_off[j + 1]; k++) {
+                const uint32_t r = out_rec[k];
+                S.set(S.rs[r], S.rs[r] ^ (1ull << (j - b)));
+                S.rs_touched.push_back(r);
+                start = std::max<int64_t>(start, rec_op[r]);
+            }
+        std::vector<Edge> &E = edges[g];
+        for (int64_t i = start; i >= 0 && S.nz > 0; i--) {
+            const HostOp &op = c->ops[size_t(i)];
+            const uint32_t *t = c->targets.data() + op.toff;
+            switch (op.code) {
+            case TMCS_M:
+            case TMCS_MX: {
+                const bool zb = op.code == TMCS_MX;
+                for (uint32_t a = op.nt; a-- > 0;) {
+                    const uint32_t r = rec_base[size_t(i)] + a;
+                    const uint64_t v = S.rs[r];
+                    if (!v) continue;
+                    uint64_t &f = zb ? S.sz[t[a]] : S.sx[t[a]];
+                    S.set(f, f ^ v);
+                    S.set(S.rs[r], 0);
+                }
+                break;
+            }
+            case TMCS_R:
+            case TMCS_RX:
+                for (uint32_t a = op.nt; a-- > 0;) {
+                    S.set(S.sx[t[a]], 0);
+                    S.set(S.sz[t[a]], 0);
+                }
+                break;
+            case TMCS_H:
+                for (uint32_t a = op.nt; a-- > 0;) std::swap(S.sx[t[a]], S.sz[t[a]]);
+                break;
+            case TMCS_S:
+                for (uint32_t a = op.nt; a-- > 0;) S.set(S.sx[t[a]], S.sx[t[a]] ^ S.sz[t[a]]);
+                break;
+            case TMCS_CX:
+                for (uint32_t a = op.nt; a >= 2; a -= 2) {
+                    const uint32_t cq = t[a - 2], tq = t[a - 1];
+                    S.set(S.sx[cq], S.sx[cq] ^ S.sx[tq]);
+                    S.set(S.sz[tq], S.sz[tq] ^ S.sz[cq]);
+                }
+                break;
+            case TMCS_XFEED:
+            case TMCS_ZFEED: {
+                const bool zb = op.code == TMCS_ZFEED;
+                for (uint32_t a = op.nt; a >= 2; a -= 2) {
+                    const uint32_t r = t[a - 2], q = t[a - 1];
+                    const uint64_t v = zb ? S.sz[q] : S.sx[q];
+                    if (!v) continue;
+                    S.set(S.rs[r], S.rs[r] ^ v);
+                    S.rs_touched.push_back(r);
+                }
+                break;
+            }
+            default:
+                if (op_desc[size_t(i)] != 0xFFFFFFFFu) {
+                    const NoiseDesc &nd = G.noise[op_desc[size_t(i)]];
+                    const uint32_t ng = sig_gens(nd.kind);
+                    for (uint32_t u = 0; u < nd.n_units; u++)
+                        for (uint32_t gg = 0; gg < ng; gg++) {
+                            const uint32_t q = nd.kind == N_DEP2 ? t[2 * u + gg / 2] : t[u];
+                            uint64_t m = (gg & 1u) ? S.sz[q] : S.sx[q];
+                            while (m) {
+                                const int bit = __builtin_ctzll(m);
+                                m &= m - 1;
+                                E.push_back({nd.tgt_off + u * ng + gg, uint32_t(base_out + uint64_t(bit)) | tag});
+                            }
+                        }
+                }
+                break;
+            }
+        }
+        if (S.nz != 0) {
+            std::fill(S.sx.begin(), S.sx.end(), 0);
+            std::fill(S.sz.begin(), S.sz.end(), 0);
+        }
+        for (uint32_t r : S.rs_touched) S.rs[r] = 0;
+        S.rs_touched.clear();
+        S.nz = 0;
+    };
+    unsigned n_thr = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (n_groups < 4 * n_thr) n_thr = 1;
+    std::vector<std::thread> pool;
+    auto worker = [&](unsigned w) {
+        Pass S;
+        S.sx.assign(Q, 0);
+        S.sz.assign(Q, 0);
+        S.rs.assign(M, 0);
+        for (uint64_t g = w; g < n_groups; g += n_thr) run_group(g, S);
+    };
+    try {
+        if (n_thr == 1) {
+            worker(0);
+        } else {
+            for (unsigned w = 0; w < n_thr; w++) pool.emplace_back(worker, w);
+            for (auto &th : pool) th.join();
+        }
+    } catch (const std::system_error &) {
+        for (auto &th : pool)
+            if (th.joinable()) th.join();
+        pool.clear();
+        worker(0);
+    }
+
+    // ---- CSR by generator (group order within a generator)
+    G.gen_off.assign(n_gens + 1, 0);
+    uint64_t n_ent = 0;
+    for (const auto &E : edges)
+        for (const Edge &x : E) G.gen_off[x.gen + 1]++;
+    for (uint64_t g = 0; g < n_gens; g++) G.gen_off[g + 1] += G.gen_off[g];
+    n_ent = G.gen_off[n_gens];
+    if (n_ent >= 0xFFFFFFFFull) {
+        G.why = "too many signature entries";
+        return TMCS_OK;
+    }
+    G.gen_ent.assign(n_ent, 0);
+    {
+        std::vector<uint32_t> fill(G.gen_off.begin(), G.gen_off.end() - 1);
+        for (const auto &E : edges)
+            for (const Edge &x : E) G.gen_ent[fill[x.gen]++] = x.out;
+    }
+    edges.clear();
+
+    // ---- device layout: one fixed-size slot of S words per unit (S = 8 or
+    // 16, the smaller one that holds 99% of the units whole), so an event's
+    // data is one aligned load at unit * S: word 0 = entry count n; if
+    // n < S the entries follow in words 1..n, else word 1 is the offset of
+    // the n entries in the overflow area after all slots. Each entry is
+    // generator << 30 | observable flag << 29 | output index.
+    {
+        uint64_t units = 0;
+        for (const NoiseDesc &nd : G.noise) {
+            G.unit_base.push_back(uint32_t(units));
+            units += nd.n_units;
+        }
+        if (D >= (1u << 29) || O >= (1u << 29)) {
+            G.why = "too many outputs for the device layout";
+            return TMCS_OK;
+        }
+        uint64_t fit8 = 0, fit16 = 0, with = 0;
+        for (const NoiseDesc &nd : G.noise) {
+            const uint32_t ng = sig_gens(nd.kind);
+            for (uint32_t u = 0; u < nd.n_units; u++) {
+                const uint32_t g0 = nd.tgt_off + u * ng;
+                const uint32_t cnt = G.gen_off[g0 + ng] - G.gen_off[g0];
+                if (!cnt) continue;
+                with++;
+                fit8 += cnt < 8;
+                fit16 += cnt < 16;
+            }
+        }
+        const uint32_t S = (with == 0 || fit8 * 100 >= with * 99) ? 8u : 16u;
+        (void)fit16;
+        if (units * S >= 0xFFFFFFFFull) {
+            G.why = "too many noise units for the device layout";
+            return TMCS_OK;
+        }
+        G.slot_words = S;
+        G.unit_ent.assign(units * S, 0u);
+        for (uint32_t di = 0; di < G.noise.size(); di++) {
+            const NoiseDesc &nd = G.noise[di];
+            const uint32_t ng = sig_gens(nd.kind);
+            for (uint32_t u = 0; u < nd.n_units; u++) {
+                const uint32_t g0 = nd.tgt_off + u * ng;
+                const uint32_t cnt = G.gen_off[g0 + ng] - G.gen_off[g0];
+                const size_t slot = size_t(G.unit_base[di] + u) * S;
+                G.unit_ent[slot] = cnt;
+                if (!cnt) continue;
+                std::vector<uint32_t> tagged;
+                for (uint32_t g = 0; g < ng; g++)
+                    for (uint32_t k = G.gen_off[g0 + g]; k < G.gen_off[g0 + g + 1]; k++) {
+                        const uint32_t v = G.gen_ent[k];
+                        const uint32_t idx = v & ~kSigObsFlag, obs = (v & kSigObsFlag) ? 1u : 0u;
+                        tagged.push_back((g << 30) | (obs << 29) | idx);
+                    }
+                if (cnt < S) {
+                    std::copy(tagged.begin(), tagged.end(), G.unit_ent.begin() + slot + 1);
+                } else {
+                    if (G.unit_ent.size() + cnt >= 0xFFFFFFFFull) {
+                        G.why = "too many signature entries";
+                        return TMCS_OK;
+                    }
+                    G.unit_ent[slot + 1] = uint32_t(G.unit_ent.size());
+                    G.unit_ent.insert(G.unit_ent.end(), tagged.begin(), tagged.end());
+                }
+            }
+        }
+        while (G.unit_ent.size() % 4) G.unit_ent.push_back(0u);
+    }
+
+    // ---- items: segments whose events flip anything; detector span per item
+    std::vector<uint32_t> dmin, dmax;
+    for (uint32_t di = 0; di < G.noise.size(); di++) {
+        const NoiseDesc &nd = G.noise[di];
+        const uint32_t ng = sig_gens(nd.kind);
+        for (uint32_t s = 0; s < nd.n_seg; s++) {
+            const uint32_t u0 = s * kSegUnits, u1 = std::min(nd.n_units, u0 + kSegUnits);
+            const uint32_t g0 = nd.tgt_off + u0 * ng, g1 = nd.tgt_off + u1 * ng;
+            if (G.gen_off[g0] == G.gen_off[g1]) continue;
+            uint32_t lo = 0xFFFFFFFFu, hi = 0;
+            bool any_det = false;
+            for (uint32_t k = G.gen_off[g0]; k < G.gen_off[g1]; k++) {
+                const uint32_t v = G.gen_ent[k];
+                if (v & kSigObsFlag) continue;
+                lo = std::min(lo, v);
+                hi = std::max(hi, v);
+                any_det = true;
+            }
+            G.items.push_back(di);
+            G.items.push_back(s);
+            dmin.push_back(any_det ? lo : 0xFFFFFFFFu);
+            dmax.push_back(any_det ? hi : 0u);
+        }
+    }
+    const size_t n_items = dmin.size();
+    std::vector<uint64_t> sufmin(n_items + 1, D);
+    for (size_t i = n_items; i-- > 0;) sufmin[i] = std::min<uint64_t>(sufmin[i + 1], dmin[i]);
+
+    // ---- window and steps: the smallest power of two >= 1024 that admits
+    // a schedule, raised to max_window (fewer, larger steps), capped by D
+    uint64_t need = 0;
+    for (size_t i = 0; i < n_items; i++)
+        if (dmin[i] != 0xFFFFFFFFu) need = std::max<uint64_t>(need, uint64_t(dmax[i]) - sufmin[i] + 1);
+    uint64_t W = 1024;
+    while (W < need) W <<= 1;
+    uint64_t Dp = 1024;
+    while (Dp < D) Dp <<= 1;
+    W = std::max<uint64_t>(W, std::min<uint64_t>(max_window, Dp));
+    if (W > max_window) {
+        G.why = "detector window " + std::to_string(need) + " exceeds " + std::to_string(max_window);
+        G.items.clear();
+        return TMCS_OK;
+    }
+    G.window = uint32_t(W);
+    {
+        uint64_t F = 0;
+        size_t i = 0;
+        while (i < n_items) {
+            size_t j = i;
+            while (j < n_items && (dmin[j] == 0xFFFFFFFFu || dmax[j] < F + W)) j++;
+            if (j == i) {  // cannot happen: W >= need and F <= sufmin[i]
+                G.why = "internal: schedule";
+                return TMCS_OK;
+            }
+            const uint64_t F2 = sufmin[j];
+            G.steps.push_back({uint32_t(i), uint32_t(j), uint32_t(F), uint32_t(F2)});
+            F = F2;
+            i = j;
+        }
+        if (G.steps.empty() || F < D) G.steps.push_back({uint32_t(n_items), uint32_t(n_items), uint32_t(F), uint32_t(D)});
+    }
+    G.ok = true;
+    G.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    return TMCS_OK;
+}
+
+}  // namespace tmcs

@@ -33,7 +33,9 @@ OP_DTYPE = np.dtype([("code", "<u4"), ("n_targets", "<u4"), ("p", "<f8"), ("arg"
 assert OP_DTYPE.itemsize == 32
 
 STATS_FIELDS = ("n_layers", "n_slots", "n_xor", "n_zero", "n_copy", "n_noise_ops", "n_noise_units",
-                "n_noise_segments", "n_parity_terms", "live_components", "pruned_updates")
+                "n_noise_segments", "n_parity_terms", "live_components", "pruned_updates",
+                "sig_ok", "sig_window", "sig_steps", "sig_items", "sig_generators", "sig_entries",
+                "sig_build_us")
 
 
 class TmcsError(RuntimeError):
@@ -95,6 +97,7 @@ def lib() -> ctypes.CDLL:
         L.tmcs_fault_count.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
         L.tmcs_fault_signatures.argtypes = [P, U64, U64, P, P, P]
         L.tmcs_sample_measurements.argtypes = [P, U64, U64, U64, P, P]
+        L.tmcs_fault_outputs.argtypes = [P, U64, P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
         L.tmcs_server_open.argtypes = [P, ctypes.POINTER(P)]
         L.tmcs_server_submit.argtypes = [P, P, U64, U64, ctypes.POINTER(ctypes.c_uint64)]
         L.tmcs_server_poll.argtypes = [P, U64, ctypes.POINTER(ctypes.c_int)]
@@ -109,7 +112,7 @@ def lib() -> ctypes.CDLL:
                   "tmcs_debug_gap_table", "tmcs_check_device", "tmcs_sample_noalloc", "tmcs_server_open",
                   "tmcs_server_submit", "tmcs_server_poll", "tmcs_server_fetch", "tmcs_server_release",
                   "tmcs_server_get_stats", "tmcs_server_close", "tmcs_fault_count", "tmcs_fault_signatures",
-                  "tmcs_sample_measurements"):
+                  "tmcs_sample_measurements", "tmcs_fault_outputs"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -182,6 +185,20 @@ def tmcs_fault_count(handle: int) -> int:
     n = ctypes.c_uint64()
     _check(lib().tmcs_fault_count(ctypes.c_void_p(handle), ctypes.byref(n)))
     return n.value
+
+
+def tmcs_fault_outputs(handle: int, fault: int) -> Tuple[List[int], List[int]]:
+    """(detectors, observables) flipped by one elementary fault, from the
+    host event-signature table."""
+    cap = 64
+    while True:
+        buf = np.zeros(cap, dtype=np.uint32)
+        n = ctypes.c_uint32()
+        _check(lib().tmcs_fault_outputs(ctypes.c_void_p(handle), fault, buf.ctypes.data, cap, ctypes.byref(n)))
+        if n.value <= cap:
+            v = [int(x) for x in buf[:n.value]]
+            return [x for x in v if x < 0x80000000], [x & 0x7FFFFFFF for x in v if x >= 0x80000000]
+        cap = n.value
 
 
 def tmcs_fault_signatures(handle: int, first_fault: int, n_faults: int, det, obs, stream=None) -> None:

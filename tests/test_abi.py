@@ -165,3 +165,53 @@ def test_measurement_program_compiles_and_validates(tmcs, kind):
         assert "program check" not in tmcs.tmcs_last_error()
     finally:
         tmcs.tmcs_circuit_free(h)
+
+
+def _sig_cases():
+    from circuit_gen import random_noisy_circuit
+    out = [("nl_sc3", C.nonlocal_cnot_circuit(C.code_by_name("sc3"), 2, 2, C.NoiseModel(0.01, 0.05))),
+           ("tp_sc3", C.teleport_circuit(C.code_by_name("sc3"), 1, 1, C.NoiseModel(0.01, 0.05))),
+           ("nl_bb18", C.nonlocal_cnot_circuit(C.code_by_name("bb18"), 1, 1, C.NoiseModel(0.01, 0.05))),
+           ("ps3_sc3", C.pauli_string_circuit(C.code_by_name("sc3"), 3, rounds_before=1,
+                                              noise=C.NoiseModel(0.01, 0.01))),
+           ("deco_sc3", C.nonlocal_cnot_circuit(C.code_by_name("sc3"), 1, 1,
+                                                C.NoiseModel(0.003, 0.02, decoherence=C.Decoherence(0.05))))]
+    for t in range(6):
+        rng = np.random.default_rng(1700 + t)
+        out.append((f"rand{t}", random_noisy_circuit(rng, int(rng.integers(2, 9)), int(rng.integers(4, 40)))))
+    return out
+
+
+@pytest.mark.parametrize("case", _sig_cases(), ids=lambda c: c[0])
+def test_event_signatures_equal_oracle_dem(tmcs, case):
+    """The host event-signature table (transposed frame pass) gives, for every
+    elementary fault, exactly the detectors and observables the oracle's
+    forward single-fault propagation flips."""
+    from oracle import dem
+    _, circ = case
+    dets, obss, _, _ = dem.signatures(circ)
+    h = tmcs.tmcs_circuit_build(circ)
+    try:
+        assert tmcs.tmcs_circuit_stats(h)["sig_ok"] == 1
+        assert tmcs.tmcs_fault_count(h) == len(dets)
+        for f, (dm, om) in enumerate(zip(dets, obss)):
+            gd, go = tmcs.tmcs_fault_outputs(h, f)
+            assert gd == [j for j in range(circ.n_det) if dm >> j & 1], f
+            assert go == [j for j in range(circ.n_obs) if om >> j & 1], f
+    finally:
+        tmcs.tmcs_circuit_free(h)
+
+
+@pytest.mark.parametrize("window", [1024, 2048])
+def test_signature_window_forces_steps(tmcs, window, monkeypatch):
+    """A detector ring smaller than the circuit's detector count splits the
+    noise segments into several flush steps; every segment is walked."""
+    monkeypatch.setenv("TMCS_SIG_WINDOW", str(window))
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc11"), 11, 11, C.NoiseModel(0.001, 0.01))
+    h = tmcs.tmcs_circuit_build(circ)
+    try:
+        st = tmcs.tmcs_circuit_stats(h)
+        assert st["sig_ok"] == 1 and st["sig_window"] == window and st["sig_steps"] > 1
+        assert st["sig_items"] == st["n_noise_segments"]
+    finally:
+        tmcs.tmcs_circuit_free(h)

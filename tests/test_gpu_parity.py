@@ -188,6 +188,49 @@ def test_every_launch_shape_is_bit_exact(monkeypatch, kernel, tile_k, threads, w
     assert_parity(circ, 64 * 53 + 17, seed=21)
 
 
+@pytest.mark.parametrize("tile_k,threads", [(1, 256), (1, 1024), (2, 512), (4, 256), (4, 1024), (8, 512)])
+@pytest.mark.parametrize("window", [0, 1024])
+def test_signature_kernel_shapes_are_bit_exact(monkeypatch, tile_k, threads, window):
+    """The event-signature kernel under every chunks-per-CTA / CTA-size
+    choice, with the default detector ring and with a 1024-detector ring that
+    splits the circuit into several flush steps, reproduces the oracle."""
+    monkeypatch.setenv("TMCS_KERNEL", "5")
+    monkeypatch.setenv("TMCS_TILE_K", str(tile_k))
+    monkeypatch.setenv("TMCS_THREADS", str(threads))
+    if window:
+        monkeypatch.setenv("TMCS_SIG_WINDOW", str(window))
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc9"), 9, 9, C.NoiseModel(0.004, 0.03))
+    h = tmcs.tmcs_circuit_build(circ)
+    st = tmcs.tmcs_circuit_stats(h)
+    tmcs.tmcs_circuit_free(h)
+    assert st["sig_ok"] == 1 and (window == 0 or st["sig_steps"] > 1)
+    assert_parity(circ, 64 * 41 + 29, seed=23, first_chunk=7)
+
+
+@pytest.mark.parametrize("queue", [1, 64])
+def test_signature_kernel_queue_overflow(monkeypatch, queue):
+    """Events that find the shared event queue full are applied directly:
+    a tiny queue under heavy noise still reproduces the oracle."""
+    monkeypatch.setenv("TMCS_KERNEL", "5")
+    monkeypatch.setenv("TMCS_SIG_QUEUE", str(queue))
+    circ = C.teleport_circuit(C.code_by_name("bb18"), 2, 2, C.NoiseModel(0.03, 0.1))
+    assert_parity(circ, 64 * 23 + 5, seed=31)
+
+
+def test_signature_kernel_observables_only():
+    """No detectors at all: the kernel still writes every observable word."""
+    circ = C.Circuit()
+    circ.append("R", [0, 1, 2])
+    circ.append("X_ERROR", [0, 1, 2], p=0.2)
+    circ.append("CX", [0, 1])
+    circ.append("DEPOLARIZE2", [0, 1], p=0.1)
+    circ.append("M", [0, 1, 2])
+    circ.append("OBSERVABLE", [0, 2], arg=0)
+    circ.append("OBSERVABLE", [1], arg=1)
+    _, go = assert_parity(circ, 64 * 5 + 3, seed=3)
+    assert go.any()
+
+
 def test_autotuned_large_call_matches_forced_shape(monkeypatch):
     """A call large enough to trigger the autotuner equals a forced-shape call."""
     circ = C.nonlocal_cnot_circuit(C.code_by_name("sc5"), 3, 3, C.NoiseModel(0.003, 0.03))
