@@ -132,6 +132,7 @@ typedef struct {
     uint64_t sig_generators;  /* X/Z generators of all noise units */
     uint64_t sig_entries;     /* (generator, output) pairs */
     uint64_t sig_build_us;    /* host time to build it, microseconds */
+    uint64_t sig_max_step_items; /* segments in the largest step */
 } tmcs_stats;
 int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out);
 

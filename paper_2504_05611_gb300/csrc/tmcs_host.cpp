@@ -1129,7 +1129,7 @@ int tmcs_circuit_build(const tmcs_op *ops, size_t n_ops, uint32_t flags, tmcs_ci
         int rc = compile(c, flags, false);
         if (rc) { delete c; return rc; }
         const char *wenv = std::getenv("TMCS_SIG_WINDOW");
-        const uint32_t max_window = (wenv && *wenv) ? uint32_t(std::atoi(wenv)) : 8192u;
+        const uint32_t max_window = (wenv && *wenv) ? uint32_t(std::atoi(wenv)) : 4096u;
         rc = build_signature_program(c, max_window);
         if (rc) { delete c; return rc; }
     } catch (const std::bad_alloc &) {
@@ -1176,6 +1176,9 @@ int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out) {
     out->sig_generators = G.gen_off.empty() ? 0 : G.gen_off.size() - 1;
     out->sig_entries = G.gen_ent.size();
     out->sig_build_us = uint64_t(G.build_seconds * 1e6);
+    out->sig_max_step_items = 0;
+    for (const SigStep &st : G.steps)
+        out->sig_max_step_items = std::max<uint64_t>(out->sig_max_step_items, st.item_end - st.item_begin);
     return TMCS_OK;
 }
 

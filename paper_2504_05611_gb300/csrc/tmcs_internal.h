@@ -161,6 +161,10 @@ struct SigProgram {
                                      // (host); the device copy carries unit_base there
     std::vector<uint32_t> tables;    // kTableWords per distinct p
     std::vector<uint32_t> items;     // (descriptor, segment) pairs, 2 words per item
+    // Device item records, 4 words per item: op index, segment, global index
+    // of the segment's first unit, kind | table << 3 | (units - 1) << 16 |
+    // descriptor << 22 (descriptor < 1024, table < 8192).
+    std::vector<uint32_t> item_rec;
     std::vector<SigStep> steps;
     std::vector<uint32_t> gen_off;   // CSR offsets per generator (n_gens + 1)
     std::vector<uint32_t> gen_ent;   // detector index, or kSigObsFlag | observable index

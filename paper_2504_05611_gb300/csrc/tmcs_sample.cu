@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(512) frame_kernel(const KernelArgs P) {
 struct SigArgs {
     const NoiseDesc *noise;   // tgt_off = first global unit index of the descriptor
     const uint32_t *tables;
-    const uint2 *items;       // (descriptor, segment)
+    const uint4 *item_rec;    // per item: op index, segment, first unit, kind | table << 3 | (units-1) << 16 | desc << 22
     const uint4 *steps;       // SigStep: item_begin, item_end, flush_lo, flush_hi
     const uint32_t *unit_ent; // slot_words words per global unit (count, entries), then overflow
     uint32_t n_steps;
@@ -576,6 +576,7 @@ struct SigArgs {
     uint32_t queue_cap;       // events the shared queue holds
     uint32_t smem_tables;     // gap tables copied to shared memory (0, or all of them)
     uint32_t slot_words;      // 8 or 16
+    uint32_t stage_items;     // shared staging buffer for a step's item records (0: read them from global)
     uint32_t key0, key1;
     uint32_t first_chunk;
     uint64_t n_cols, last_mask, n_tiles;
@@ -661,12 +662,6 @@ __device__ __forceinline__ void sig_apply_events(const SigArgs &A, const uint64_
     }
 }
 
-__device__ __forceinline__ void sig_apply_event(const SigArgs &A, uint64_t q, uint64_t *ring, uint64_t *oacc,
-                                                int K) {
-    const uint64_t qq[1] = {q};
-    sig_apply_events<1>(A, qq, 1, ring, oacc, K);
-}
-
 // Warp-aggregated shared counter: the calling lane's index among all lanes
 // that call together (one atomic per warp).
 __device__ __forceinline__ uint32_t grab_index(uint32_t *ctr) {
@@ -679,66 +674,107 @@ __device__ __forceinline__ uint32_t grab_index(uint32_t *ctr) {
     return base + uint32_t(__popc(mask & ((1u << lane) - 1u)));
 }
 
-// Walk phase of one step: every lane holds one (segment, chunk) stream and
-// runs one Philox call (two draws) of it per iteration; a lane whose stream
-// ends takes the next from the step's counter, so the warp stays converged on
-// the generator. Events go to the shared queue (or, when it is full, straight
-// to the ring). tabs: the gap tables, in shared memory when SMT.
+// Applies the n events of a warp's queue slice, converged: lane l takes
+// events l, l + 32, ... four at a time. Called by all 32 lanes.
+__device__ __forceinline__ void sig_warp_apply(const SigArgs &A, const uint64_t *wq, uint32_t n, uint64_t *ring,
+                                               uint64_t *oacc, int K) {
+    __syncwarp();
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t e0 = lane; e0 < n; e0 += 128u) {
+        uint64_t qb[4];
+        int nb = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t e = e0 + 32u * uint32_t(j);
+            qb[j] = e < n ? wq[e] : 0ull;
+            nb += e < n ? 1 : 0;
+        }
+        sig_apply_events<4>(A, qb, nb, ring, oacc, K);
+    }
+    __syncwarp();
+}
+
+// Walk phase of one step for one warp: every lane holds one (segment, chunk)
+// stream and runs one Philox call (two draws) of it per iteration; a lane
+// whose stream ends takes the next from the step's counter, so the warp stays
+// converged on the generator. Events go to the warp's own queue slice at
+// offsets from a ballot (no atomics); events that find the slice full are
+// applied at once by their lanes. Returns the number of queued events.
+// tabs: the gap tables, in shared memory when SMT.
 template <bool SMT>
-__device__ __forceinline__ void sig_walk(const SigArgs &A, const uint4 st, uint32_t n, uint32_t nvalid,
-                                         uint32_t chunk0, const uint32_t *tabs, uint64_t *queue, uint32_t qcap,
-                                         uint32_t *s_next, uint32_t *s_qn, uint64_t *ring, uint64_t *oacc, int K) {
-    bool have = false;
+__device__ __forceinline__ uint32_t sig_walk(const SigArgs &A, const uint4 st, uint32_t n, uint32_t nvalid,
+                                             uint32_t chunk0, const uint32_t *tabs, const uint4 *sitems,
+                                             uint64_t *wq, uint32_t wcap, uint32_t *s_next, uint64_t *ring,
+                                             uint64_t *oacc, int K) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t qn = 0;  // events in the slice (warp-uniform)
+    bool have = false, exhausted = false;
     uint32_t call = 0, seg = 0, op = 0, kind = 0, chunk = 0, ubase = 0, tag = 0, t1 = 0, t2 = 0, npauli = 1;
     int pos = -1, n_trials = 0;
     const uint32_t *Tt = tabs;
     float inv = 0.f;
     for (;;) {
-        if (!have) {
+        if (!have && !exhausted) {
             const uint32_t i = grab_index(s_next);
+            exhausted = i >= n;
             if (i < n) {
-                const uint32_t it = st.x + i / uint32_t(nvalid);
-                const uint32_t k = i % uint32_t(nvalid);
-                const uint2 item = __ldg(A.items + it);
-                const NoiseDesc nd = A.noise[item.x];
-                Tt = tabs + size_t(nd.table) * kTableWords;
+                const uint32_t il = i / nvalid;
+                const uint32_t k = i % nvalid;
+                const uint4 rec = sitems ? sitems[il] : __ldg(A.item_rec + st.x + il);
+                kind = rec.w & 7u;
+                Tt = tabs + size_t((rec.w >> 3) & 0x1FFFu) * kTableWords;
                 inv = __uint_as_float(Tt[kGapLen]);
-                seg = item.y;
-                op = nd.op_index;
-                kind = nd.kind;
-                t1 = nd.t1;
-                t2 = nd.t2;
-                npauli = npauli_of(nd.kind);
+                seg = rec.y;
+                op = rec.x;
+                if (kind == N_PC1) {
+                    t1 = A.noise[rec.w >> 22].t1;
+                    t2 = A.noise[rec.w >> 22].t2;
+                }
+                npauli = npauli_of(kind);
                 chunk = chunk0 + k;
-                ubase = nd.tgt_off + item.y * kSegUnits;
-                tag = (k << 6) | (nd.kind << 13);
-                n_trials = 64 * int(min(kSegUnits, nd.n_units - item.y * kSegUnits));
+                ubase = rec.z;
+                tag = (k << 6) | (kind << 13);
+                n_trials = 64 * int(((rec.w >> 16) & 63u) + 1u);
                 call = 0;
                 pos = -1;
                 have = true;
             }
         }
         if (!__any_sync(0xFFFFFFFFu, have)) break;
-        if (!have) continue;
-        const uint4 w = philox4x32_10(call, chunk, op, seg, A.key0, A.key1);
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (have) w = philox4x32_10(call, chunk, op, seg, A.key0, A.key1);
         call++;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-            if (!have) break;
-            const uint32_t wg = h ? w.z : w.x, wp = h ? w.w : w.y;
-            pos += 1 + gap_count_t<SMT>(Tt, inv, wg);
-            if (pos >= n_trials) {
-                have = false;
-                break;
+            bool ev = false;
+            uint64_t q = 0;
+            if (have) {
+                const uint32_t wg = h ? w.z : w.x, wp = h ? w.w : w.y;
+                pos += 1 + gap_count_t<SMT>(Tt, inv, wg);
+                if (pos >= n_trials) {
+                    have = false;
+                } else {
+                    const uint32_t pk = kind == N_PC1 ? (wp < t1 ? 1u : wp < t2 ? 3u : 2u)
+                                                      : 1u + __umulhi(wp, npauli);
+                    q = uint64_t(ubase + uint32_t(pos >> 6)) | (uint64_t(tag | uint32_t(pos & 63) | (pk << 9)) << 32);
+                    ev = true;
+                }
             }
-            const uint32_t pk = kind == N_PC1 ? (wp < t1 ? 1u : wp < t2 ? 3u : 2u) : 1u + __umulhi(wp, npauli);
-            const uint64_t q = uint64_t(ubase + uint32_t(pos >> 6)) |
-                               (uint64_t(tag | uint32_t(pos & 63) | (pk << 9)) << 32);
-            const uint32_t slot = grab_index(s_qn);
-            if (slot < qcap) queue[slot] = q;
-            else sig_apply_event(A, q, ring, oacc, K);
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, ev);
+            if (m) {
+                const uint32_t c = uint32_t(__popc(m));
+                if (qn + c <= wcap) {
+                    if (ev) wq[qn + uint32_t(__popc(m & lt))] = q;
+                    qn += c;
+                } else if (ev) {
+                    const uint64_t q1[1] = {q};
+                    sig_apply_events<1>(A, q1, 1, ring, oacc, K);
+                }
+            }
         }
     }
+    return qn;
 }
 
 // Per step: (1) threads take (segment, chunk) streams from a shared counter
@@ -749,51 +785,45 @@ __device__ __forceinline__ void sig_walk(const SigArgs &A, const uint4 st, uint3
 template <int K>
 __global__ void __launch_bounds__(1024) sig_kernel(const SigArgs A) {
     extern __shared__ __align__(128) uint64_t smem[];
-    __shared__ uint32_t s_next, s_qn;
+    __shared__ uint32_t s_next;
     const uint32_t W = A.window_mask + 1u;
+    // layout (same as sig_smem_bytes): ring, observables (padded to 16
+    // bytes), gap tables, staged item records, event queue
     uint64_t *ring = smem;
     uint64_t *oacc = smem + size_t(W) * K;
-    uint32_t *stab = reinterpret_cast<uint32_t *>(oacc + size_t(A.n_obs) * K);
-    uint64_t *queue = reinterpret_cast<uint64_t *>(stab + size_t(A.smem_tables) * kTableWords);
+    uint32_t *stab = reinterpret_cast<uint32_t *>(smem + ((size_t(W + A.n_obs) * K + 1) & ~size_t(1)));
+    uint4 *sitems_buf = reinterpret_cast<uint4 *>(stab + size_t(A.smem_tables) * kTableWords);
+    const uint4 *sitems = A.stage_items ? sitems_buf : nullptr;
+    uint64_t *queue = reinterpret_cast<uint64_t *>(sitems_buf + A.stage_items);
     const uint32_t qcap = A.queue_cap;
     const uint32_t T_ = blockDim.x, tid = threadIdx.x;
     for (uint32_t i = tid; i < (W + A.n_obs) * K; i += T_) smem[i] = 0ull;
     for (uint32_t i = tid; i < A.smem_tables * kTableWords; i += T_) stab[i] = __ldg(A.tables + i);
-    if (tid == 0) {
-        s_next = 0;
-        s_qn = 0;
-    }
+    if (tid == 0) s_next = 0;
     __syncthreads();
+    const uint32_t wcap = qcap / (T_ >> 5);  // queue slice per warp
     for (uint64_t tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
         const uint64_t col0 = tile * K;
         const uint64_t rem = A.n_cols - col0;
         const int nvalid = rem < uint64_t(K) ? int(rem) : K;
         const uint32_t chunk0 = A.first_chunk + uint32_t(col0);
+        if (A.stage_items) {
+            const uint4 s0 = __ldg(A.steps);
+            for (uint32_t i = tid; i < s0.y - s0.x; i += T_) sitems_buf[i] = __ldg(A.item_rec + s0.x + i);
+            __syncthreads();
+        }
         for (uint32_t si = 0; si < A.n_steps; si++) {
             const uint4 st = __ldg(A.steps + si);
             const uint32_t n = (st.y - st.x) * uint32_t(nvalid);
-            if (A.smem_tables)
-                sig_walk<true>(A, st, n, uint32_t(nvalid), chunk0, stab, queue, qcap, &s_next, &s_qn, ring, oacc, K);
-            else
-                sig_walk<false>(A, st, n, uint32_t(nvalid), chunk0, A.tables, queue, qcap, &s_next, &s_qn, ring, oacc, K);
+            uint64_t *wq = queue + size_t(tid >> 5) * wcap;
+            const uint32_t left =
+                A.smem_tables
+                    ? sig_walk<true>(A, st, n, uint32_t(nvalid), chunk0, stab, sitems, wq, wcap, &s_next, ring, oacc, K)
+                    : sig_walk<false>(A, st, n, uint32_t(nvalid), chunk0, A.tables, sitems, wq, wcap, &s_next, ring,
+                                      oacc, K);
+            sig_warp_apply(A, wq, left, ring, oacc, K);
             __syncthreads();
-            const uint32_t nq = min(s_qn, qcap);
-            for (uint32_t e0 = tid; e0 < nq; e0 += 4 * T_) {
-                uint64_t qb[4];
-                int nb = 0;
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const uint32_t e = e0 + uint32_t(j) * T_;
-                    qb[j] = e < nq ? queue[e] : 0ull;
-                    nb += e < nq ? 1 : 0;
-                }
-                sig_apply_events<4>(A, qb, nb, ring, oacc, K);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                s_next = 0;
-                s_qn = 0;
-            }
+            if (tid == 0) s_next = 0;
             const uint32_t nf = (st.w - st.z) * K;
             for (uint32_t i = tid; i < nf; i += T_) {
                 const uint32_t d = st.z + i / K;
@@ -807,7 +837,11 @@ __global__ void __launch_bounds__(1024) sig_kernel(const SigArgs A) {
                 }
                 const uint64_t col = col0 + uint64_t(k);
                 if (col == A.n_cols - 1) v &= A.last_mask;
-                A.det[uint64_t(d) * A.n_cols + col] = v;
+                __stcs(reinterpret_cast<unsigned long long *>(A.det + uint64_t(d) * A.n_cols + col), v);
+            }
+            if (A.stage_items && si + 1 < A.n_steps) {
+                const uint4 s1 = __ldg(A.steps + si + 1);
+                for (uint32_t i = tid; i < s1.y - s1.x; i += T_) sitems_buf[i] = __ldg(A.item_rec + s1.x + i);
             }
             __syncthreads();
         }
@@ -830,20 +864,31 @@ constexpr uint32_t kSigQueueMin = 256;
 
 static size_t sig_table_bytes(const SigProgram &G) { return G.tables.size() * 4; }
 
+// Step item records staged in shared memory: the largest step's, if that
+// is at most 1024 records.
+static uint32_t sig_stage_items(const SigProgram &G) {
+    uint32_t m = 0;
+    for (const SigStep &st : G.steps) m = std::max(m, st.item_end - st.item_begin);
+    return m <= 1024 ? m : 0u;
+}
+
+// ring and observables, padded to 16 bytes
 static size_t sig_ring_bytes(const SigProgram &G, uint64_t n_obs, int K) {
-    return (size_t(G.window) + size_t(n_obs)) * size_t(K) * 8;
+    return ((size_t(G.window) + size_t(n_obs)) * size_t(K) * 8 + 15) & ~size_t(15);
 }
 
 // Ring + observables + event queue: the queue takes what is left of `budget`
 // (at least kSigQueueMin events, at most kSigQueueMax).
 static uint32_t sig_queue_cap(const SigProgram &G, uint64_t n_obs, int K, size_t budget, bool smem_tables) {
-    const size_t ring = sig_ring_bytes(G, n_obs, K) + (smem_tables ? sig_table_bytes(G) : 0);
+    const size_t ring = sig_ring_bytes(G, n_obs, K) + (smem_tables ? sig_table_bytes(G) : 0) +
+                        size_t(sig_stage_items(G)) * 16;
     const size_t left = budget > ring ? (budget - ring) / 8 : 0;
     return uint32_t(std::min<size_t>(kSigQueueMax, std::max<size_t>(kSigQueueMin, left & ~size_t(255))));
 }
 
 static size_t sig_smem_bytes(const SigProgram &G, uint64_t n_obs, int K, uint32_t qcap, bool smem_tables) {
-    return sig_ring_bytes(G, n_obs, K) + (smem_tables ? sig_table_bytes(G) : 0) + size_t(qcap) * 8;
+    return sig_ring_bytes(G, n_obs, K) + (smem_tables ? sig_table_bytes(G) : 0) + size_t(sig_stage_items(G)) * 16 +
+           size_t(qcap) * 8;
 }
 
 // ---------------------------------------------------------------------------
@@ -1296,7 +1341,7 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
     const SigProgram &G = c->sig;
     const size_t b_noise = align256(G.noise.size() * sizeof(NoiseDesc));
     const size_t b_tables = align256(G.tables.size() * 4);
-    const size_t b_items = align256(G.items.size() * 4);
+    const size_t b_items = align256(G.item_rec.size() * 4);
     const size_t b_steps = align256(G.steps.size() * sizeof(SigStep));
     const size_t b_ent = align256(G.unit_ent.size() * 4);
     const size_t total = std::max<size_t>(b_noise + b_tables + b_items + b_steps + b_ent, 256);
@@ -1312,7 +1357,7 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
     for (size_t i = 0; i < dn.size(); i++) dn[i].tgt_off = G.unit_base[i];
     const size_t o_noise = put(dn.data(), dn.size() * sizeof(NoiseDesc), b_noise);
     const size_t o_tables = put(G.tables.data(), G.tables.size() * 4, b_tables);
-    const size_t o_items = put(G.items.data(), G.items.size() * 4, b_items);
+    const size_t o_items = put(G.item_rec.data(), G.item_rec.size() * 4, b_items);
     const size_t o_steps = put(G.steps.data(), G.steps.size() * sizeof(SigStep), b_steps);
     const size_t o_ent = put(G.unit_ent.data(), G.unit_ent.size() * 4, b_ent);
     void *base = nullptr;
@@ -1468,6 +1513,8 @@ static LaunchShape make_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const 
     s.qcap = sig_queue_cap(c->sig, c->n_obs, K, budget, s.smem_tables);
     const int qforce = env_int("TMCS_SIG_QUEUE", 0);  // tuning/testing knob: queue capacity
     if (qforce > 0) s.qcap = uint32_t(std::min<int>(qforce, int(kSigQueueMax)));
+    // every warp's slice holds at least one ballot's worth (32 events)
+    s.qcap = std::max<uint32_t>(s.qcap, uint32_t(threads));
     s.smem = sig_smem_bytes(c->sig, c->n_obs, K, s.qcap, s.smem_tables);
     const uint64_t n_tiles = (n_cols + K - 1) / K;
     s.tiles = std::min<uint64_t>(n_tiles, uint64_t(lim.sms) * ctas);
@@ -1550,7 +1597,7 @@ static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream
         SigArgs a{};
         a.noise = ds->noise;
         a.tables = ds->tables;
-        a.items = reinterpret_cast<const uint2 *>(ds->items);
+        a.item_rec = reinterpret_cast<const uint4 *>(ds->items);
         a.steps = reinterpret_cast<const uint4 *>(ds->steps);
         a.unit_ent = ds->unit_ent;
         a.n_steps = uint32_t(G->steps.size());
@@ -1559,6 +1606,7 @@ static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream
         a.queue_cap = s.qcap;
         a.smem_tables = s.smem_tables ? uint32_t(G->tables.size() / kTableWords) : 0u;
         a.slot_words = G->slot_words;
+        a.stage_items = sig_stage_items(*G);
         a.key0 = a0.key0;
         a.key1 = a0.key1;
         a.first_chunk = a0.first_chunk;
@@ -1696,7 +1744,7 @@ static LaunchShape choose_shape_sig(const tmcs_circuit *c, uint64_t n_cols, cons
         while (K > 1 && 2 * (sig_smem_bytes(c->sig, c->n_obs, K, kSigQueueMin, false) + 1024) > lim.smem_per_sm) K >>= 1;
         while (K > 1 && (n_cols + K - 1) / K < uint64_t(2 * lim.sms)) K >>= 1;
     }
-    int threads = 512;
+    int threads = K >= 4 ? 1024 : 512;
     const int tforce = env_int("TMCS_THREADS", 0);
     if (tforce >= 32 && tforce <= 1024 && tforce % 32 == 0) threads = tforce;
     return make_shape_sig(c, n_cols, lim, K, threads);

@@ -412,6 +412,42 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
             i = j;
         }
         if (G.steps.empty() || F < D) G.steps.push_back({uint32_t(n_items), uint32_t(n_items), uint32_t(F), uint32_t(D)});
+        // within a step, longest streams first (expected draws ~ p x units),
+        // so the step's tail is short; order within a step does not change
+        // the output (events XOR into the ring)
+        std::vector<uint32_t> perm(n_items);
+        for (size_t i = 0; i < n_items; i++) perm[i] = uint32_t(i);
+        for (const SigStep &st : G.steps) {
+            auto cost = [&](uint32_t i) {
+                const NoiseDesc &nd = G.noise[G.items[2 * i]];
+                const uint32_t units = std::min(kSegUnits, nd.n_units - G.items[2 * i + 1] * kSegUnits);
+                return table_p[nd.table] * double(units);
+            };
+            std::stable_sort(perm.begin() + st.item_begin, perm.begin() + st.item_end,
+                             [&](uint32_t a, uint32_t b) { return cost(a) > cost(b); });
+        }
+        std::vector<uint32_t> items2(G.items.size());
+        for (size_t i = 0; i < n_items; i++) {
+            items2[2 * i] = G.items[2 * perm[i]];
+            items2[2 * i + 1] = G.items[2 * perm[i] + 1];
+        }
+        G.items.swap(items2);
+    }
+    // device item records (the walk reads one 16-byte record per stream)
+    if (G.noise.size() > 1024 || G.tables.size() / kTableWords > 8192) {
+        G.why = "too many noise ops or distinct probabilities for the device item records";
+        G.items.clear();
+        G.steps.clear();
+        return TMCS_OK;
+    }
+    for (size_t i = 0; i < n_items; i++) {
+        const uint32_t di = G.items[2 * i], sg = G.items[2 * i + 1];
+        const NoiseDesc &nd = G.noise[di];
+        const uint32_t units = std::min(kSegUnits, nd.n_units - sg * kSegUnits);
+        G.item_rec.push_back(nd.op_index);
+        G.item_rec.push_back(sg);
+        G.item_rec.push_back(G.unit_base[di] + sg * kSegUnits);
+        G.item_rec.push_back(nd.kind | (nd.table << 3) | ((units - 1) << 16) | (di << 22));
     }
     G.ok = true;
     G.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();

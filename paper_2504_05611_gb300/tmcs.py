@@ -35,7 +35,7 @@ assert OP_DTYPE.itemsize == 32
 STATS_FIELDS = ("n_layers", "n_slots", "n_xor", "n_zero", "n_copy", "n_noise_ops", "n_noise_units",
                 "n_noise_segments", "n_parity_terms", "live_components", "pruned_updates",
                 "sig_ok", "sig_window", "sig_steps", "sig_items", "sig_generators", "sig_entries",
-                "sig_build_us")
+                "sig_build_us", "sig_max_step_items")
 
 
 class TmcsError(RuntimeError):
