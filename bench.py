@@ -250,12 +250,18 @@ def main():
     avg_launch_s = statistics.mean(launch_ms) / 1e3
     peak, peak_kind = measured_peaks()
     achieved = out_bytes / avg_launch_s / 1e9
+    # the kernel the autotuner picked for this workload, and its DRAM traffic
+    # per launch from an ncu capture of the same kernel build, if committed
+    shape = tmcs.tmcs_launch_shape(sampler.handle)
+    kernel = shape["kernel"] or "autotuner not run (call below its size threshold)"
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "frame_kernel_traffic.json")
-    if os.path.exists(prof):
-        with open(prof) as f:
+    sha = _kernel_sha()
+    for fn in sorted(os.listdir(os.path.join(ROOT, "profiles"))):
+        if not fn.endswith("_traffic.json"):
+            continue
+        with open(os.path.join(ROOT, "profiles", fn)) as f:
             p = json.load(f)
-        if p.get("workload") == workload.name and p.get("kernel_sha") == _kernel_sha():
+        if p.get("workload") == workload.name and p.get("kernel") == kernel and p.get("kernel_sha") == sha:
             traffic = p.get("dram_bytes_per_launch")
 
     # end-to-end through the public API with host buffers: per step, sample
@@ -339,7 +345,7 @@ def main():
                          "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
                          else "fallback 6.8 TB/s",
                          "algorithmic_bytes_per_launch": out_bytes, "avg_launch_ms": avg_launch_s * 1e3,
-                         "kernel": "frame_kernel"},
+                         "kernel": kernel},
             "clocks": clk,
             "gpu_launches": args.steps,
             "e2e": e2e,
@@ -547,7 +553,7 @@ def serve_bench(args):
 def _kernel_sha():
     import hashlib
     h = hashlib.sha256()
-    for f in ("tmcs_sample.cu", "tmcs_internal.h", "tmcs_host.cpp"):
+    for f in ("tmcs_sample.cu", "tmcs_internal.h", "tmcs_host.cpp", "tmcs_signature.cpp"):
         with open(os.path.join(ROOT, "paper_2504_05611_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

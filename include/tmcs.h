@@ -274,6 +274,16 @@ int tmcs_batch_sample(const tmcs_job *jobs, size_t n_jobs, void *stream);
 int tmcs_check_device(void);
 
 /*
+ * The launch shape the autotuner chose for this circuit on the current
+ * device (for reports): *mode = 0 if it has not run yet (first large call),
+ * 3 = CTA-wide frame kernel, 4 = warp-group frame kernel, 5 = event-signature
+ * kernel; *chunks = 64-shot chunks per CTA (mode 3, 5) or per warp group
+ * (mode 4); *threads = CTA size. Any pointer may be NULL.
+ * Errors: TMCS_E_INVALID (NULL circuit), TMCS_E_CUDA (no current device).
+ */
+int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *threads);
+
+/*
  * Sampling server (continuous batching). A host scheduler thread admits
  * submitted requests in arrival order as soon as their output words fit in a
  * device arena (admission by HBM footprint), cuts every admitted request into

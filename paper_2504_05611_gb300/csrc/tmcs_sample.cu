@@ -2205,6 +2205,20 @@ int tmcs_check_device(void) {
     return TMCS_OK;
 }
 
+int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *threads) {
+    if (!c) return fail(TMCS_E_INVALID, "circuit is NULL");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(c->mu);
+    auto it = c->dev.find(dev);
+    const DeviceProgram *dp = it == c->dev.end() ? nullptr : &it->second;
+    if (mode) *mode = dp ? dp->tuned_mode : 0;
+    if (chunks) *chunks = dp ? dp->tuned_K : 0;
+    if (threads) *threads = dp ? dp->tuned_threads : 0;
+    return TMCS_OK;
+}
+
 int tmcs_batch_sample(const tmcs_job *jobs, size_t n_jobs, void *stream) {
     return batch_sample(jobs, n_jobs, stream);
 }

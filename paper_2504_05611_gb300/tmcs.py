@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
         L.tmcs_fault_signatures.argtypes = [P, U64, U64, P, P, P]
         L.tmcs_sample_measurements.argtypes = [P, U64, U64, U64, P, P]
         L.tmcs_fault_outputs.argtypes = [P, U64, P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
+        L.tmcs_launch_shape.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
         L.tmcs_server_open.argtypes = [P, ctypes.POINTER(P)]
         L.tmcs_server_submit.argtypes = [P, P, U64, U64, ctypes.POINTER(ctypes.c_uint64)]
         L.tmcs_server_poll.argtypes = [P, U64, ctypes.POINTER(ctypes.c_int)]
@@ -112,7 +113,7 @@ def lib() -> ctypes.CDLL:
                   "tmcs_debug_gap_table", "tmcs_check_device", "tmcs_sample_noalloc", "tmcs_server_open",
                   "tmcs_server_submit", "tmcs_server_poll", "tmcs_server_fetch", "tmcs_server_release",
                   "tmcs_server_get_stats", "tmcs_server_close", "tmcs_fault_count", "tmcs_fault_signatures",
-                  "tmcs_sample_measurements", "tmcs_fault_outputs"):
+                  "tmcs_sample_measurements", "tmcs_fault_outputs", "tmcs_launch_shape"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -321,6 +322,19 @@ def tmcs_sample_measurements(handle: int, first_chunk: int, shots: int, seed: in
     _check_size(meas, info["n_meas"], cols, "measurement")
     _check(lib().tmcs_sample_measurements(ctypes.c_void_p(handle), first_chunk, shots, seed & (2 ** 64 - 1),
                                           _dev_ptr(meas), _stream_ptr(stream)))
+
+
+KERNEL_NAMES = {3: "frame_kernel", 4: "frame_kernel_w", 5: "sig_kernel"}
+
+
+def tmcs_launch_shape(handle: int) -> Dict[str, object]:
+    """Autotuned launch shape on the current device: mode (0 = not tuned),
+    chunks per CTA (or per warp group), CTA size, and the kernel's name."""
+    m, k, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().tmcs_launch_shape(ctypes.c_void_p(handle), ctypes.byref(m), ctypes.byref(k), ctypes.byref(t)))
+    name = KERNEL_NAMES.get(m.value)
+    return {"mode": m.value, "chunks": k.value, "threads": t.value,
+            "kernel": f"{name}<{k.value}> ({t.value} threads)" if name else None}
 
 
 def tmcs_batch_sample(jobs: Sequence[Tuple[int, int, int, object, object]], stream=None) -> None:
