@@ -777,85 +777,156 @@ __device__ __forceinline__ uint32_t sig_walk(const SigArgs &A, const uint4 st, u
     return qn;
 }
 
-// Per step: (1) threads take (segment, chunk) streams from a shared counter
-// and walk them, appending each event to a shared queue (an event that finds
-// the queue full is applied at once); (2) all threads apply the queued events,
-// one per thread, so the output lookups and ring updates run converged;
-// (3) the step's final detectors are written out and cleared.
+// Shared-memory regions of one circuit's layout (same order and sizes as
+// sig_smem_bytes): detector ring, observables (padded to 16 bytes), gap
+// tables, staged item records, event queue.
+struct SigSmem {
+    uint64_t *ring, *oacc;
+    uint32_t *stab;
+    uint4 *sitems_buf;
+    uint64_t *queue;
+};
+
+__device__ __forceinline__ SigSmem sig_layout(uint64_t *smem, const SigArgs &A, int K) {
+    SigSmem S;
+    const size_t W = size_t(A.window_mask) + 1;
+    S.ring = smem;
+    S.oacc = smem + W * K;
+    S.stab = reinterpret_cast<uint32_t *>(smem + (((W + A.n_obs) * K + 1) & ~size_t(1)));
+    S.sitems_buf = reinterpret_cast<uint4 *>(S.stab + size_t(A.smem_tables) * kTableWords);
+    S.queue = reinterpret_cast<uint64_t *>(S.sitems_buf + A.stage_items);
+    return S;
+}
+
+// Clears the ring and observables and loads the gap tables of circuit A
+// (all threads; ends with a barrier).
+template <int K>
+__device__ __forceinline__ void sig_setup(const SigArgs &A, const SigSmem &S) {
+    const uint32_t T_ = blockDim.x, tid = threadIdx.x;
+    const uint32_t W = A.window_mask + 1u;
+    for (uint32_t i = tid; i < (W + A.n_obs) * K; i += T_) S.ring[i] = 0ull;
+    for (uint32_t i = tid; i < A.smem_tables * kTableWords; i += T_) S.stab[i] = __ldg(A.tables + i);
+    __syncthreads();
+}
+
+// One tile of K chunks, all threads. Per step: (1) every warp walks
+// (segment, chunk) streams taken from a shared counter and queues its events
+// in its own slice of the queue; (2) every warp applies its slice; (3) after
+// a barrier the step's final detectors are written out and cleared. Leaves
+// the ring, the observables and the counter clean for the next tile.
+template <int K>
+__device__ __forceinline__ void sig_tile(const SigArgs &A, const SigSmem &S, uint64_t tile, uint32_t *s_next) {
+    const uint32_t T_ = blockDim.x, tid = threadIdx.x;
+    const uint32_t W = A.window_mask + 1u;
+    const uint32_t wcap = A.queue_cap / (T_ >> 5);  // queue slice per warp
+    const uint4 *sitems = A.stage_items ? S.sitems_buf : nullptr;
+    const uint64_t col0 = tile * K;
+    const uint64_t rem = A.n_cols - col0;
+    const int nvalid = rem < uint64_t(K) ? int(rem) : K;
+    const uint32_t chunk0 = A.first_chunk + uint32_t(col0);
+    if (A.stage_items) {
+        const uint4 s0 = __ldg(A.steps);
+        for (uint32_t i = tid; i < s0.y - s0.x; i += T_) S.sitems_buf[i] = __ldg(A.item_rec + s0.x + i);
+        __syncthreads();
+    }
+    for (uint32_t si = 0; si < A.n_steps; si++) {
+        const uint4 st = __ldg(A.steps + si);
+        const uint32_t n = (st.y - st.x) * uint32_t(nvalid);
+        uint64_t *wq = S.queue + size_t(tid >> 5) * wcap;
+        const uint32_t left =
+            A.smem_tables
+                ? sig_walk<true>(A, st, n, uint32_t(nvalid), chunk0, S.stab, sitems, wq, wcap, s_next, S.ring, S.oacc, K)
+                : sig_walk<false>(A, st, n, uint32_t(nvalid), chunk0, A.tables, sitems, wq, wcap, s_next, S.ring,
+                                  S.oacc, K);
+        sig_warp_apply(A, wq, left, S.ring, S.oacc, K);
+        __syncthreads();
+        if (tid == 0) *s_next = 0;
+        const uint32_t nf = (st.w - st.z) * K;
+        for (uint32_t i = tid; i < nf; i += T_) {
+            const uint32_t d = st.z + i / K;
+            const int k = int(i % K);
+            if (k >= nvalid) continue;
+            uint64_t v = 0ull;
+            if (d - st.z < W) {
+                uint64_t *r = S.ring + size_t(d & A.window_mask) * K + k;
+                v = *r;
+                *r = 0ull;
+            }
+            const uint64_t col = col0 + uint64_t(k);
+            if (col == A.n_cols - 1) v &= A.last_mask;
+            __stcs(reinterpret_cast<unsigned long long *>(A.det + uint64_t(d) * A.n_cols + col), v);
+        }
+        if (A.stage_items && si + 1 < A.n_steps) {
+            const uint4 s1 = __ldg(A.steps + si + 1);
+            for (uint32_t i = tid; i < s1.y - s1.x; i += T_) S.sitems_buf[i] = __ldg(A.item_rec + s1.x + i);
+        }
+        __syncthreads();
+    }
+    for (uint32_t i = tid; i < A.n_obs * K; i += T_) {
+        const uint32_t o = i / K;
+        const int k = int(i % K);
+        uint64_t v = S.oacc[i];
+        S.oacc[i] = 0ull;
+        if (k >= nvalid) continue;
+        const uint64_t col = col0 + uint64_t(k);
+        if (col == A.n_cols - 1) v &= A.last_mask;
+        A.obs[uint64_t(o) * A.n_cols + col] = v;
+    }
+    __syncthreads();
+}
+
+// One circuit: persistent CTAs take tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 template <int K>
 __global__ void __launch_bounds__(1024) sig_kernel(const SigArgs A) {
     extern __shared__ __align__(128) uint64_t smem[];
     __shared__ uint32_t s_next;
-    const uint32_t W = A.window_mask + 1u;
-    // layout (same as sig_smem_bytes): ring, observables (padded to 16
-    // bytes), gap tables, staged item records, event queue
-    uint64_t *ring = smem;
-    uint64_t *oacc = smem + size_t(W) * K;
-    uint32_t *stab = reinterpret_cast<uint32_t *>(smem + ((size_t(W + A.n_obs) * K + 1) & ~size_t(1)));
-    uint4 *sitems_buf = reinterpret_cast<uint4 *>(stab + size_t(A.smem_tables) * kTableWords);
-    const uint4 *sitems = A.stage_items ? sitems_buf : nullptr;
-    uint64_t *queue = reinterpret_cast<uint64_t *>(sitems_buf + A.stage_items);
-    const uint32_t qcap = A.queue_cap;
-    const uint32_t T_ = blockDim.x, tid = threadIdx.x;
-    for (uint32_t i = tid; i < (W + A.n_obs) * K; i += T_) smem[i] = 0ull;
-    for (uint32_t i = tid; i < A.smem_tables * kTableWords; i += T_) stab[i] = __ldg(A.tables + i);
-    if (tid == 0) s_next = 0;
-    __syncthreads();
-    const uint32_t wcap = qcap / (T_ >> 5);  // queue slice per warp
-    for (uint64_t tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
-        const uint64_t col0 = tile * K;
-        const uint64_t rem = A.n_cols - col0;
-        const int nvalid = rem < uint64_t(K) ? int(rem) : K;
-        const uint32_t chunk0 = A.first_chunk + uint32_t(col0);
-        if (A.stage_items) {
-            const uint4 s0 = __ldg(A.steps);
-            for (uint32_t i = tid; i < s0.y - s0.x; i += T_) sitems_buf[i] = __ldg(A.item_rec + s0.x + i);
-            __syncthreads();
-        }
-        for (uint32_t si = 0; si < A.n_steps; si++) {
-            const uint4 st = __ldg(A.steps + si);
-            const uint32_t n = (st.y - st.x) * uint32_t(nvalid);
-            uint64_t *wq = queue + size_t(tid >> 5) * wcap;
-            const uint32_t left =
-                A.smem_tables
-                    ? sig_walk<true>(A, st, n, uint32_t(nvalid), chunk0, stab, sitems, wq, wcap, &s_next, ring, oacc, K)
-                    : sig_walk<false>(A, st, n, uint32_t(nvalid), chunk0, A.tables, sitems, wq, wcap, &s_next, ring,
-                                      oacc, K);
-            sig_warp_apply(A, wq, left, ring, oacc, K);
-            __syncthreads();
-            if (tid == 0) s_next = 0;
-            const uint32_t nf = (st.w - st.z) * K;
-            for (uint32_t i = tid; i < nf; i += T_) {
-                const uint32_t d = st.z + i / K;
-                const int k = int(i % K);
-                if (k >= nvalid) continue;
-                uint64_t v = 0ull;
-                if (d - st.z < W) {
-                    uint64_t *r = ring + size_t(d & A.window_mask) * K + k;
-                    v = *r;
-                    *r = 0ull;
-                }
-                const uint64_t col = col0 + uint64_t(k);
-                if (col == A.n_cols - 1) v &= A.last_mask;
-                __stcs(reinterpret_cast<unsigned long long *>(A.det + uint64_t(d) * A.n_cols + col), v);
-            }
-            if (A.stage_items && si + 1 < A.n_steps) {
-                const uint4 s1 = __ldg(A.steps + si + 1);
-                for (uint32_t i = tid; i < s1.y - s1.x; i += T_) sitems_buf[i] = __ldg(A.item_rec + s1.x + i);
-            }
-            __syncthreads();
-        }
-        for (uint32_t i = tid; i < A.n_obs * K; i += T_) {
-            const uint32_t o = i / K;
-            const int k = int(i % K);
-            uint64_t v = oacc[i];
-            oacc[i] = 0ull;
-            if (k >= nvalid) continue;
-            const uint64_t col = col0 + uint64_t(k);
-            if (col == A.n_cols - 1) v &= A.last_mask;
-            A.obs[uint64_t(o) * A.n_cols + col] = v;
-        }
+    const SigSmem S = sig_layout(smem, A, K);
+    if (threadIdx.x == 0) s_next = 0;
+    sig_setup<K>(A, S);
+    for (uint64_t tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) sig_tile<K>(A, S, tile, &s_next);
+}
+
+// Many circuits in one persistent launch: work items (job, tile) in job
+// order, taken from a device counter; a CTA re-lays its shared memory out
+// (and reloads gap tables) only when it moves to another job. The job table
+// is a kernel parameter, so a launch is a memset and a kernel node under
+// graph capture.
+constexpr int kMaxSigBatch = 96;
+
+struct SigBatchArgs {
+    SigArgs jobs[kMaxSigBatch];
+    uint64_t item_begin[kMaxSigBatch + 1];  // first work item of each job; [n_jobs] = total
+    uint32_t n_jobs;
+    unsigned long long *counter;
+};
+
+template <int K>
+__global__ void __launch_bounds__(1024) sig_batch_kernel(const __grid_constant__ SigBatchArgs B) {
+    extern __shared__ __align__(128) uint64_t smem[];
+    __shared__ uint32_t s_next;
+    __shared__ unsigned long long s_item;
+    if (threadIdx.x == 0) s_next = 0;
+    int cur = -1;
+    SigSmem S{};
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(B.counter, 1ull);
         __syncthreads();
+        const unsigned long long item = s_item;
+        __syncthreads();
+        if (item >= B.item_begin[B.n_jobs]) break;
+        int lo = 0, hi = int(B.n_jobs) - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (B.item_begin[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const SigArgs &A = B.jobs[lo];
+        if (lo != cur) {
+            S = sig_layout(smem, A, K);
+            sig_setup<K>(A, S);
+            cur = lo;
+        }
+        sig_tile<K>(A, S, item - B.item_begin[lo], &s_next);
     }
 }
 
@@ -1927,6 +1998,134 @@ static cudaError_t batch_side_stream(int dev, cudaStream_t *s, cudaEvent_t *f, c
     return cudaSuccess;
 }
 
+static_assert(sizeof(SigBatchArgs) <= 32000, "batch job table exceeds the kernel parameter limit");
+
+// Batched launch through the event-signature kernel. Two size classes run
+// concurrently (forked stream): circuits whose 8-chunk tile fits in half of an
+// SM's shared memory (512 threads, two CTAs per SM), and the rest (4-chunk
+// tiles, 1024 threads, one CTA per SM). *used = false (nothing launched) if
+// some job cannot take this path; the caller then uses the frame kernels.
+template <int K>
+static cudaError_t launch_sig_batch(const SigBatchArgs &B, int threads, size_t smem, int sms, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(sig_batch_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sig_batch_kernel<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             int(cudaSharedmemCarveoutMaxShared));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sig_batch_kernel<K>, threads, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t items = B.item_begin[B.n_jobs];
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(items, uint64_t(sms) * uint64_t(std::max(per_sm, 1))));
+    sig_batch_kernel<K><<<unsigned(grid), threads, smem, st>>>(B);
+    return cudaGetLastError();
+}
+
+static int sig_batch_sample(const tmcs_job *jobs, size_t n_jobs, cudaStream_t st, const DeviceLimits &lim, int dev,
+                            unsigned long long *counter, bool *used) {
+    *used = false;
+    if (env_int("TMCS_KERNEL", 0) == 3 || env_int("TMCS_KERNEL", 0) == 4) return TMCS_OK;
+    struct Cls {
+        int K, threads;
+        size_t budget;
+    };
+    // dynamic shared memory budgets leave 1 KB for the kernel's static shared
+    // variables (dynamic + static must fit the per-block limit)
+    const Cls cls_def[2] = {{4, 1024, lim.smem_optin - 1024},
+                            {8, 512, std::min(lim.smem_optin - 1024, lim.smem_per_sm / 2 - 2048)}};
+    struct Item {
+        size_t j;
+        const DeviceSig *ds;
+        double cost;
+    };
+    std::vector<Item> cls[2];
+    for (size_t j = 0; j < n_jobs; j++) {
+        const tmcs_job &J = jobs[j];
+        const SigProgram &G = J.c->sig;
+        if (!G.ok) return TMCS_OK;
+        int ci = -1;
+        for (int c = 1; c >= 0 && ci < 0; c--) {
+            const int warps = cls_def[c].threads / 32;
+            if (sig_smem_bytes(G, J.c->n_obs, cls_def[c].K, uint32_t(32 * warps), false) <= cls_def[c].budget) ci = c;
+        }
+        if (ci < 0) return TMCS_OK;
+        cls[ci].push_back({j, nullptr, double(G.items.size() / 2 + 1) * double((J.shots + 63) / 64)});
+    }
+    for (auto &v : cls)
+        for (Item &it : v) {
+            int rc = device_sig(jobs[it.j].c, &it.ds);
+            if (rc) return rc;
+        }
+    *used = true;
+    for (auto &v : cls)
+        std::stable_sort(v.begin(), v.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
+    const bool fork = !cls[0].empty() && !cls[1].empty();
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaError_t e;
+    if (fork) {
+        if ((e = batch_side_stream(dev, &side, &ev_fork, &ev_join)) != cudaSuccess) return cuda_fail(e, "batch stream");
+        if ((e = cudaEventRecord(ev_fork, st)) != cudaSuccess) return cuda_fail(e, "batch fork");
+        if ((e = cudaStreamWaitEvent(side, ev_fork, 0)) != cudaSuccess) return cuda_fail(e, "batch fork");
+    }
+    for (int ci = 0; ci < 2; ci++) {
+        const Cls &C = cls_def[ci];
+        cudaStream_t cs = (fork && ci == 1) ? side : st;
+        unsigned long long *ctr = counter + (ci == 1 ? 16 : 0);
+        const std::vector<Item> &ord = cls[ci];
+        for (size_t base = 0; base < ord.size(); base += kMaxSigBatch) {
+            const size_t nb = std::min<size_t>(kMaxSigBatch, ord.size() - base);
+            SigBatchArgs B;
+            std::memset(&B, 0, sizeof(B));
+            uint64_t items = 0;
+            for (size_t i = 0; i < nb; i++) {
+                const tmcs_job &J = jobs[ord[base + i].j];
+                const SigProgram &G = J.c->sig;
+                const DeviceSig *ds = ord[base + i].ds;
+                const uint64_t n_cols = (J.shots + 63) / 64;
+                const uint32_t qmin = uint32_t(C.threads);
+                const bool tabs = sig_smem_bytes(G, J.c->n_obs, C.K, 2048, true) <= C.budget;
+                SigArgs &a = B.jobs[i];
+                a.noise = ds->noise;
+                a.tables = ds->tables;
+                a.item_rec = reinterpret_cast<const uint4 *>(ds->items);
+                a.steps = reinterpret_cast<const uint4 *>(ds->steps);
+                a.unit_ent = ds->unit_ent;
+                a.n_steps = uint32_t(G.steps.size());
+                a.window_mask = G.window - 1u;
+                a.n_obs = uint32_t(J.c->n_obs);
+                a.smem_tables = tabs ? uint32_t(G.tables.size() / kTableWords) : 0u;
+                a.queue_cap = std::max(qmin, sig_queue_cap(G, J.c->n_obs, C.K, C.budget, tabs));
+                a.slot_words = G.slot_words;
+                a.stage_items = sig_stage_items(G);
+                a.key0 = uint32_t(J.seed);
+                a.key1 = uint32_t(J.seed >> 32);
+                a.first_chunk = 0;
+                a.n_cols = n_cols;
+                a.last_mask = (J.shots % 64) ? ((uint64_t(1) << (J.shots % 64)) - 1) : ~uint64_t(0);
+                a.n_tiles = (n_cols + uint64_t(C.K) - 1) / uint64_t(C.K);
+                a.det = J.det;
+                a.obs = J.obs;
+                B.item_begin[i] = items;
+                items += a.n_tiles;
+            }
+            B.item_begin[nb] = items;
+            B.n_jobs = uint32_t(nb);
+            B.counter = ctr;
+            if ((e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), cs)) != cudaSuccess)
+                return cuda_fail(e, "batch queue reset");
+            e = ci == 0 ? launch_sig_batch<4>(B, C.threads, C.budget, lim.sms, cs)
+                        : launch_sig_batch<8>(B, C.threads, C.budget, lim.sms, cs);
+            if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+        }
+    }
+    if (fork) {
+        if ((e = cudaEventRecord(ev_join, side)) != cudaSuccess) return cuda_fail(e, "batch join");
+        if ((e = cudaStreamWaitEvent(st, ev_join, 0)) != cudaSuccess) return cuda_fail(e, "batch join");
+    }
+    return TMCS_OK;
+}
+
 static int batch_sample(const tmcs_job *jobs, size_t n_jobs, void *stream) {
     if (n_jobs && !jobs) return fail(TMCS_E_INVALID, "jobs is NULL");
     if (n_jobs == 0) return TMCS_OK;
@@ -1967,6 +2166,11 @@ static int batch_sample(const tmcs_job *jobs, size_t n_jobs, void *stream) {
     }
     std::stable_sort(order.begin(), order.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    {
+        bool used = false;
+        if ((rc = sig_batch_sample(jobs, n_jobs, st, lim, dev, counter, &used))) return rc;
+        if (used) return TMCS_OK;
+    }
     // Size classes: jobs whose single 64-shot chunk needs more than 24 KB of
     // shared memory share one launch; smaller circuits get their own launch
     // with a smaller budget (more CTAs per SM, larger tiles). The classes run

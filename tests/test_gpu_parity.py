@@ -124,7 +124,20 @@ def test_random_circuits(trial):
     assert_parity(circ, 64 * 9 + int(rng.integers(1, 64)), seed=int(rng.integers(1, 2 ** 62)))
 
 
-def test_batch_equals_solo():
+def _batch(jobs, kernel, monkeypatch):
+    """Batched launch; kernel "frame" forces the frame-kernel batch path."""
+    if kernel == "frame":
+        with monkeypatch.context() as m:
+            m.setenv("TMCS_KERNEL", "3")
+            tmcs.tmcs_batch_sample(jobs)
+    else:
+        tmcs.tmcs_batch_sample(jobs)
+
+
+@pytest.mark.parametrize("kernel", ["signature", "frame"])
+def test_batch_equals_solo(kernel, monkeypatch):
+    """Batched launch (event-signature or frame-kernel path) equals each job's
+    solo call (default path)."""
     circs = [C.nonlocal_cnot_circuit(C.code_by_name("sc3"), 2, 2, C.NoiseModel(0.01, 0.1)),
              C.teleport_circuit(C.code_by_name("bb18"), 1, 1, C.NoiseModel(0.003, 0.03)),
              C.memory_circuit(C.code_by_name("sc5"), 3, C.NoiseModel(0.02, 0.02))]
@@ -132,7 +145,7 @@ def test_batch_equals_solo():
     shots = [64 * 7 + 3, 1000, 64 * 33]
     outs = [s.alloc(n) for s, n in zip(samplers, shots)]
     jobs = [(s.handle, n, 40 + i, d, o) for i, (s, n, (d, o)) in enumerate(zip(samplers, shots, outs))]
-    tmcs.tmcs_batch_sample(jobs)
+    _batch(jobs, kernel, monkeypatch)
     torch.cuda.synchronize()
     for i, (circ, n) in enumerate(zip(circs, shots)):
         d, o = outs[i]
@@ -259,19 +272,43 @@ def _batch_case(n_jobs, seed):
     return circs, shots
 
 
-def test_batch_many_uneven_jobs_two_launches():
+@pytest.mark.parametrize("kernel", ["signature", "frame"])
+def test_batch_many_uneven_jobs_two_launches(kernel, monkeypatch):
     """More jobs than one launch holds (96): every job still equals its solo run."""
     circs, shots = _batch_case(110, 5)
     samplers = [tmcs.Sampler(c) for c in circs]
     outs = [s.alloc(n) for s, n in zip(samplers, shots)]
     jobs = [(s.handle, n, 1000 + i, d, o) for i, (s, n, (d, o)) in enumerate(zip(samplers, shots, outs))]
-    tmcs.tmcs_batch_sample(jobs)
+    _batch(jobs, kernel, monkeypatch)
     torch.cuda.synchronize()
     for i in range(0, len(circs), 7):
         sd, so = gpu_sample(circs[i], shots[i], 1000 + i)
         d, o = outs[i]
         assert np.array_equal(d.cpu().numpy().view(np.uint64), sd)
         assert np.array_equal(o[: circs[i].n_obs].cpu().numpy().view(np.uint64), so)
+    for s in samplers:
+        s.close()
+
+
+def test_batch_mixed_sizes_against_oracle():
+    """Both size classes of the batched signature launch (d=3..11 and BB18
+    in the 8-chunk class, d=29 in the 4-chunk class) in one call: jobs
+    checked against the oracle directly."""
+    circs = [C.nonlocal_cnot_circuit(C.code_by_name("sc3"), 2, 2, C.NoiseModel(0.01, 0.05)),
+             C.WORKLOADS["nl_sc29"].circuit(),
+             C.teleport_circuit(C.code_by_name("bb18"), 1, 1, C.NoiseModel(0.004, 0.03)),
+             C.nonlocal_cnot_circuit(C.code_by_name("sc11"), 3, 3, C.NoiseModel(0.002, 0.02))]
+    shots = [64 * 40 + 9, 64 * 3 + 5, 64 * 21, 64 * 11 + 63]
+    samplers = [tmcs.Sampler(c) for c in circs]
+    outs = [s.alloc(n) for s, n in zip(samplers, shots)]
+    jobs = [(s.handle, n, 300 + i, d, o) for i, (s, n, (d, o)) in enumerate(zip(samplers, shots, outs))]
+    tmcs.tmcs_batch_sample(jobs)
+    torch.cuda.synchronize()
+    for i, (circ, n) in enumerate(zip(circs, shots)):
+        od, oo = oracle.sample(circ, n, 300 + i, threads=8)
+        d, o = outs[i]
+        assert np.array_equal(d.cpu().numpy().view(np.uint64), od), i
+        assert np.array_equal(o[: circ.n_obs].cpu().numpy().view(np.uint64), oo), i
     for s in samplers:
         s.close()
 
