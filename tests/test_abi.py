@@ -215,3 +215,41 @@ def test_signature_window_forces_steps(tmcs, window, monkeypatch):
         assert st["sig_items"] == st["n_noise_segments"]
     finally:
         tmcs.tmcs_circuit_free(h)
+
+
+def _long_span_circuit(n_mid):
+    """An X error on qubit 0 flips detector 0 (first measurement) and the last
+    detector (second measurement, after n_mid other detectors)."""
+    c = C.Circuit()
+    c.append("R", [0])
+    c.append("X_ERROR", [0], p=0.1)
+    r0 = c.append("M", [0])
+    c.append("DETECTOR", [int(r0[0])])
+    c.append("R", list(range(1, n_mid + 1)))
+    c.append("X_ERROR", list(range(1, n_mid + 1)), p=0.01)
+    rs = c.append("M", list(range(1, n_mid + 1)))
+    for r in rs:
+        c.append("DETECTOR", [int(r)])
+    r1 = c.append("M", [0])
+    c.append("DETECTOR", [int(r1[0])])
+    c.append("OBSERVABLE", [int(r1[0])], arg=0)
+    return c
+
+
+def test_signature_program_refuses_spans_beyond_the_ring(tmcs, monkeypatch):
+    """A fault whose detectors lie further apart than the ring allows makes
+    the event-signature program unusable (sampling then uses the frame
+    kernels); a larger ring accepts the same circuit."""
+    circ = _long_span_circuit(1500)
+    monkeypatch.setenv("TMCS_SIG_WINDOW", "1024")
+    h = tmcs.tmcs_circuit_build(circ)
+    try:
+        assert tmcs.tmcs_circuit_stats(h)["sig_ok"] == 0
+    finally:
+        tmcs.tmcs_circuit_free(h)
+    monkeypatch.setenv("TMCS_SIG_WINDOW", "2048")
+    h = tmcs.tmcs_circuit_build(circ)
+    try:
+        assert tmcs.tmcs_circuit_stats(h)["sig_ok"] == 1
+    finally:
+        tmcs.tmcs_circuit_free(h)

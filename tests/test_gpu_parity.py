@@ -230,6 +230,22 @@ def test_signature_kernel_queue_overflow(monkeypatch, queue):
     assert_parity(circ, 64 * 23 + 5, seed=31)
 
 
+@pytest.mark.parametrize("window", [1024, 2048])
+def test_long_detector_span(monkeypatch, window):
+    """A fault that flips the first and the last of 1502 detectors: with a
+    1024-detector ring the signature program is refused and sampling runs on
+    the frame kernels, with a 2048 ring on the signature kernel; both equal
+    the oracle."""
+    from test_abi import _long_span_circuit
+    monkeypatch.setenv("TMCS_SIG_WINDOW", str(window))
+    circ = _long_span_circuit(1500)
+    h = tmcs.tmcs_circuit_build(circ)
+    assert tmcs.tmcs_circuit_stats(h)["sig_ok"] == (1 if window == 2048 else 0)
+    tmcs.tmcs_circuit_free(h)
+    gd, _ = assert_parity(circ, 64 * 9 + 3, seed=8)
+    assert gd.any()
+
+
 def test_signature_kernel_observables_only():
     """No detectors at all: the kernel still writes every observable word."""
     circ = C.Circuit()
