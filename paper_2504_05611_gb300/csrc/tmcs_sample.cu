@@ -1564,7 +1564,7 @@ static LaunchShape make_shape_w(const Program &P, uint64_t n_cols, int KW, int W
 // Event-signature kernel: K chunks per CTA, persistent grid of the CTAs that
 // fit on the device at once (shared memory and thread limits).
 static bool sig_fits(const tmcs_circuit *c, const DeviceLimits &lim, int K) {
-    return c->sig.ok && sig_smem_bytes(c->sig, c->n_obs, K, kSigQueueMin, false) <= lim.smem_optin;
+    return c->sig.ok && sig_smem_bytes(c->sig, c->n_obs, K, kSigQueueMin, false) + 1024 <= lim.smem_optin;
 }
 
 // The queue gets the shared memory left once the CTAs that the register file
@@ -1577,7 +1577,9 @@ static LaunchShape make_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const 
     s.threads = threads;
     s.sms = lim.sms;
     const size_t ctas = size_t(std::max(1, 1024 / threads));
-    const size_t budget = std::min(lim.smem_optin, lim.smem_per_sm / ctas - 1024);
+    // leave 1 KB for the kernel's static shared variables (dynamic + static
+    // must fit the per-block limit)
+    const size_t budget = std::min(lim.smem_optin - 1024, lim.smem_per_sm / ctas - 1024);
     // gap tables go to shared memory if they fit next to the ring and a
     // queue of 2048 events
     s.smem_tables = sig_smem_bytes(c->sig, c->n_obs, K, 2048, true) <= budget;
@@ -1591,6 +1593,10 @@ static LaunchShape make_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const 
     s.tiles = std::min<uint64_t>(n_tiles, uint64_t(lim.sms) * ctas);
     return s;
 }
+
+// Dynamic shared memory of a signature shape plus 1 KB of static shared
+// variables within the per-block limit.
+static bool sig_shape_fits(const LaunchShape &s, const DeviceLimits &lim) { return s.smem + 1024 <= lim.smem_optin; }
 
 static LaunchShape choose_shape_cta(const Program &P, uint64_t n_cols, const DeviceLimits &lim);
 
@@ -1741,7 +1747,10 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
     if (ds)
         for (int K = 1; K <= 8; K *= 2) {
             if (!sig_fits(c, lim, K)) break;
-            for (int threads : {256, 512, 1024}) cands.push_back(make_shape_sig(c, n_cols, lim, K, threads));
+            for (int threads : {256, 512, 1024}) {
+                const LaunchShape cs = make_shape_sig(c, n_cols, lim, K, threads);
+                if (sig_shape_fits(cs, lim)) cands.push_back(cs);
+            }
         }
     for (int K = 1; K <= 16; K *= 2) {
         if (!shape_fits(P, lim, K)) break;
@@ -1818,7 +1827,13 @@ static LaunchShape choose_shape_sig(const tmcs_circuit *c, uint64_t n_cols, cons
     int threads = K >= 4 ? 1024 : 512;
     const int tforce = env_int("TMCS_THREADS", 0);
     if (tforce >= 32 && tforce <= 1024 && tforce % 32 == 0) threads = tforce;
-    return make_shape_sig(c, n_cols, lim, K, threads);
+    LaunchShape s = make_shape_sig(c, n_cols, lim, K, threads);
+    // the queue floor (one ballot per warp) may not fit next to a large ring
+    while (!sig_shape_fits(s, lim) && (s.K > 1 || s.threads > 128)) {
+        if (s.threads > 128) s = make_shape_sig(c, n_cols, lim, s.K, s.threads / 2);
+        else s = make_shape_sig(c, n_cols, lim, s.K / 2, threads);
+    }
+    return s;
 }
 
 static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
@@ -1853,6 +1868,12 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
         return fail(TMCS_E_INVALID, "TMCS_KERNEL=5: no event-signature program for this circuit (" +
                                         (c->sig.ok ? std::string("ring does not fit") : c->sig.why) + ")");
     LaunchShape s = ds ? choose_shape_sig(c, n_cols, lim) : choose_shape(P, n_cols, lim);
+    if (ds && !sig_shape_fits(s, lim)) {  // no signature shape fits: frame kernels
+        if (kmode == 5 && !fault_mode)
+            return fail(TMCS_E_INVALID, "TMCS_KERNEL=5: the signature kernel's shared memory does not fit");
+        ds = nullptr;
+        s = choose_shape(P, n_cols, lim);
+    }
     const bool forced = env_int("TMCS_TILE_K", 0) > 0 || env_int("TMCS_THREADS", 0) > 0 ||
                         kmode > 0 || env_int("TMCS_WARPS", 0) > 0 || env_int("TMCS_GROUP", 0) > 0;
     if (!forced && !fault_mode) {
