@@ -61,8 +61,16 @@ __device__ __forceinline__ int gap_count(const uint32_t *__restrict__ T, float i
     const float lg = __log2f(__uint2float_rn(w) + 1.0f) - 32.0f;
     const float est = lg * inv_log2;
     int g = est >= float(kGapLen) ? int(kGapLen) : (est > 0.0f ? int(est) : 0);
-    while (g < int(kGapLen) && w < __ldg(T + g)) g++;
-    while (g > 0 && w >= __ldg(T + g - 1)) g--;
+    // both neighbours of the estimate at once (T[kGapLen] is in bounds and
+    // used only below kGapLen); the loops run only when the estimate is off
+    const uint32_t at = __ldg(T + g), below = __ldg(T + (g > 0 ? g - 1 : 0));
+    if (g < int(kGapLen) && w < at) {
+        g++;
+        while (g < int(kGapLen) && w < __ldg(T + g)) g++;
+    } else if (g > 0 && w >= below) {
+        g--;
+        while (g > 0 && w >= __ldg(T + g - 1)) g--;
+    }
     return g;
 }
 
@@ -73,8 +81,17 @@ __device__ __forceinline__ int gap_count_t(const uint32_t *__restrict__ T, float
     const float lg = __log2f(__uint2float_rn(w) + 1.0f) - 32.0f;
     const float est = lg * inv_log2;
     int g = est >= float(kGapLen) ? int(kGapLen) : (est > 0.0f ? int(est) : 0);
-    while (g < int(kGapLen) && w < T[g]) g++;
-    while (g > 0 && w >= T[g - 1]) g--;
+    // both neighbours of the estimate at once (a table row has more than
+    // kGapLen + 1 words, so T[kGapLen] is in bounds; it is used only below
+    // kGapLen); the correction loops run only when the estimate is off
+    const uint32_t at = T[g], below = T[g > 0 ? g - 1 : 0];
+    if (g < int(kGapLen) && w < at) {
+        g++;
+        while (g < int(kGapLen) && w < T[g]) g++;
+    } else if (g > 0 && w >= below) {
+        g--;
+        while (g > 0 && w >= T[g - 1]) g--;
+    }
     return g;
 }
 
