@@ -166,6 +166,9 @@ def main():
     if args.workload == "serve":
         serve_bench(args)
         return
+    if args.workload == "peaks":
+        peaks_bench(args)
+        return
     workload = circuits.WORKLOADS[args.workload]
     if args.shots:
         workload = circuits.Workload(workload.name, workload.code, workload.op, workload.rounds_before,
@@ -548,6 +551,24 @@ def serve_bench(args):
     print(json.dumps(line), flush=True)
     for h in cache.values():
         h.close()
+
+
+def peaks_bench(args):
+    """Measured non-HBM ceilings of this GPU (shared-memory loads, shared
+    atomics, LOP3), the denominators of the kernels' shared-memory and
+    integer-pipe fractions; one JSON line."""
+    import torch
+    from paper_2504_05611_gb300 import build as lib_build
+    lib_build.build()
+    from paper_2504_05611_gb300 import tmcs
+    torch.cuda.set_device(0)
+    runs = [tmcs.tmcs_measure_peaks() for _ in range(3)]
+    best = {k: max(r[k] for r in runs) for k in runs[0]}
+    print(json.dumps({"metric": "device peaks (microbenchmarks)", "smem_load_TBps": best["smem_load_bytes_per_s"] / 1e12,
+                      "smem_wavefronts_per_s": best["smem_load_wavefronts_per_s"],
+                      "smem_atomic_lanes_per_s": best["smem_atomic_lanes_per_s"],
+                      "lop3_lanes_per_s": best["lop3_lanes_per_s"], "lop3_warp_inst_per_s": best["lop3_warp_inst_per_s"],
+                      "sms": best["sms"], "sm_clock_mhz_attribute": best["sm_clock_mhz"], "runs": 3}), flush=True)
 
 
 def _kernel_sha():

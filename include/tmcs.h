@@ -284,6 +284,26 @@ int tmcs_check_device(void);
 int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *threads);
 
 /*
+ * Measured non-HBM ceilings of the current device, for roofline reports (the
+ * samplers do GF(2) bit work, so besides HBM their co-bounds are the shared
+ * memory pipe and the integer pipe). Three compute-only microbenchmarks on
+ * every SM: conflict-free 32-bit shared loads (one 128-byte wavefront per
+ * warp-wide load), 32-bit shared atomic XORs, and chains of lop3.b32.
+ * Synchronous; allocates and frees a small result buffer; about 0.1 s.
+ * Errors: TMCS_E_INVALID (NULL), TMCS_E_OOM, TMCS_E_CUDA.
+ */
+typedef struct {
+    double smem_load_bytes_per_s;      /* conflict-free shared loads, whole device */
+    double smem_load_wavefronts_per_s;
+    double smem_atomic_lanes_per_s;    /* 32-bit shared atomics, lanes per second */
+    double lop3_lanes_per_s;           /* lop3.b32 per lane per second */
+    double lop3_warp_inst_per_s;
+    double sm_clock_mhz;               /* device attribute (not the live clock) */
+    int sms;
+} tmcs_peaks;
+int tmcs_measure_peaks(tmcs_peaks *out);
+
+/*
  * Sampling server (continuous batching). A host scheduler thread admits
  * submitted requests in arrival order as soon as their output words fit in a
  * device arena (admission by HBM footprint), cuts every admitted request into

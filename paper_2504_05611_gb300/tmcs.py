@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
         L.tmcs_sample_measurements.argtypes = [P, U64, U64, U64, P, P]
         L.tmcs_fault_outputs.argtypes = [P, U64, P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
         L.tmcs_launch_shape.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
+        L.tmcs_measure_peaks.argtypes = [P]
         L.tmcs_server_open.argtypes = [P, ctypes.POINTER(P)]
         L.tmcs_server_submit.argtypes = [P, P, U64, U64, ctypes.POINTER(ctypes.c_uint64)]
         L.tmcs_server_poll.argtypes = [P, U64, ctypes.POINTER(ctypes.c_int)]
@@ -113,7 +114,7 @@ def lib() -> ctypes.CDLL:
                   "tmcs_debug_gap_table", "tmcs_check_device", "tmcs_sample_noalloc", "tmcs_server_open",
                   "tmcs_server_submit", "tmcs_server_poll", "tmcs_server_fetch", "tmcs_server_release",
                   "tmcs_server_get_stats", "tmcs_server_close", "tmcs_fault_count", "tmcs_fault_signatures",
-                  "tmcs_sample_measurements", "tmcs_fault_outputs", "tmcs_launch_shape"):
+                  "tmcs_sample_measurements", "tmcs_fault_outputs", "tmcs_launch_shape", "tmcs_measure_peaks"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -335,6 +336,21 @@ def tmcs_launch_shape(handle: int) -> Dict[str, object]:
     name = KERNEL_NAMES.get(m.value)
     return {"mode": m.value, "chunks": k.value, "threads": t.value,
             "kernel": f"{name}<{k.value}> ({t.value} threads)" if name else None}
+
+
+class _Peaks(ctypes.Structure):
+    _fields_ = [("smem_load_bytes_per_s", ctypes.c_double), ("smem_load_wavefronts_per_s", ctypes.c_double),
+                ("smem_atomic_lanes_per_s", ctypes.c_double), ("lop3_lanes_per_s", ctypes.c_double),
+                ("lop3_warp_inst_per_s", ctypes.c_double), ("sm_clock_mhz", ctypes.c_double),
+                ("sms", ctypes.c_int)]
+
+
+def tmcs_measure_peaks() -> Dict[str, float]:
+    """Measured shared-memory load, shared-atomic and LOP3 rates of the
+    current device (microbenchmarks; see include/tmcs.h)."""
+    p = _Peaks()
+    _check(lib().tmcs_measure_peaks(ctypes.byref(p)))
+    return {f: getattr(p, f) for f, _ in _Peaks._fields_}
 
 
 def tmcs_batch_sample(jobs: Sequence[Tuple[int, int, int, object, object]], stream=None) -> None:

@@ -95,3 +95,15 @@ def test_admission_waits_for_arena_space():
     finally:
         srv.close()
         s.close()
+
+
+def test_measured_peaks_are_plausible():
+    """The shared-memory and integer-pipe microbenchmarks give rates in the
+    range a Blackwell part can reach (per SM: at most one 128-byte shared
+    wavefront and 128 LOP3 lane-operations per clock at <= 3 GHz)."""
+    p = tmcs.tmcs_measure_peaks()
+    sms = p["sms"]
+    assert sms > 0
+    assert 0.1e12 * sms / 152 < p["smem_load_bytes_per_s"] <= sms * 128 * 3e9
+    assert 1e9 < p["smem_atomic_lanes_per_s"] <= sms * 32 * 3e9
+    assert 1e12 < p["lop3_lanes_per_s"] <= sms * 128 * 3e9
