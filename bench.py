@@ -324,10 +324,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         rate, n_shots, secs = oracle_rate(circ, workload.seed, args.cpu_budget, threads)
+        rate1, n1, secs1 = oracle_rate(circ, workload.seed, args.cpu_budget / 4, 1)
         cpu = {"value": rate * info["n_det"], "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{n_shots} shots ({n_shots // 64} chunks) of {workload.name} in {secs:.1f} s, "
-                         f"one-shot-at-a-time oracle on {threads} threads",
-               "shots_per_s": rate}
+                         f"one-shot-at-a-time oracle on {threads} threads; single thread: {n1} shots "
+                         f"in {secs1:.1f} s",
+               "shots_per_s": rate, "shots_per_s_1_thread": rate1}
 
     if rank == 0:
         line = {
