@@ -1769,17 +1769,24 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
                 if (sig_shape_fits(cs, lim)) cands.push_back(cs);
             }
         }
-    for (int K = 1; K <= 16; K *= 2) {
-        if (!shape_fits(P, lim, K)) break;
-        for (int threads : {128, 256, 512}) cands.push_back(make_shape(P, n_cols, K, threads));
-    }
-    for (int KW = 1; KW <= 2; KW++)
-        for (int G : {1, 2, 4}) {
-            const int Wmax = max_groups_w(P, lim, KW, G);
-            if (Wmax >= 1) cands.push_back(make_shape_w(P, n_cols, KW, Wmax, G));
-            if ((Wmax + 1) / 2 >= 1 && (Wmax + 1) / 2 < Wmax)
-                cands.push_back(make_shape_w(P, n_cols, KW, (Wmax + 1) / 2, G));
+    // With a signature program the frame kernels are compared through their
+    // heuristic shape only (they lost to kernel 4 on every measured
+    // workload); without one, every feasible frame shape is timed.
+    if (ds) {
+        cands.push_back(choose_shape_cta(P, n_cols, lim));
+    } else {
+        for (int K = 1; K <= 16; K *= 2) {
+            if (!shape_fits(P, lim, K)) break;
+            for (int threads : {128, 256, 512}) cands.push_back(make_shape(P, n_cols, K, threads));
         }
+        for (int KW = 1; KW <= 2; KW++)
+            for (int G : {1, 2, 4}) {
+                const int Wmax = max_groups_w(P, lim, KW, G);
+                if (Wmax >= 1) cands.push_back(make_shape_w(P, n_cols, KW, Wmax, G));
+                if ((Wmax + 1) / 2 >= 1 && (Wmax + 1) / 2 < Wmax)
+                    cands.push_back(make_shape_w(P, n_cols, KW, (Wmax + 1) / 2, G));
+            }
+    }
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
