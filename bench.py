@@ -199,7 +199,8 @@ def main():
 
     shots = workload.shots
     cols = (shots + 63) // 64
-    first_chunk = rank * cols          # weak scaling: disjoint global chunk ranges
+    from paper_2504_05611_gb300.shard import max_over_ranks, rank_chunk_range
+    first_chunk, _ = rank_chunk_range(rank, world, shots)  # weak scaling: disjoint global chunk ranges
     sampler = tmcs.Sampler(circ)
     info = sampler.info
     stats = sampler.stats()
@@ -239,12 +240,7 @@ def main():
     total_ms = t0.elapsed_time(t1)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     ms_local = total_ms / args.steps
-    if world > 1:
-        t = torch.tensor([ms_local], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    else:
-        ms_step = ms_local
+    ms_step = max_over_ranks(ms_local, dev)
     total_shots = shots * world
     shots_s = total_shots / (ms_step / 1e3)
     value = shots_s * info["n_det"]
@@ -311,11 +307,7 @@ def main():
             d2h_bytes = e2e_step()
         torch.cuda.synchronize()
         barrier()
-        e2e_s = (time.perf_counter() - w0) / args.e2e_steps
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks((time.perf_counter() - w0) / args.e2e_steps, dev)
         e2e = {"value": total_shots * info["n_det"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": d2h_bytes, "shots_per_s": total_shots / e2e_s,
                "launches_per_step": nslices}
