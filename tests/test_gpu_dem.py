@@ -86,3 +86,38 @@ def test_table_iii_columns_on_gpu(key):
         s = tmcs.Sampler(fn(code, 4, 3))
         assert len(tmcs.dem_columns(s)) == T3[key][idx]
         s.close()
+
+
+@pytest.mark.parametrize("case", ["nl_sc5", "tp_bb18"])
+def test_gpu_marginals_match_exact_dem(case):
+    """Whole-circuit statistics of 4e6 GPU shots: every detector's and
+    observable's flip frequency is within 6 standard errors of the exact
+    probability from the oracle's single-fault DEM, (1 - prod(1 - 2 P_c)) / 2,
+    and so is the parity of detector pairs that share a fault."""
+    from oracle import dem
+    if case == "nl_sc5":
+        circ = C.nonlocal_cnot_circuit(C.code_by_name("sc5"), 3, 3, C.NoiseModel(0.002, 0.02))
+    else:
+        circ = C.teleport_circuit(C.code_by_name("bb18"), 2, 2, C.NoiseModel(0.002, 0.02))
+    shots = 4_000_000
+    s = tmcs.Sampler(circ)
+    det, obs = s.sample(shots, seed=2024)
+    torch.cuda.synchronize()
+    d = det.cpu().numpy().view(np.uint64)
+    o = obs.cpu().numpy().view(np.uint64)
+    s.close()
+
+    def freq(words):
+        bits = np.unpackbits(words.view(np.uint8).reshape(words.shape[0], -1), axis=1, bitorder="little")
+        return bits[:, :shots].sum(axis=1) / shots
+
+    pd, po = dem.flip_probabilities(circ)
+    for f, p in ((freq(d), pd), (freq(o), po)):
+        se = np.sqrt(np.maximum(p * (1 - p), 1e-12) / shots)
+        assert np.all(np.abs(f - p) <= 6 * se + 1e-9), np.max(np.abs(f - p) / se)
+    # detector pairs: first detector with each of the next few
+    bits = np.unpackbits(d.view(np.uint8).reshape(d.shape[0], -1), axis=1, bitorder="little")[:, :shots]
+    for a, b in ((0, 1), (0, 5), (3, 9), (10, 11)):
+        p = dem.pair_flip_probability(circ, a, b)
+        f = np.mean(bits[a] ^ bits[b])
+        assert abs(f - p) <= 6 * np.sqrt(max(p * (1 - p), 1e-12) / shots) + 1e-9, (a, b, f, p)
