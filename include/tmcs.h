@@ -175,9 +175,11 @@ int tmcs_sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shot
  * device -- it calls no cudaMalloc, cudaFree or other allocating routine.
  * Its scratch is one file-scope device array of 8 MiB (every GPU that loads
  * libtmcs.so holds it until the process exits): each call clears the status
- * word in it, copies the circuit's compiled program into it (stream-ordered
- * on `stream`) and launches the same kernel as tmcs_sample_range, so outputs
- * are bit-identical to tmcs_sample_range with the same arguments.
+ * word in it, copies the circuit's compiled frame program into it
+ * (stream-ordered on `stream`) and launches the CTA-wide frame kernel on it.
+ * Every sampling kernel draws the same noise streams, so outputs are
+ * bit-identical to tmcs_sample_range with the same arguments, whichever
+ * kernel that call uses.
  *   - Circuits whose compiled program exceeds the array (device_bytes of
  *     tmcs_circuit_info plus 256) are rejected with TMCS_E_INVALID.
  *   - The first call on each device looks up the array's device address with
