@@ -148,8 +148,18 @@ int tmcs_reference_sample(const tmcs_circuit *c, uint8_t *meas_bits);
  * Sample `shots` shots with global 64-shot chunks 0 .. ceil(shots/64)-1.
  * detector_bits:   device, n_det * ceil(shots/64) uint64, 8-byte aligned
  * observable_bits: device, n_obs * ceil(shots/64) uint64 (may be NULL if n_obs == 0)
- * Asynchronous on `stream`; the first call on a device uploads the compiled
- * program to it (synchronously, before the launch).
+ * Asynchronous on `stream`, with two one-time exceptions per circuit and
+ * device: the first call uploads the compiled programs (synchronously, before
+ * the launch), and the first call with at least 16 chunks per SM times the
+ * candidate launch shapes on the leading columns of its own output
+ * (synchronously; skipped while `stream` is being captured) and keeps the
+ * fastest. Make such a call before capturing a graph or timing steps.
+ * Kernel choice: the event-signature sampler when the circuit has a usable
+ * event-signature program (tmcs_circuit_stats sig_ok), else the frame
+ * kernels; both give the same bits. Tuning knobs in the environment change
+ * only the schedule: TMCS_KERNEL (3 CTA frame kernel, 4 warp-group frame
+ * kernel, 5 event-signature kernel), TMCS_TILE_K, TMCS_THREADS,
+ * TMCS_SIG_WINDOW (read by tmcs_circuit_build), TMCS_AUTOTUNE=0.
  * Errors: TMCS_E_INVALID (NULL circuit/buffer, shots == 0), TMCS_E_CUDA,
  * TMCS_E_OOM (program upload).
  */
