@@ -126,13 +126,15 @@ typedef struct {
     uint64_t pruned_updates;  /* slot updates removed by pruning */
     /* event-signature program (see tmcs_fault_outputs) */
     uint64_t sig_ok;          /* 1 if the signature sampler can run this circuit */
-    uint64_t sig_window;      /* detector ring size (words per chunk) */
-    uint64_t sig_steps;       /* flush steps */
+    uint64_t sig_window;      /* detector ring size of the main schedule (words per chunk) */
+    uint64_t sig_steps;       /* flush steps of the main schedule */
     uint64_t sig_items;       /* noise segments walked per chunk */
     uint64_t sig_generators;  /* X/Z generators of all noise units */
     uint64_t sig_entries;     /* (generator, output) pairs */
     uint64_t sig_build_us;    /* host time to build it, microseconds */
     uint64_t sig_max_step_items; /* segments in the largest step */
+    uint64_t sig_schedules;   /* ring-window schedules carried (window halves each time) */
+    uint64_t sig_min_window;  /* ring size of the smallest schedule */
 } tmcs_stats;
 int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out);
 
@@ -290,10 +292,11 @@ int tmcs_check_device(void);
  * device (for reports): *mode = 0 if it has not run yet (first large call),
  * 3 = CTA-wide frame kernel, 4 = warp-group frame kernel, 5 = event-signature
  * kernel; *chunks = 64-shot chunks per CTA (mode 3, 5) or per warp group
- * (mode 4); *threads = CTA size. Any pointer may be NULL.
+ * (mode 4); *threads = CTA size; *ring_window = detector ring of the chosen
+ * event-signature schedule (mode 5; 0 otherwise). Any pointer may be NULL.
  * Errors: TMCS_E_INVALID (NULL circuit), TMCS_E_CUDA (no current device).
  */
-int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *threads);
+int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *threads, int *ring_window);
 
 /*
  * Measured non-HBM ceilings of the current device, for roofline reports (the

@@ -1170,15 +1170,20 @@ int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out) {
     *out = c->stats;
     const SigProgram &G = c->sig;
     out->sig_ok = G.ok ? 1 : 0;
-    out->sig_window = G.window;
-    out->sig_steps = G.steps.size();
-    out->sig_items = G.items.size() / 2;
     out->sig_generators = G.gen_off.empty() ? 0 : G.gen_off.size() - 1;
     out->sig_entries = G.gen_ent.size();
     out->sig_build_us = uint64_t(G.build_seconds * 1e6);
-    out->sig_max_step_items = 0;
-    for (const SigStep &st : G.steps)
-        out->sig_max_step_items = std::max<uint64_t>(out->sig_max_step_items, st.item_end - st.item_begin);
+    out->sig_window = out->sig_steps = out->sig_items = out->sig_max_step_items = 0;
+    out->sig_schedules = G.sched.size();
+    if (!G.sched.empty()) {
+        const SigSchedule &S = G.sched[0];
+        out->sig_window = S.window;
+        out->sig_steps = S.steps.size();
+        out->sig_items = S.items.size() / 2;
+        for (const SigStep &st : S.steps)
+            out->sig_max_step_items = std::max<uint64_t>(out->sig_max_step_items, st.item_end - st.item_begin);
+        out->sig_min_window = G.sched.back().window;
+    }
     return TMCS_OK;
 }
 

@@ -97,6 +97,7 @@ struct Program {
 };
 
 struct SigStep;
+constexpr int kSigMaxSchedules = 3;  // ring windows an event-signature program carries
 
 // One device copy of a program.
 struct DeviceProgram {
@@ -113,6 +114,7 @@ struct DeviceProgram {
     int tuned_warps = 0;
     int tuned_group = 0;
     int tuned_threads = 0;
+    int tuned_sched = 0;    // event-signature schedule the autotuner chose
 };
 
 // One device copy of an event-signature program.
@@ -122,8 +124,8 @@ struct DeviceSig {
     size_t bytes = 0;
     const NoiseDesc *noise = nullptr;
     const uint32_t *tables = nullptr;
-    const uint32_t *items = nullptr;
-    const SigStep *steps = nullptr;
+    const uint32_t *items[kSigMaxSchedules] = {};  // item records of each schedule
+    const SigStep *steps[kSigMaxSchedules] = {};
     const uint32_t *unit_ent = nullptr;
 };
 
@@ -153,19 +155,28 @@ struct SigStep {
 
 constexpr uint32_t kSigObsFlag = 0x80000000u;  // entry = observable index | flag
 
-struct SigProgram {
-    bool ok = false;
-    std::string why;                 // reason the program is unusable (ok = false)
+// One schedule of a program: its items in walk order, its steps and the
+// ring size they need. Schedules differ only in the window; the output is
+// the same for every one of them.
+struct SigSchedule {
     uint32_t window = 0;             // ring size in detectors (power of two)
-    std::vector<NoiseDesc> noise;    // every noise op with p > 0; tgt_off = first generator id
-                                     // (host); the device copy carries unit_base there
-    std::vector<uint32_t> tables;    // kTableWords per distinct p
     std::vector<uint32_t> items;     // (descriptor, segment) pairs, 2 words per item
     // Device item records, 4 words per item: op index, segment, global index
     // of the segment's first unit, kind | table << 3 | (units - 1) << 16 |
     // descriptor << 22 (descriptor < 1024, table < 8192).
     std::vector<uint32_t> item_rec;
     std::vector<SigStep> steps;
+};
+
+struct SigProgram {
+    bool ok = false;
+    std::string why;                 // reason the program is unusable (ok = false)
+    std::vector<NoiseDesc> noise;    // every noise op with p > 0; tgt_off = first generator id
+                                     // (host); the device copy carries unit_base there
+    std::vector<uint32_t> tables;    // kTableWords per distinct p
+    // Schedules by decreasing window; schedule 0 has the largest window
+    // (fewest steps) and is the one the batch sampler and the statistics use.
+    std::vector<SigSchedule> sched;
     std::vector<uint32_t> gen_off;   // CSR offsets per generator (n_gens + 1)
     std::vector<uint32_t> gen_ent;   // detector index, or kSigObsFlag | observable index
     // Device layout: a slot of slot_words (8 or 16) words per noise unit,

@@ -954,29 +954,31 @@ static size_t sig_table_bytes(const SigProgram &G) { return G.tables.size() * 4;
 
 // Step item records staged in shared memory: the largest step's, if that
 // is at most 1024 records.
-static uint32_t sig_stage_items(const SigProgram &G) {
+static uint32_t sig_stage_items(const SigProgram &G, int sched) {
     uint32_t m = 0;
-    for (const SigStep &st : G.steps) m = std::max(m, st.item_end - st.item_begin);
+    for (const SigStep &st : G.sched[sched].steps) m = std::max(m, st.item_end - st.item_begin);
     return m <= 1024 ? m : 0u;
 }
 
 // ring and observables, padded to 16 bytes
-static size_t sig_ring_bytes(const SigProgram &G, uint64_t n_obs, int K) {
-    return ((size_t(G.window) + size_t(n_obs)) * size_t(K) * 8 + 15) & ~size_t(15);
+static size_t sig_ring_bytes(const SigProgram &G, int sched, uint64_t n_obs, int K) {
+    return ((size_t(G.sched[sched].window) + size_t(n_obs)) * size_t(K) * 8 + 15) & ~size_t(15);
 }
 
 // Ring + observables + event queue: the queue takes what is left of `budget`
 // (at least kSigQueueMin events, at most kSigQueueMax).
-static uint32_t sig_queue_cap(const SigProgram &G, uint64_t n_obs, int K, size_t budget, bool smem_tables) {
-    const size_t ring = sig_ring_bytes(G, n_obs, K) + (smem_tables ? sig_table_bytes(G) : 0) +
-                        size_t(sig_stage_items(G)) * 16;
+static uint32_t sig_queue_cap(const SigProgram &G, int sched, uint64_t n_obs, int K, size_t budget,
+                              bool smem_tables) {
+    const size_t ring = sig_ring_bytes(G, sched, n_obs, K) + (smem_tables ? sig_table_bytes(G) : 0) +
+                        size_t(sig_stage_items(G, sched)) * 16;
     const size_t left = budget > ring ? (budget - ring) / 8 : 0;
     return uint32_t(std::min<size_t>(kSigQueueMax, std::max<size_t>(kSigQueueMin, left & ~size_t(255))));
 }
 
-static size_t sig_smem_bytes(const SigProgram &G, uint64_t n_obs, int K, uint32_t qcap, bool smem_tables) {
-    return sig_ring_bytes(G, n_obs, K) + (smem_tables ? sig_table_bytes(G) : 0) + size_t(sig_stage_items(G)) * 16 +
-           size_t(qcap) * 8;
+static size_t sig_smem_bytes(const SigProgram &G, int sched, uint64_t n_obs, int K, uint32_t qcap,
+                             bool smem_tables) {
+    return sig_ring_bytes(G, sched, n_obs, K) + (smem_tables ? sig_table_bytes(G) : 0) +
+           size_t(sig_stage_items(G, sched)) * 16 + size_t(qcap) * 8;
 }
 
 // ---------------------------------------------------------------------------
@@ -1429,10 +1431,15 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
     const SigProgram &G = c->sig;
     const size_t b_noise = align256(G.noise.size() * sizeof(NoiseDesc));
     const size_t b_tables = align256(G.tables.size() * 4);
-    const size_t b_items = align256(G.item_rec.size() * 4);
-    const size_t b_steps = align256(G.steps.size() * sizeof(SigStep));
+    const size_t n_sched = G.sched.size();
+    size_t b_items[kSigMaxSchedules] = {}, b_steps[kSigMaxSchedules] = {}, b_sched = 0;
+    for (size_t k = 0; k < n_sched; k++) {
+        b_items[k] = align256(G.sched[k].item_rec.size() * 4);
+        b_steps[k] = align256(G.sched[k].steps.size() * sizeof(SigStep));
+        b_sched += b_items[k] + b_steps[k];
+    }
     const size_t b_ent = align256(G.unit_ent.size() * 4);
-    const size_t total = std::max<size_t>(b_noise + b_tables + b_items + b_steps + b_ent, 256);
+    const size_t total = std::max<size_t>(b_noise + b_tables + b_sched + b_ent, 256);
     std::vector<uint8_t> host(total, 0);
     size_t o = 0;
     auto put = [&](const void *src, size_t n, size_t span) {
@@ -1445,8 +1452,12 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
     for (size_t i = 0; i < dn.size(); i++) dn[i].tgt_off = G.unit_base[i];
     const size_t o_noise = put(dn.data(), dn.size() * sizeof(NoiseDesc), b_noise);
     const size_t o_tables = put(G.tables.data(), G.tables.size() * 4, b_tables);
-    const size_t o_items = put(G.item_rec.data(), G.item_rec.size() * 4, b_items);
-    const size_t o_steps = put(G.steps.data(), G.steps.size() * sizeof(SigStep), b_steps);
+    size_t o_items[kSigMaxSchedules] = {}, o_steps[kSigMaxSchedules] = {};
+    for (size_t k = 0; k < n_sched; k++) {
+        const SigSchedule &S = G.sched[k];
+        o_items[k] = put(S.item_rec.data(), S.item_rec.size() * 4, b_items[k]);
+        o_steps[k] = put(S.steps.data(), S.steps.size() * sizeof(SigStep), b_steps[k]);
+    }
     const size_t o_ent = put(G.unit_ent.data(), G.unit_ent.size() * 4, b_ent);
     void *base = nullptr;
     e = cudaMalloc(&base, total);
@@ -1466,8 +1477,10 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
     uint8_t *b = static_cast<uint8_t *>(base);
     ds.noise = reinterpret_cast<const NoiseDesc *>(b + o_noise);
     ds.tables = reinterpret_cast<const uint32_t *>(b + o_tables);
-    ds.items = reinterpret_cast<const uint32_t *>(b + o_items);
-    ds.steps = reinterpret_cast<const SigStep *>(b + o_steps);
+    for (size_t k = 0; k < n_sched; k++) {
+        ds.items[k] = reinterpret_cast<const uint32_t *>(b + o_items[k]);
+        ds.steps[k] = reinterpret_cast<const SigStep *>(b + o_steps[k]);
+    }
     ds.unit_ent = reinterpret_cast<const uint32_t *>(b + o_ent);
     auto ins = c->dev_sig.emplace(dev, ds);
     *out = &ins.first->second;
@@ -1528,6 +1541,7 @@ struct LaunchShape {
     int sms = 0;       // mode 5: SM count (grid = SMs x resident CTAs per SM)
     uint32_t qcap = 0; // mode 5: event-queue capacity
     bool smem_tables = false;  // mode 5: gap tables staged in shared memory
+    int sched = 0;     // mode 5: schedule (ring window) of the signature program
 };
 
 static int env_int(const char *name, int dflt) {
@@ -1580,16 +1594,17 @@ static LaunchShape make_shape_w(const Program &P, uint64_t n_cols, int KW, int W
 
 // Event-signature kernel: K chunks per CTA, persistent grid of the CTAs that
 // fit on the device at once (shared memory and thread limits).
-static bool sig_fits(const tmcs_circuit *c, const DeviceLimits &lim, int K) {
-    return c->sig.ok && sig_smem_bytes(c->sig, c->n_obs, K, kSigQueueMin, false) + 1024 <= lim.smem_optin;
+static bool sig_fits(const tmcs_circuit *c, const DeviceLimits &lim, int K, int sched = 0) {
+    return c->sig.ok && sig_smem_bytes(c->sig, sched, c->n_obs, K, kSigQueueMin, false) + 1024 <= lim.smem_optin;
 }
 
 // The queue gets the shared memory left once the CTAs that the register file
 // allows at this CTA size (64 registers per thread) each hold their ring.
 static LaunchShape make_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const DeviceLimits &lim, int K,
-                                  int threads) {
+                                  int threads, int sched = 0) {
     LaunchShape s;
     s.mode = 5;
+    s.sched = sched;
     s.K = K;
     s.threads = threads;
     s.sms = lim.sms;
@@ -1599,13 +1614,13 @@ static LaunchShape make_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const 
     const size_t budget = std::min(lim.smem_optin - 1024, lim.smem_per_sm / ctas - 1024);
     // gap tables go to shared memory if they fit next to the ring and a
     // queue of 2048 events
-    s.smem_tables = sig_smem_bytes(c->sig, c->n_obs, K, 2048, true) <= budget;
-    s.qcap = sig_queue_cap(c->sig, c->n_obs, K, budget, s.smem_tables);
+    s.smem_tables = sig_smem_bytes(c->sig, sched, c->n_obs, K, 2048, true) <= budget;
+    s.qcap = sig_queue_cap(c->sig, sched, c->n_obs, K, budget, s.smem_tables);
     const int qforce = env_int("TMCS_SIG_QUEUE", 0);  // tuning/testing knob: queue capacity
     if (qforce > 0) s.qcap = uint32_t(std::min<int>(qforce, int(kSigQueueMax)));
     // every warp's slice holds at least one ballot's worth (32 events)
     s.qcap = std::max<uint32_t>(s.qcap, uint32_t(threads));
-    s.smem = sig_smem_bytes(c->sig, c->n_obs, K, s.qcap, s.smem_tables);
+    s.smem = sig_smem_bytes(c->sig, sched, c->n_obs, K, s.qcap, s.smem_tables);
     const uint64_t n_tiles = (n_cols + K - 1) / K;
     s.tiles = std::min<uint64_t>(n_tiles, uint64_t(lim.sms) * ctas);
     return s;
@@ -1687,20 +1702,21 @@ static cudaError_t launch_sig(const SigArgs &a, const LaunchShape &s, cudaStream
 static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream_t st,
                           const DeviceSig *ds = nullptr, const SigProgram *G = nullptr, uint32_t n_obs = 0) {
     if (s.mode == 5) {
-        if (!ds || !G) return cudaErrorInvalidValue;
+        if (!ds || !G || s.sched < 0 || size_t(s.sched) >= G->sched.size()) return cudaErrorInvalidValue;
+        const SigSchedule &S = G->sched[s.sched];
         SigArgs a{};
         a.noise = ds->noise;
         a.tables = ds->tables;
-        a.item_rec = reinterpret_cast<const uint4 *>(ds->items);
-        a.steps = reinterpret_cast<const uint4 *>(ds->steps);
+        a.item_rec = reinterpret_cast<const uint4 *>(ds->items[s.sched]);
+        a.steps = reinterpret_cast<const uint4 *>(ds->steps[s.sched]);
         a.unit_ent = ds->unit_ent;
-        a.n_steps = uint32_t(G->steps.size());
-        a.window_mask = G->window - 1u;
+        a.n_steps = uint32_t(S.steps.size());
+        a.window_mask = S.window - 1u;
         a.n_obs = n_obs;
         a.queue_cap = s.qcap;
         a.smem_tables = s.smem_tables ? uint32_t(G->tables.size() / kTableWords) : 0u;
         a.slot_words = G->slot_words;
-        a.stage_items = sig_stage_items(*G);
+        a.stage_items = sig_stage_items(*G, s.sched);
         a.key0 = a0.key0;
         a.key1 = a0.key1;
         a.first_chunk = a0.first_chunk;
@@ -1762,13 +1778,14 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
     const Program &P = c->prog;
     std::vector<LaunchShape> cands;
     if (ds)
-        for (int K = 1; K <= 8; K *= 2) {
-            if (!sig_fits(c, lim, K)) break;
-            for (int threads : {256, 512, 1024}) {
-                const LaunchShape cs = make_shape_sig(c, n_cols, lim, K, threads);
-                if (sig_shape_fits(cs, lim)) cands.push_back(cs);
+        for (int sched = 0; sched < int(c->sig.sched.size()); sched++)
+            for (int K = 1; K <= 8; K *= 2) {
+                if (!sig_fits(c, lim, K, sched)) break;
+                for (int threads : {256, 512, 1024}) {
+                    const LaunchShape cs = make_shape_sig(c, n_cols, lim, K, threads, sched);
+                    if (sig_shape_fits(cs, lim)) cands.push_back(cs);
+                }
             }
-        }
     // With a signature program the frame kernels are compared through their
     // heuristic shape only (they lost to kernel 4 on every measured
     // workload); without one, every feasible frame shape is timed.
@@ -1834,6 +1851,7 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
     mdp.tuned_warps = chosen.warps;
     mdp.tuned_group = chosen.group;
     mdp.tuned_threads = chosen.threads;
+    mdp.tuned_sched = chosen.sched;
     return TMCS_OK;
 }
 
@@ -1841,21 +1859,24 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
 // leaves room for two CTAs per SM and still gives every SM two tiles.
 static LaunchShape choose_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const DeviceLimits &lim) {
     const int kcap = env_int("TMCS_TILE_K", 0);
+    // tuning/testing knob: schedule index (0 = largest ring window)
+    const int sched = std::min(std::max(env_int("TMCS_SIG_SCHED", 0), 0), int(c->sig.sched.size()) - 1);
     int K = kcap > 0 ? std::min(kcap, 8) : 4;
     while (K > 1 && (K & (K - 1))) K--;
-    while (K > 1 && !sig_fits(c, lim, K)) K >>= 1;
+    while (K > 1 && !sig_fits(c, lim, K, sched)) K >>= 1;
     if (kcap <= 0) {
-        while (K > 1 && 2 * (sig_smem_bytes(c->sig, c->n_obs, K, kSigQueueMin, false) + 1024) > lim.smem_per_sm) K >>= 1;
+        while (K > 1 && 2 * (sig_smem_bytes(c->sig, sched, c->n_obs, K, kSigQueueMin, false) + 1024) > lim.smem_per_sm)
+            K >>= 1;
         while (K > 1 && (n_cols + K - 1) / K < uint64_t(2 * lim.sms)) K >>= 1;
     }
     int threads = K >= 4 ? 1024 : 512;
     const int tforce = env_int("TMCS_THREADS", 0);
     if (tforce >= 32 && tforce <= 1024 && tforce % 32 == 0) threads = tforce;
-    LaunchShape s = make_shape_sig(c, n_cols, lim, K, threads);
+    LaunchShape s = make_shape_sig(c, n_cols, lim, K, threads, sched);
     // the queue floor (one ballot per warp) may not fit next to a large ring
     while (!sig_shape_fits(s, lim) && (s.K > 1 || s.threads > 128)) {
-        if (s.threads > 128) s = make_shape_sig(c, n_cols, lim, s.K, s.threads / 2);
-        else s = make_shape_sig(c, n_cols, lim, s.K / 2, threads);
+        if (s.threads > 128) s = make_shape_sig(c, n_cols, lim, s.K, s.threads / 2, sched);
+        else s = make_shape_sig(c, n_cols, lim, s.K / 2, threads, sched);
     }
     return s;
 }
@@ -1899,13 +1920,15 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
         s = choose_shape(P, n_cols, lim);
     }
     const bool forced = env_int("TMCS_TILE_K", 0) > 0 || env_int("TMCS_THREADS", 0) > 0 ||
-                        kmode > 0 || env_int("TMCS_WARPS", 0) > 0 || env_int("TMCS_GROUP", 0) > 0;
+                        kmode > 0 || env_int("TMCS_WARPS", 0) > 0 || env_int("TMCS_GROUP", 0) > 0 ||
+                        env_int("TMCS_SIG_SCHED", 0) > 0;
     if (!forced && !fault_mode) {
         std::lock_guard<std::mutex> lock(c->mu);
         DeviceProgram &mdp = c->dev[dp->device];
         if (mdp.tuned_mode == 3) s = make_shape(P, n_cols, mdp.tuned_K, mdp.tuned_threads);
         if (mdp.tuned_mode == 4) s = make_shape_w(P, n_cols, mdp.tuned_K, mdp.tuned_warps, mdp.tuned_group);
-        if (mdp.tuned_mode == 5 && ds) s = make_shape_sig(c, n_cols, lim, mdp.tuned_K, mdp.tuned_threads);
+        if (mdp.tuned_mode == 5 && ds)
+            s = make_shape_sig(c, n_cols, lim, mdp.tuned_K, mdp.tuned_threads, mdp.tuned_sched);
     }
     if (fault_mode) s = choose_shape(P, n_cols, lim);
     KernelArgs a{};
@@ -2091,10 +2114,10 @@ static int sig_batch_sample(const tmcs_job *jobs, size_t n_jobs, cudaStream_t st
         int ci = -1;
         for (int c = 1; c >= 0 && ci < 0; c--) {
             const int warps = cls_def[c].threads / 32;
-            if (sig_smem_bytes(G, J.c->n_obs, cls_def[c].K, uint32_t(32 * warps), false) <= cls_def[c].budget) ci = c;
+            if (sig_smem_bytes(G, 0, J.c->n_obs, cls_def[c].K, uint32_t(32 * warps), false) <= cls_def[c].budget) ci = c;
         }
         if (ci < 0) return TMCS_OK;
-        cls[ci].push_back({j, nullptr, double(G.items.size() / 2 + 1) * double((J.shots + 63) / 64)});
+        cls[ci].push_back({j, nullptr, double(G.sched[0].items.size() / 2 + 1) * double((J.shots + 63) / 64)});
     }
     for (auto &v : cls)
         for (Item &it : v) {
@@ -2129,20 +2152,21 @@ static int sig_batch_sample(const tmcs_job *jobs, size_t n_jobs, cudaStream_t st
                 const DeviceSig *ds = ord[base + i].ds;
                 const uint64_t n_cols = (J.shots + 63) / 64;
                 const uint32_t qmin = uint32_t(C.threads);
-                const bool tabs = sig_smem_bytes(G, J.c->n_obs, C.K, 2048, true) <= C.budget;
+                // the batch runs every job on its main (largest-window) schedule
+                const bool tabs = sig_smem_bytes(G, 0, J.c->n_obs, C.K, 2048, true) <= C.budget;
                 SigArgs &a = B.jobs[i];
                 a.noise = ds->noise;
                 a.tables = ds->tables;
-                a.item_rec = reinterpret_cast<const uint4 *>(ds->items);
-                a.steps = reinterpret_cast<const uint4 *>(ds->steps);
+                a.item_rec = reinterpret_cast<const uint4 *>(ds->items[0]);
+                a.steps = reinterpret_cast<const uint4 *>(ds->steps[0]);
                 a.unit_ent = ds->unit_ent;
-                a.n_steps = uint32_t(G.steps.size());
-                a.window_mask = G.window - 1u;
+                a.n_steps = uint32_t(G.sched[0].steps.size());
+                a.window_mask = G.sched[0].window - 1u;
                 a.n_obs = uint32_t(J.c->n_obs);
                 a.smem_tables = tabs ? uint32_t(G.tables.size() / kTableWords) : 0u;
-                a.queue_cap = std::max(qmin, sig_queue_cap(G, J.c->n_obs, C.K, C.budget, tabs));
+                a.queue_cap = std::max(qmin, sig_queue_cap(G, 0, J.c->n_obs, C.K, C.budget, tabs));
                 a.slot_words = G.slot_words;
-                a.stage_items = sig_stage_items(G);
+                a.stage_items = sig_stage_items(G, 0);
                 a.key0 = uint32_t(J.seed);
                 a.key1 = uint32_t(J.seed >> 32);
                 a.first_chunk = 0;
@@ -2454,7 +2478,7 @@ int tmcs_check_device(void) {
     return TMCS_OK;
 }
 
-int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *threads) {
+int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *threads, int *ring_window) {
     if (!c) return fail(TMCS_E_INVALID, "circuit is NULL");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -2465,6 +2489,10 @@ int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *thread
     if (mode) *mode = dp ? dp->tuned_mode : 0;
     if (chunks) *chunks = dp ? dp->tuned_K : 0;
     if (threads) *threads = dp ? dp->tuned_threads : 0;
+    if (ring_window) {
+        const int k = dp ? dp->tuned_sched : 0;
+        *ring_window = (dp && dp->tuned_mode == 5 && size_t(k) < c->sig.sched.size()) ? int(c->sig.sched[k].window) : 0;
+    }
     return TMCS_OK;
 }
 

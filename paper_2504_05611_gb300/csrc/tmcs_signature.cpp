@@ -353,7 +353,7 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
     }
 
     // ---- items: segments whose events flip anything; detector span per item
-    std::vector<uint32_t> dmin, dmax;
+    std::vector<uint32_t> items, dmin, dmax;
     for (uint32_t di = 0; di < G.noise.size(); di++) {
         const NoiseDesc &nd = G.noise[di];
         const uint32_t ng = sig_gens(nd.kind);
@@ -370,8 +370,8 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
                 hi = std::max(hi, v);
                 any_det = true;
             }
-            G.items.push_back(di);
-            G.items.push_back(s);
+            items.push_back(di);
+            items.push_back(s);
             dmin.push_back(any_det ? lo : 0xFFFFFFFFu);
             dmax.push_back(any_det ? hi : 0u);
         }
@@ -379,75 +379,82 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
     const size_t n_items = dmin.size();
     std::vector<uint64_t> sufmin(n_items + 1, D);
     for (size_t i = n_items; i-- > 0;) sufmin[i] = std::min<uint64_t>(sufmin[i + 1], dmin[i]);
+    if (G.noise.size() > 1024 || G.tables.size() / kTableWords > 8192) {
+        G.why = "too many noise ops or distinct probabilities for the device item records";
+        return TMCS_OK;
+    }
 
-    // ---- window and steps: the smallest power of two >= 1024 that admits
-    // a schedule, raised to max_window (fewer, larger steps), capped by D
+    // ---- schedules. The smallest feasible window is the smallest power of
+    // two >= 1024 that holds every item's detector span above its flush
+    // point; the main schedule raises it to max_window (fewer, larger steps,
+    // capped by D), and up to two more schedules halve it while feasible
+    // (a smaller ring lets more chunks or CTAs share an SM; the autotuner
+    // picks).
     uint64_t need = 0;
     for (size_t i = 0; i < n_items; i++)
         if (dmin[i] != 0xFFFFFFFFu) need = std::max<uint64_t>(need, uint64_t(dmax[i]) - sufmin[i] + 1);
-    uint64_t W = 1024;
-    while (W < need) W <<= 1;
+    uint64_t Wmin = 1024;
+    while (Wmin < need) Wmin <<= 1;
     uint64_t Dp = 1024;
     while (Dp < D) Dp <<= 1;
-    W = std::max<uint64_t>(W, std::min<uint64_t>(max_window, Dp));
-    if (W > max_window) {
+    const uint64_t W0 = std::max<uint64_t>(Wmin, std::min<uint64_t>(max_window, Dp));
+    if (W0 > max_window) {
         G.why = "detector window " + std::to_string(need) + " exceeds " + std::to_string(max_window);
-        G.items.clear();
         return TMCS_OK;
     }
-    G.window = uint32_t(W);
-    {
+    auto build_schedule = [&](uint64_t W, SigSchedule &S) {
+        S = SigSchedule();
+        S.window = uint32_t(W);
+        S.items = items;
         uint64_t F = 0;
         size_t i = 0;
         while (i < n_items) {
             size_t j = i;
             while (j < n_items && (dmin[j] == 0xFFFFFFFFu || dmax[j] < F + W)) j++;
-            if (j == i) {  // cannot happen: W >= need and F <= sufmin[i]
-                G.why = "internal: schedule";
-                return TMCS_OK;
-            }
+            if (j == i) return false;  // cannot happen: W >= need and F <= sufmin[i]
             const uint64_t F2 = sufmin[j];
-            G.steps.push_back({uint32_t(i), uint32_t(j), uint32_t(F), uint32_t(F2)});
+            S.steps.push_back({uint32_t(i), uint32_t(j), uint32_t(F), uint32_t(F2)});
             F = F2;
             i = j;
         }
-        if (G.steps.empty() || F < D) G.steps.push_back({uint32_t(n_items), uint32_t(n_items), uint32_t(F), uint32_t(D)});
+        if (S.steps.empty() || F < D) S.steps.push_back({uint32_t(n_items), uint32_t(n_items), uint32_t(F), uint32_t(D)});
         // within a step, longest streams first (expected draws ~ p x units),
         // so the step's tail is short; order within a step does not change
         // the output (events XOR into the ring)
         std::vector<uint32_t> perm(n_items);
-        for (size_t i = 0; i < n_items; i++) perm[i] = uint32_t(i);
-        for (const SigStep &st : G.steps) {
-            auto cost = [&](uint32_t i) {
-                const NoiseDesc &nd = G.noise[G.items[2 * i]];
-                const uint32_t units = std::min(kSegUnits, nd.n_units - G.items[2 * i + 1] * kSegUnits);
-                return table_p[nd.table] * double(units);
-            };
+        for (size_t k = 0; k < n_items; k++) perm[k] = uint32_t(k);
+        auto cost = [&](uint32_t k) {
+            const NoiseDesc &nd = G.noise[items[2 * k]];
+            const uint32_t units = std::min(kSegUnits, nd.n_units - items[2 * k + 1] * kSegUnits);
+            return table_p[nd.table] * double(units);
+        };
+        for (const SigStep &st : S.steps)
             std::stable_sort(perm.begin() + st.item_begin, perm.begin() + st.item_end,
-                             [&](uint32_t a, uint32_t b) { return cost(a) > cost(b); });
+                             [&](uint32_t x, uint32_t y) { return cost(x) > cost(y); });
+        for (size_t k = 0; k < n_items; k++) {
+            S.items[2 * k] = items[2 * perm[k]];
+            S.items[2 * k + 1] = items[2 * perm[k] + 1];
         }
-        std::vector<uint32_t> items2(G.items.size());
-        for (size_t i = 0; i < n_items; i++) {
-            items2[2 * i] = G.items[2 * perm[i]];
-            items2[2 * i + 1] = G.items[2 * perm[i] + 1];
+        // device item records (the walk reads one 16-byte record per stream)
+        for (size_t k = 0; k < n_items; k++) {
+            const uint32_t di = S.items[2 * k], sg = S.items[2 * k + 1];
+            const NoiseDesc &nd = G.noise[di];
+            const uint32_t units = std::min(kSegUnits, nd.n_units - sg * kSegUnits);
+            S.item_rec.push_back(nd.op_index);
+            S.item_rec.push_back(sg);
+            S.item_rec.push_back(G.unit_base[di] + sg * kSegUnits);
+            S.item_rec.push_back(nd.kind | (nd.table << 3) | ((units - 1) << 16) | (di << 22));
         }
-        G.items.swap(items2);
-    }
-    // device item records (the walk reads one 16-byte record per stream)
-    if (G.noise.size() > 1024 || G.tables.size() / kTableWords > 8192) {
-        G.why = "too many noise ops or distinct probabilities for the device item records";
-        G.items.clear();
-        G.steps.clear();
-        return TMCS_OK;
-    }
-    for (size_t i = 0; i < n_items; i++) {
-        const uint32_t di = G.items[2 * i], sg = G.items[2 * i + 1];
-        const NoiseDesc &nd = G.noise[di];
-        const uint32_t units = std::min(kSegUnits, nd.n_units - sg * kSegUnits);
-        G.item_rec.push_back(nd.op_index);
-        G.item_rec.push_back(sg);
-        G.item_rec.push_back(G.unit_base[di] + sg * kSegUnits);
-        G.item_rec.push_back(nd.kind | (nd.table << 3) | ((units - 1) << 16) | (di << 22));
+        return true;
+    };
+    for (uint64_t W = W0; W >= Wmin && G.sched.size() < kSigMaxSchedules; W >>= 1) {
+        G.sched.emplace_back();
+        if (!build_schedule(W, G.sched.back())) {
+            G.why = "internal: schedule";
+            G.sched.clear();
+            return TMCS_OK;
+        }
+        if (W == 1024) break;
     }
     G.ok = true;
     G.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();

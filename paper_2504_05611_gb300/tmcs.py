@@ -35,7 +35,7 @@ assert OP_DTYPE.itemsize == 32
 STATS_FIELDS = ("n_layers", "n_slots", "n_xor", "n_zero", "n_copy", "n_noise_ops", "n_noise_units",
                 "n_noise_segments", "n_parity_terms", "live_components", "pruned_updates",
                 "sig_ok", "sig_window", "sig_steps", "sig_items", "sig_generators", "sig_entries",
-                "sig_build_us", "sig_max_step_items")
+                "sig_build_us", "sig_max_step_items", "sig_schedules", "sig_min_window")
 
 
 class TmcsError(RuntimeError):
@@ -98,7 +98,7 @@ def lib() -> ctypes.CDLL:
         L.tmcs_fault_signatures.argtypes = [P, U64, U64, P, P, P]
         L.tmcs_sample_measurements.argtypes = [P, U64, U64, U64, P, P]
         L.tmcs_fault_outputs.argtypes = [P, U64, P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
-        L.tmcs_launch_shape.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
+        L.tmcs_launch_shape.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
         L.tmcs_measure_peaks.argtypes = [P]
         L.tmcs_server_open.argtypes = [P, ctypes.POINTER(P)]
         L.tmcs_server_submit.argtypes = [P, P, U64, U64, ctypes.POINTER(ctypes.c_uint64)]
@@ -330,12 +330,16 @@ KERNEL_NAMES = {3: "frame_kernel", 4: "frame_kernel_w", 5: "sig_kernel"}
 
 def tmcs_launch_shape(handle: int) -> Dict[str, object]:
     """Autotuned launch shape on the current device: mode (0 = not tuned),
-    chunks per CTA (or per warp group), CTA size, and the kernel's name."""
-    m, k, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(lib().tmcs_launch_shape(ctypes.c_void_p(handle), ctypes.byref(m), ctypes.byref(k), ctypes.byref(t)))
+    chunks per CTA (or per warp group), CTA size, detector ring of the chosen
+    signature schedule (0 for the frame kernels), and the kernel's name."""
+    m, k, t, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().tmcs_launch_shape(ctypes.c_void_p(handle), ctypes.byref(m), ctypes.byref(k), ctypes.byref(t),
+                                   ctypes.byref(w)))
     name = KERNEL_NAMES.get(m.value)
-    return {"mode": m.value, "chunks": k.value, "threads": t.value,
-            "kernel": f"{name}<{k.value}> ({t.value} threads)" if name else None}
+    label = None
+    if name:
+        label = f"{name}<{k.value}> ({t.value} threads" + (f", ring {w.value})" if w.value else ")")
+    return {"mode": m.value, "chunks": k.value, "threads": t.value, "ring_window": w.value, "kernel": label}
 
 
 class _Peaks(ctypes.Structure):

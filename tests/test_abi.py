@@ -217,6 +217,31 @@ def test_signature_window_forces_steps(tmcs, window, monkeypatch):
         tmcs.tmcs_circuit_free(h)
 
 
+def test_signature_schedules_halve_the_ring(tmcs):
+    """The program carries up to three schedules whose rings halve from the
+    main one down to the smallest feasible power of two (>= 1024); a
+    1024-detector main ring leaves a single schedule."""
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc11"), 11, 11, C.NoiseModel(0.001, 0.01))
+    h = tmcs.tmcs_circuit_build(circ)
+    try:
+        st = tmcs.tmcs_circuit_stats(h)
+        assert st["sig_ok"] == 1 and st["sig_window"] == 4096
+        assert st["sig_schedules"] == 3 and st["sig_min_window"] == 1024
+    finally:
+        tmcs.tmcs_circuit_free(h)
+
+
+def test_signature_single_schedule_at_the_floor(tmcs, monkeypatch):
+    monkeypatch.setenv("TMCS_SIG_WINDOW", "1024")
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc11"), 11, 11, C.NoiseModel(0.001, 0.01))
+    h = tmcs.tmcs_circuit_build(circ)
+    try:
+        st = tmcs.tmcs_circuit_stats(h)
+        assert st["sig_schedules"] == 1 and st["sig_min_window"] == st["sig_window"] == 1024
+    finally:
+        tmcs.tmcs_circuit_free(h)
+
+
 def _long_span_circuit(n_mid):
     """An X error on qubit 0 flips detector 0 (first measurement) and the last
     detector (second measurement, after n_mid other detectors)."""

@@ -220,6 +220,23 @@ def test_signature_kernel_shapes_are_bit_exact(monkeypatch, tile_k, threads, win
     assert_parity(circ, 64 * 41 + 29, seed=23, first_chunk=7)
 
 
+@pytest.mark.parametrize("sched", [0, 1, 2])
+@pytest.mark.parametrize("tile_k,threads", [(4, 1024), (8, 512), (2, 256)])
+def test_signature_schedules_are_bit_exact(monkeypatch, sched, tile_k, threads):
+    """Every ring-window schedule of the program (4096, 2048 and 1024
+    detectors for this circuit) reproduces the oracle."""
+    monkeypatch.setenv("TMCS_KERNEL", "5")
+    monkeypatch.setenv("TMCS_SIG_SCHED", str(sched))
+    monkeypatch.setenv("TMCS_TILE_K", str(tile_k))
+    monkeypatch.setenv("TMCS_THREADS", str(threads))
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc11"), 11, 11, C.NoiseModel(0.003, 0.02))
+    h = tmcs.tmcs_circuit_build(circ)
+    st = tmcs.tmcs_circuit_stats(h)
+    tmcs.tmcs_circuit_free(h)
+    assert st["sig_schedules"] == 3
+    assert_parity(circ, 64 * 19 + 45, seed=29, first_chunk=3)
+
+
 @pytest.mark.parametrize("queue", [1, 64])
 def test_signature_kernel_queue_overflow(monkeypatch, queue):
     """Events that find the shared event queue full are applied directly:
