@@ -133,8 +133,9 @@ typedef struct {
     uint64_t sig_entries;     /* (generator, output) pairs */
     uint64_t sig_build_us;    /* host time to build it, microseconds */
     uint64_t sig_max_step_items; /* segments in the largest step */
-    uint64_t sig_schedules;   /* ring-window schedules carried (window halves each time) */
-    uint64_t sig_min_window;  /* ring size of the smallest schedule */
+    uint64_t sig_schedules;   /* barrier schedules carried (ring window halves each time) */
+    uint64_t sig_min_window;  /* ring size of the smallest barrier schedule */
+    uint64_t sig_pipe_schedules; /* pipelined schedules carried (several steps in flight) */
 } tmcs_stats;
 int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out);
 
@@ -160,7 +161,8 @@ int tmcs_reference_sample(const tmcs_circuit *c, uint8_t *meas_bits);
  * event-signature program (tmcs_circuit_stats sig_ok), else the frame
  * kernels; both give the same bits. Tuning knobs in the environment change
  * only the schedule: TMCS_KERNEL (3 CTA frame kernel, 4 warp-group frame
- * kernel, 5 event-signature kernel), TMCS_TILE_K, TMCS_THREADS,
+ * kernel, 5 event-signature kernel, 6 pipelined event-signature kernel),
+ * TMCS_TILE_K, TMCS_THREADS, TMCS_SIG_SCHED (signature schedule index),
  * TMCS_SIG_WINDOW (read by tmcs_circuit_build), TMCS_AUTOTUNE=0.
  * Errors: TMCS_E_INVALID (NULL circuit/buffer, shots == 0), TMCS_E_CUDA,
  * TMCS_E_OOM (program upload).
@@ -291,9 +293,9 @@ int tmcs_check_device(void);
  * The launch shape the autotuner chose for this circuit on the current
  * device (for reports): *mode = 0 if it has not run yet (first large call),
  * 3 = CTA-wide frame kernel, 4 = warp-group frame kernel, 5 = event-signature
- * kernel; *chunks = 64-shot chunks per CTA (mode 3, 5) or per warp group
+ * kernel, 6 = pipelined event-signature kernel; *chunks = 64-shot chunks per CTA (mode 3, 5) or per warp group
  * (mode 4); *threads = CTA size; *ring_window = detector ring of the chosen
- * event-signature schedule (mode 5; 0 otherwise). Any pointer may be NULL.
+ * event-signature schedule (modes 5, 6; 0 otherwise). Any pointer may be NULL.
  * Errors: TMCS_E_INVALID (NULL circuit), TMCS_E_CUDA (no current device).
  */
 int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *threads, int *ring_window);

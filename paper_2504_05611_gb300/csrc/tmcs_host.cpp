@@ -1174,7 +1174,15 @@ int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out) {
     out->sig_entries = G.gen_ent.size();
     out->sig_build_us = uint64_t(G.build_seconds * 1e6);
     out->sig_window = out->sig_steps = out->sig_items = out->sig_max_step_items = 0;
-    out->sig_schedules = G.sched.size();
+    out->sig_schedules = out->sig_pipe_schedules = out->sig_min_window = 0;
+    for (const SigSchedule &S : G.sched) {
+        if (S.lag) {
+            out->sig_pipe_schedules++;
+            continue;
+        }
+        out->sig_schedules++;
+        out->sig_min_window = S.window;
+    }
     if (!G.sched.empty()) {
         const SigSchedule &S = G.sched[0];
         out->sig_window = S.window;
@@ -1182,7 +1190,6 @@ int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out) {
         out->sig_items = S.items.size() / 2;
         for (const SigStep &st : S.steps)
             out->sig_max_step_items = std::max<uint64_t>(out->sig_max_step_items, st.item_end - st.item_begin);
-        out->sig_min_window = G.sched.back().window;
     }
     return TMCS_OK;
 }
@@ -1191,30 +1198,28 @@ int tmcs_fault_outputs(const tmcs_circuit *c, uint64_t fault, uint32_t *out, uin
     if (!c || !n_out || (cap && !out)) return fail(TMCS_E_INVALID, "NULL argument");
     const SigProgram &G = c->sig;
     if (!G.ok) return fail(TMCS_E_INVALID, "no event-signature table: " + G.why);
+    // read from the device table the samplers apply (one slot per event, in
+    // fault order), converted back to output ids
     uint64_t f = fault;
-    for (const NoiseDesc &nd : G.noise) {
-        const uint64_t KP = nd.kind == N_DEP2 ? 15 : (nd.kind == N_DEP1 || nd.kind == N_PC1) ? 3 : 1;
-        const uint64_t nf = uint64_t(nd.n_units) * KP;
+    for (uint32_t di = 0; di < G.noise.size(); di++) {
+        const NoiseDesc &nd = G.noise[di];
+        const uint64_t nf = uint64_t(nd.n_units) * sig_paulis(nd.kind);
         if (f >= nf) {
             f -= nf;
             continue;
         }
-        const uint32_t unit = uint32_t(f / KP), pk = uint32_t(f % KP) + 1u;
-        const uint32_t mask = sig_mask(nd.kind, pk), ng = sig_gens(nd.kind);
-        std::vector<uint32_t> v;
-        for (uint32_t g = 0; g < ng; g++)
-            if (mask >> g & 1u) {
-                const uint32_t id = nd.tgt_off + unit * ng + g;
-                v.insert(v.end(), G.gen_ent.begin() + G.gen_off[id], G.gen_ent.begin() + G.gen_off[id + 1]);
-            }
-        std::sort(v.begin(), v.end());
-        std::vector<uint32_t> w;  // XOR: drop pairs
-        for (size_t i = 0; i < v.size();) {
-            size_t j = i;
-            while (j < v.size() && v[j] == v[i]) j++;
-            if ((j - i) & 1) w.push_back(v[i]);
-            i = j;
+        const size_t slot = 2 * (size_t(G.ev_base[di]) + size_t(f));
+        const uint32_t w0 = G.ev_ent[slot], w1 = G.ev_ent[slot + 1];
+        std::vector<uint32_t> w;
+        if (w0 == kEvNone) {
+        } else if (w0 & kEvOverflow) {
+            w.assign(G.ev_ent.begin() + (w0 & ~kEvOverflow), G.ev_ent.begin() + (w0 & ~kEvOverflow) + w1);
+        } else {
+            w.push_back(w0);
+            if (w1 != kEvNone) w.push_back(w1);
         }
+        for (uint32_t &e : w) e = (e & (1u << 29)) ? (kSigObsFlag | (e & 0x1FFFFFFFu)) : e;
+        std::sort(w.begin(), w.end());
         *n_out = uint32_t(w.size());
         for (size_t i = 0; i < w.size() && i < cap; i++) out[i] = w[i];
         return TMCS_OK;

@@ -97,7 +97,8 @@ struct Program {
 };
 
 struct SigStep;
-constexpr int kSigMaxSchedules = 3;  // ring windows an event-signature program carries
+constexpr int kSigMaxSchedules = 9;  // schedules an event-signature program carries
+constexpr int kSigMaxLag = 4;        // steps in flight in a pipelined schedule
 
 // One device copy of a program.
 struct DeviceProgram {
@@ -126,7 +127,7 @@ struct DeviceSig {
     const uint32_t *tables = nullptr;
     const uint32_t *items[kSigMaxSchedules] = {};  // item records of each schedule
     const SigStep *steps[kSigMaxSchedules] = {};
-    const uint32_t *unit_ent = nullptr;
+    const uint32_t *ev_ent = nullptr;
 };
 
 // Per-device scratch of the library: a status word that kernels set when a
@@ -154,12 +155,20 @@ struct SigStep {
 };
 
 constexpr uint32_t kSigObsFlag = 0x80000000u;  // entry = observable index | flag
+constexpr uint32_t kEvNone = 0xFFFFFFFFu;      // empty word of an event slot
+constexpr uint32_t kEvOverflow = 0x80000000u;  // event slot word 0: list in the overflow area
 
 // One schedule of a program: its items in walk order, its steps and the
 // ring size they need. Schedules differ only in the window; the output is
 // the same for every one of them.
 struct SigSchedule {
-    uint32_t window = 0;             // ring size in detectors (power of two)
+    // Ring size in detectors (power of two). For a barrier schedule (lag 0)
+    // every step's detectors lie in [flush_lo, flush_lo + window). For a
+    // pipelined schedule (lag L > 0) up to L consecutive steps, of this tile
+    // and the next, run at once; the ring then holds every detector that
+    // such a run of steps touches or has yet to flush.
+    uint32_t window = 0;
+    uint32_t lag = 0;
     std::vector<uint32_t> items;     // (descriptor, segment) pairs, 2 words per item
     // Device item records, 4 words per item: op index, segment, global index
     // of the segment's first unit, kind | table << 3 | (units - 1) << 16 |
@@ -172,21 +181,22 @@ struct SigProgram {
     bool ok = false;
     std::string why;                 // reason the program is unusable (ok = false)
     std::vector<NoiseDesc> noise;    // every noise op with p > 0; tgt_off = first generator id
-                                     // (host); the device copy carries unit_base there
+                                     // (host); the device copy carries ev_base there
     std::vector<uint32_t> tables;    // kTableWords per distinct p
-    // Schedules by decreasing window; schedule 0 has the largest window
-    // (fewest steps) and is the one the batch sampler and the statistics use.
+    uint32_t n_det = 0;              // detectors of the circuit
+    // Barrier schedules (lag 0) by decreasing window, then pipelined ones.
+    // Schedule 0 has the largest window (fewest steps) and is the one the
+    // batch sampler and the statistics use.
     std::vector<SigSchedule> sched;
     std::vector<uint32_t> gen_off;   // CSR offsets per generator (n_gens + 1)
     std::vector<uint32_t> gen_ent;   // detector index, or kSigObsFlag | observable index
-    // Device layout: a slot of slot_words (8 or 16) words per noise unit,
-    // global unit index = descriptor's unit_base + unit: word 0 = entry count
-    // n; n < slot_words: entries in words 1..n; else word 1 = offset of the n
-    // entries in the overflow area that follows the slots. An entry is
-    // generator << 30 | observable flag << 29 | output index.
-    std::vector<uint32_t> unit_base;  // per descriptor: first global unit index
-    std::vector<uint32_t> unit_ent;
-    uint32_t slot_words = 8;
+    // Device layout: two words per event (unit, Pauli index), in fault order
+    // from the descriptor's ev_base: word 0 = first entry, kEvNone (no
+    // outputs) or kEvOverflow | offset of the list in the overflow area
+    // that follows the slots (then word 1 = its length); word 1 = second
+    // entry or kEvNone. An entry is observable flag << 29 | output index.
+    std::vector<uint32_t> ev_base;   // per descriptor: index of its first event slot
+    std::vector<uint32_t> ev_ent;
     double build_seconds = 0;
 };
 
@@ -198,6 +208,9 @@ struct SigProgram {
 #define TMCS_HD
 #endif
 TMCS_HD inline uint32_t sig_gens(uint32_t kind) { return kind == 3u ? 4u : 2u; }
+// Pauli indices (events) per unit: 15 for DEPOLARIZE2, 3 for DEPOLARIZE1 and
+// PAULI_CHANNEL_1, 1 for X_ERROR and Z_ERROR.
+TMCS_HD inline uint32_t sig_paulis(uint32_t kind) { return kind == 3u ? 15u : (kind == 2u || kind == 4u) ? 3u : 1u; }
 // Generator mask of Pauli index pk (bit 0 = X part, bit 1 = Z part per qubit).
 TMCS_HD inline uint32_t sig_mask(uint32_t kind, uint32_t pk) {
     return kind == 3u ? ((pk >> 2) | ((pk & 3u) << 2)) : kind == 0u ? 1u : kind == 1u ? 2u : pk;

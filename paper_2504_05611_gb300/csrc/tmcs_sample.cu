@@ -586,19 +586,24 @@ struct SigArgs {
     const uint32_t *tables;
     const uint4 *item_rec;    // per item: op index, segment, first unit, kind | table << 3 | (units-1) << 16 | desc << 22
     const uint4 *steps;       // SigStep: item_begin, item_end, flush_lo, flush_hi
-    const uint32_t *unit_ent; // slot_words words per global unit (count, entries), then overflow
+    const uint32_t *ev_ent;   // two words per event slot (see SigProgram), then the overflow lists
     uint32_t n_steps;
     uint32_t window_mask;     // ring size - 1 (power of two)
     uint32_t n_obs;
     uint32_t queue_cap;       // events the shared queue holds
     uint32_t smem_tables;     // gap tables copied to shared memory (0, or all of them)
-    uint32_t slot_words;      // 8 or 16
     uint32_t stage_items;     // shared staging buffer for a step's item records (0: read them from global)
     uint32_t key0, key1;
     uint32_t first_chunk;
     uint64_t n_cols, last_mask, n_tiles;
     uint64_t *det;
     uint64_t *obs;
+    // pipelined kernel only
+    uint32_t lag;             // steps in flight (> 0)
+    uint32_t n_items;         // item records of the schedule
+    uint32_t n_det;           // detectors (tile T's ring offset is T * n_det)
+    uint32_t vec_out;         // det is 16-byte aligned and n_cols even: 16-byte output stores
+    uint32_t *status;         // device status word (bit 0: a bounded wait expired)
 };
 
 // Draws of one (segment, chunk) stream from its start; sink(pos, pauli) per
@@ -621,60 +626,40 @@ __device__ __forceinline__ void walk_stream(const NoiseDesc &nd, const uint32_t 
     }
 }
 
-// Queued events: global unit index (low word), and lane | chunk k << 6 |
-// Pauli index << 9 | noise kind << 13 (high word). A thread applies up to N
-// at once; each event's data is the first 32 bytes of its unit's slot (the
-// count and up to 7 entries), all N loaded before any is used so their
-// latencies overlap. Longer units read the rest of the slot (16-word slots)
-// or their overflow list.
+// Queued events: event slot index (low word), and lane | chunk k << 6 |
+// ring offset << 16 | observable buffer << 30 (high word; the last two are
+// zero in the barrier kernel; bits 9-15 are not read here). A thread
+// applies up to N at once, all N slot loads issued before any is used so
+// their latencies overlap.
 template <int N>
 __device__ __forceinline__ void sig_apply_events(const SigArgs &A, const uint64_t (&q)[N], int n, uint64_t *ring,
                                                  uint64_t *oacc, int K) {
-    uint4 v0[N], v1[N];
+    uint2 v[N];
+#pragma unroll
+    for (int j = 0; j < N; j++)
+        v[j] = j < n ? __ldg(reinterpret_cast<const uint2 *>(A.ev_ent) + uint32_t(q[j])) : make_uint2(kEvNone, kEvNone);
 #pragma unroll
     for (int j = 0; j < N; j++) {
-        if (j < n) {
-            const uint4 *sl = reinterpret_cast<const uint4 *>(A.unit_ent + size_t(uint32_t(q[j])) * A.slot_words);
-            v0[j] = __ldg(sl);
-            v1[j] = __ldg(sl + 1);
-        } else {
-            v0[j] = make_uint4(0u, 0u, 0u, 0u);
-            v1[j] = v0[j];
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < N; j++) {
-        const uint32_t cnt = v0[j].x;
-        if (cnt == 0) continue;
+        if (v[j].x == kEvNone) continue;
         const uint32_t hi = uint32_t(q[j] >> 32);
         const uint32_t lane = hi & 63u, k = (hi >> 6) & 7u;
-        const uint32_t m = sig_mask(hi >> 13, (hi >> 9) & 15u);
+        const uint32_t roff = (hi >> 16) & 0x3FFFu;
         unsigned int *ring32 = reinterpret_cast<unsigned int *>(ring + k) + (lane >> 5);
-        unsigned int *obs32 = reinterpret_cast<unsigned int *>(oacc + k) + (lane >> 5);
+        unsigned int *obs32 =
+            reinterpret_cast<unsigned int *>(oacc + k + size_t((hi >> 30) & 1u) * A.n_obs * K) + (lane >> 5);
         const uint32_t bit = 1u << (lane & 31u);
         auto put = [&](uint32_t w) {
-            if (!((m >> (w >> 30)) & 1u)) return;
             const uint32_t idx = w & 0x1FFFFFFFu;
             unsigned int *p = (w & (1u << 29)) ? obs32 + size_t(idx) * 2 * K
-                                                : ring32 + size_t(idx & A.window_mask) * 2 * K;
+                                                : ring32 + size_t((idx + roff) & A.window_mask) * 2 * K;
             atomicXor(p, bit);
         };
-        if (cnt < 8) {
-            const uint32_t w7[7] = {v0[j].y, v0[j].z, v0[j].w, v1[j].x, v1[j].y, v1[j].z, v1[j].w};
-#pragma unroll
-            for (uint32_t t = 0; t < 7; t++)
-                if (t < cnt) put(w7[t]);
-        } else if (cnt < A.slot_words) {
-            const uint4 *sl = reinterpret_cast<const uint4 *>(A.unit_ent + size_t(uint32_t(q[j])) * A.slot_words);
-            const uint4 v2 = __ldg(sl + 2), v3 = __ldg(sl + 3);
-            const uint32_t w15[15] = {v0[j].y, v0[j].z, v0[j].w, v1[j].x, v1[j].y, v1[j].z, v1[j].w,
-                                      v2.x, v2.y, v2.z, v2.w, v3.x, v3.y, v3.z, v3.w};
-#pragma unroll
-            for (uint32_t t = 0; t < 15; t++)
-                if (t < cnt) put(w15[t]);
+        if (v[j].x & kEvOverflow) {
+            const uint32_t *ov = A.ev_ent + (v[j].x & ~kEvOverflow);
+            for (uint32_t x = 0; x < v[j].y; x++) put(__ldg(ov + x));
         } else {
-            const uint32_t *ov = A.unit_ent + v0[j].y;
-            for (uint32_t x = 0; x < cnt; x++) put(__ldg(ov + x));
+            put(v[j].x);
+            if (v[j].y != kEvNone) put(v[j].y);
         }
     }
 }
@@ -692,21 +677,22 @@ __device__ __forceinline__ uint32_t grab_index(uint32_t *ctr) {
 }
 
 // Applies the n events of a warp's queue slice, converged: lane l takes
-// events l, l + 32, ... four at a time. Called by all 32 lanes.
+// events l, l + 32, ... N at a time. Called by all 32 lanes.
+template <int N = 4>
 __device__ __forceinline__ void sig_warp_apply(const SigArgs &A, const uint64_t *wq, uint32_t n, uint64_t *ring,
                                                uint64_t *oacc, int K) {
     __syncwarp();
     const uint32_t lane = threadIdx.x & 31u;
-    for (uint32_t e0 = lane; e0 < n; e0 += 128u) {
-        uint64_t qb[4];
+    for (uint32_t e0 = lane; e0 < n; e0 += 32u * N) {
+        uint64_t qb[N];
         int nb = 0;
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < N; j++) {
             const uint32_t e = e0 + 32u * uint32_t(j);
             qb[j] = e < n ? wq[e] : 0ull;
             nb += e < n ? 1 : 0;
         }
-        sig_apply_events<4>(A, qb, nb, ring, oacc, K);
+        sig_apply_events<N>(A, qb, nb, ring, oacc, K);
     }
     __syncwarp();
 }
@@ -727,7 +713,7 @@ __device__ __forceinline__ uint32_t sig_walk(const SigArgs &A, const uint4 st, u
     const uint32_t lt = (1u << lane) - 1u;
     uint32_t qn = 0;  // events in the slice (warp-uniform)
     bool have = false, exhausted = false;
-    uint32_t call = 0, seg = 0, op = 0, kind = 0, chunk = 0, ubase = 0, tag = 0, t1 = 0, t2 = 0, npauli = 1;
+    uint32_t call = 0, seg = 0, op = 0, kind = 0, chunk = 0, ubase = 0, tag = 0, t1 = 0, t2 = 0, npauli = 1, kp = 1;
     int pos = -1, n_trials = 0;
     const uint32_t *Tt = tabs;
     float inv = 0.f;
@@ -749,9 +735,10 @@ __device__ __forceinline__ uint32_t sig_walk(const SigArgs &A, const uint4 st, u
                     t2 = A.noise[rec.w >> 22].t2;
                 }
                 npauli = npauli_of(kind);
+                kp = sig_paulis(kind);
                 chunk = chunk0 + k;
                 ubase = rec.z;
-                tag = (k << 6) | (kind << 13);
+                tag = k << 6;
                 n_trials = 64 * int(((rec.w >> 16) & 63u) + 1u);
                 call = 0;
                 pos = -1;
@@ -774,7 +761,7 @@ __device__ __forceinline__ uint32_t sig_walk(const SigArgs &A, const uint4 st, u
                 } else {
                     const uint32_t pk = kind == N_PC1 ? (wp < t1 ? 1u : wp < t2 ? 3u : 2u)
                                                       : 1u + __umulhi(wp, npauli);
-                    q = uint64_t(ubase + uint32_t(pos >> 6)) | (uint64_t(tag | uint32_t(pos & 63) | (pk << 9)) << 32);
+                    q = uint64_t(ubase + uint32_t(pos >> 6) * kp + (pk - 1u)) | (uint64_t(tag | uint32_t(pos & 63)) << 32);
                     ev = true;
                 }
             }
@@ -903,6 +890,361 @@ __global__ void __launch_bounds__(1024) sig_kernel(const SigArgs A) {
     for (uint64_t tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) sig_tile<K>(A, S, tile, &s_next);
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined event-signature kernel: the walk and the event application of
+// sig_kernel without CTA barriers. The last warp of the CTA flushes; the
+// others walk. Walkers take (tile, step, item, chunk) streams in CTA order
+// from one shared counter, across step and tile boundaries; a stream of
+// step q (counted over the CTA's tiles) starts once steps < q + 1 - lag are
+// flushed, so at most `lag` steps are in flight and the ring (sized for any
+// lag consecutive steps by the schedule builder) never holds two live
+// detectors in one slot. A walker counts its finished streams per step and
+// publishes the counts after applying its queued events; the flusher waits
+// for step q's count to reach its stream total, writes and clears the
+// detectors step q finalised (and the tile's observables after its last
+// step), stages the item records of step q + lag, then advances `flushed`.
+// Tile T's detector d lives in ring slot (T * n_det + d) mod ring, its
+// observables in buffer T mod 2. Every wait is bounded (kWaitNs); on expiry
+// the kernel sets the status bit and every warp leaves.
+
+// events a walker lane applies at once (their slot loads overlap)
+#ifndef TMCS_PIPE_APPLY
+#define TMCS_PIPE_APPLY 1
+#endif
+constexpr int kPipeApply = TMCS_PIPE_APPLY;
+
+struct PipeCtl {
+    unsigned long long next;          // streams handed out
+    uint32_t flushed;                 // steps flushed
+    uint32_t abort;                   // a bounded wait expired
+    uint32_t done[kSigMaxLag];        // published finished streams of step q (slot q mod lag)
+    uint32_t wdone[32 * kSigMaxLag];  // per warp: finished streams not yet published
+};
+
+struct PipeSmem {
+    uint64_t *ring, *oacc;
+    uint32_t *stab;
+    uint4 *sitems;
+    uint64_t *queue;
+};
+
+// Same order and sizes as sig_smem_bytes for a pipelined schedule: ring,
+// two observable buffers (padded to 16 bytes), gap tables, lag staging
+// buffers of item records, event queue.
+__device__ __forceinline__ PipeSmem pipe_layout(uint64_t *smem, const SigArgs &A, int K) {
+    PipeSmem S;
+    const size_t W = size_t(A.window_mask) + 1;
+    S.ring = smem;
+    S.oacc = smem + W * K;
+    S.stab = reinterpret_cast<uint32_t *>(smem + (((W + 2 * size_t(A.n_obs)) * K + 1) & ~size_t(1)));
+    S.sitems = reinterpret_cast<uint4 *>(S.stab + size_t(A.smem_tables) * kTableWords);
+    S.queue = reinterpret_cast<uint64_t *>(S.sitems + size_t(A.stage_items) * A.lag);
+    return S;
+}
+
+__device__ __forceinline__ uint32_t ld_shared_volatile(const uint32_t *p) {
+    return *reinterpret_cast<const volatile uint32_t *>(p);
+}
+
+// 64-bit warp-aggregated counter (see grab_index).
+__device__ __forceinline__ uint64_t grab_index64(unsigned long long *ctr) {
+    const uint32_t mask = __activemask();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t leader = uint32_t(__ffs(mask)) - 1u;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, int(leader));
+    return uint64_t(base) + uint64_t(__popc(mask & ((1u << lane) - 1u)));
+}
+
+// Adds this warp's finished-stream counts to the step totals. All 32 lanes;
+// every event of those streams has been applied by this warp before. The
+// queue slice of a walker warp holds at least 64 events (two ballots).
+__device__ __forceinline__ void pipe_publish(PipeCtl &C, uint32_t warp, uint32_t lag) {
+    __syncwarp();
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane < lag) {
+        const uint32_t v = C.wdone[warp * kSigMaxLag + lane];
+        if (v) {
+            C.wdone[warp * kSigMaxLag + lane] = 0;
+            __threadfence_block();
+            atomicAdd(&C.done[lane], v);
+        }
+    }
+    __syncwarp();
+}
+
+template <bool SMT, int K>
+__device__ __forceinline__ void pipe_walk(const SigArgs &A, const PipeSmem &S, PipeCtl &C, uint32_t nt,
+                                          uint32_t nv_last, const uint32_t *tabs) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t lag = A.lag, n_steps = A.n_steps;
+    const uint32_t wcap = A.queue_cap / ((blockDim.x >> 5) - 1u);
+    uint64_t *wq = S.queue + size_t(warp) * wcap;
+    const uint64_t per_tile = uint64_t(A.n_items) * K;
+    const uint64_t total = uint64_t(nt - 1) * per_tile + uint64_t(A.n_items) * nv_last;
+    uint32_t qn = 0, unpub = 0;  // warp-uniform
+    bool have = false, pend = false, exhausted = false, waiting = false;
+    // the lane's stream: Philox counter words (call, chunk, op, seg), first
+    // unit, event tag (chunk k, kind, ring offset, observable buffer), gap
+    // table (word offset), position and length in trials
+    uint32_t call = 0, seg = 0, op = 0, chunk = 0, ubase = 0, tag = 0, toff = 0, t1 = 0, t2 = 0;
+    int pos = -1, n_trials = 0;
+    float inv = 0.f;
+    // cursor over the CTA's tiles and steps; pq = the grabbed stream's index
+    // within tile curT (valid while pend, and its step is curS)
+    uint32_t curT = 0xFFFFFFFFu, curS = 0, ring_off = 0, pq = 0, t_wait = 0;
+    uint64_t tbase = 0;
+    for (;;) {
+        if (!have && !pend && !exhausted) {
+            const uint64_t p = grab_index64(&C.next);
+            if (p >= total || ld_shared_volatile(&C.abort)) {
+                exhausted = true;
+            } else {
+                if (curT == 0xFFFFFFFFu || p - tbase >= per_tile) {
+                    curT = uint32_t(p / per_tile);
+                    tbase = uint64_t(curT) * per_tile;
+                    curS = 0;
+                    ring_off = uint32_t((uint64_t(curT) * A.n_det) & A.window_mask);
+                }
+                pq = uint32_t(p - tbase);
+                const uint32_t nv = curT == nt - 1 ? nv_last : uint32_t(K);
+                const uint32_t il = nv == uint32_t(K) ? pq / uint32_t(K) : pq / nv;
+                while (il >= __ldg(&A.steps[curS].y)) curS++;
+                pend = true;
+            }
+        }
+        if (pend && curT * n_steps + curS < ld_shared_volatile(&C.flushed) + lag) {
+            __threadfence_block();  // the flusher's clears of the ring precede this stream's events
+            const uint32_t nv = curT == nt - 1 ? nv_last : uint32_t(K);
+            uint32_t il, k;
+            if (nv == uint32_t(K)) {
+                il = pq / uint32_t(K);
+                k = pq % uint32_t(K);
+            } else {
+                il = pq / nv;
+                k = pq - il * nv;
+            }
+            const uint32_t seq = curT * n_steps + curS;
+            const uint4 rec = A.stage_items
+                                  ? S.sitems[size_t(seq % lag) * A.stage_items + (il - __ldg(&A.steps[curS].x))]
+                                  : __ldg(A.item_rec + il);
+            const uint32_t kind = rec.w & 7u;
+            toff = ((rec.w >> 3) & 0x1FFFu) * kTableWords;
+            inv = __uint_as_float(tabs[toff + kGapLen]);
+            seg = rec.y;
+            op = rec.x;
+            if (kind == N_PC1) {
+                t1 = A.noise[rec.w >> 22].t1;
+                t2 = A.noise[rec.w >> 22].t2;
+            }
+            const uint64_t col = (uint64_t(blockIdx.x) + uint64_t(curT) * gridDim.x) * K + k;
+            chunk = A.first_chunk + uint32_t(col);
+            ubase = rec.z;
+            tag = (k << 6) | (kind << 13) | (ring_off << 16) | ((curT & 1u) << 30);
+            n_trials = 64 * int(((rec.w >> 16) & 63u) + 1u);
+            call = 0;
+            pos = -1;
+            have = true;
+            pend = false;
+        }
+        const uint32_t act = __ballot_sync(0xFFFFFFFFu, have);
+        const uint32_t gated = __ballot_sync(0xFFFFFFFFu, pend);
+        // apply the queue and publish the finished streams (one place, so the
+        // apply code is inlined once): when this iteration's events (at most
+        // 64) might not fit, when lanes wait for a flush that may need this
+        // warp's counts, and before leaving
+        if (qn + 64u > wcap || (gated && unpub) || (!act && (qn || unpub))) {
+            if (qn) sig_warp_apply<kPipeApply>(A, wq, qn, S.ring, S.oacc, K);
+            qn = 0;
+            if (unpub) pipe_publish(C, warp, lag);
+            unpub = 0;
+        }
+        if (!act) {
+            if (!gated) break;
+            // every live lane waits for a flush: back off (bounded)
+            if (!waiting) {
+                t_wait = uint32_t(globaltimer_ns());
+                waiting = true;
+            } else if (__any_sync(0xFFFFFFFFu, uint32_t(globaltimer_ns()) - t_wait > uint32_t(kWaitNs) ||
+                                                   ld_shared_volatile(&C.abort))) {
+                // the whole warp leaves together
+                if (lane == 0 && !ld_shared_volatile(&C.abort)) {
+                    C.abort = 1u;
+                    atomicOr(A.status, 1u);
+                }
+                return;
+            }
+            __nanosleep(128);
+            continue;
+        }
+        waiting = false;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (have) w = philox4x32_10(call, chunk, op, seg, A.key0, A.key1);
+        call++;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            bool ev = false, fin = false;
+            uint64_t q = 0;
+            if (have) {
+                const uint32_t wg = h ? w.z : w.x, wp = h ? w.w : w.y;
+                pos += 1 + gap_count_t<SMT>(tabs + toff, inv, wg);
+                if (pos >= n_trials) {
+                    have = false;
+                    fin = true;
+                } else {
+                    const uint32_t kind = (tag >> 13) & 7u;
+                    const uint32_t pauli = kind == N_PC1 ? (wp < t1 ? 1u : wp < t2 ? 3u : 2u)
+                                                         : 1u + __umulhi(wp, npauli_of(kind));
+                    q = uint64_t(ubase + uint32_t(pos >> 6) * sig_paulis(kind) + (pauli - 1u)) |
+                        (uint64_t(tag | uint32_t(pos & 63)) << 32);
+                    ev = true;
+                }
+            }
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, ev);
+            if (ev) wq[qn + uint32_t(__popc(m & lt))] = q;
+            qn += uint32_t(__popc(m));
+            const uint32_t f = __ballot_sync(0xFFFFFFFFu, fin);
+            if (fin) atomicAdd(&C.wdone[warp * kSigMaxLag + (curT * n_steps + curS) % lag], 1u);
+            unpub += uint32_t(__popc(f));
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void pipe_flush(const SigArgs &A, const PipeSmem &S, PipeCtl &C, uint32_t nt,
+                                           uint32_t nv_last) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t lag = A.lag, n_steps = A.n_steps, nseq = nt * n_steps;
+    const uint32_t mask = A.window_mask;
+    for (uint32_t seq = 0; seq < nseq; seq++) {
+        const uint32_t T = seq / n_steps, s = seq - T * n_steps;
+        const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(T) * gridDim.x;
+        const uint32_t nv = T == nt - 1 ? nv_last : uint32_t(K);
+        const uint4 st = __ldg(A.steps + s);
+        const uint32_t need = (st.y - st.x) * nv;
+        const uint32_t slot = seq % lag;
+        uint32_t ok = 1;
+        if (lane == 0 && ld_shared_volatile(&C.done[slot]) != need) {
+            const uint64_t t0 = globaltimer_ns();
+            while (ld_shared_volatile(&C.done[slot]) != need) {
+                if (ld_shared_volatile(&C.abort) || globaltimer_ns() - t0 > kWaitNs) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) {
+            if (lane == 0) {
+                C.abort = 1u;
+                atomicOr(A.status, 1u);
+            }
+            return;
+        }
+        __threadfence_block();  // the walkers' events precede the reads below
+        const uint32_t roff = uint32_t((uint64_t(T) * A.n_det) & mask);
+        const uint64_t col0 = tile * K;
+        const uint32_t nd = st.w - st.z;
+        // 16-byte ring reads and output stores (two chunk words) when the
+        // output rows allow them
+        bool vec_done = false;
+        if constexpr (K % 2 == 0) {
+            if (A.vec_out) {
+                vec_done = true;
+                constexpr uint32_t H = uint32_t(K) / 2u;
+                for (uint32_t i = lane; i < nd * H; i += 32u) {
+                    const uint32_t d = st.z + i / H, k = 2u * (i % H);
+                    ulonglong2 *r = reinterpret_cast<ulonglong2 *>(S.ring + size_t((d + roff) & mask) * K + k);
+                    ulonglong2 v = *r;
+                    *r = make_ulonglong2(0ull, 0ull);
+                    if (k >= nv) continue;
+                    const uint64_t col = col0 + k;
+                    if (col == A.n_cols - 1) v.x &= A.last_mask;
+                    if (col + 1 == A.n_cols - 1) v.y &= A.last_mask;
+                    unsigned long long *out =
+                        reinterpret_cast<unsigned long long *>(A.det + uint64_t(d) * A.n_cols + col);
+                    if (k + 1 < nv) __stcs(reinterpret_cast<ulonglong2 *>(out), v);
+                    else __stcs(out, v.x);
+                }
+            }
+        }
+        if (!vec_done) {
+            for (uint32_t i = lane; i < nd * uint32_t(K); i += 32u) {
+                const uint32_t d = st.z + i / uint32_t(K), k = i % uint32_t(K);
+                uint64_t *r = S.ring + size_t((d + roff) & mask) * K + k;
+                uint64_t v = *r;
+                *r = 0ull;
+                if (k >= nv) continue;
+                const uint64_t col = col0 + k;
+                if (col == A.n_cols - 1) v &= A.last_mask;
+                __stcs(reinterpret_cast<unsigned long long *>(A.det + uint64_t(d) * A.n_cols + col), v);
+            }
+        }
+        if (s == n_steps - 1) {
+            uint64_t *ob = S.oacc + size_t(T & 1u) * A.n_obs * K;
+            for (uint32_t i = lane; i < A.n_obs * uint32_t(K); i += 32u) {
+                const uint32_t o = i / uint32_t(K), k = i % uint32_t(K);
+                uint64_t v = ob[i];
+                ob[i] = 0ull;
+                if (k >= nv) continue;
+                const uint64_t col = col0 + k;
+                if (col == A.n_cols - 1) v &= A.last_mask;
+                A.obs[uint64_t(o) * A.n_cols + col] = v;
+            }
+        }
+        if (lane == 0) C.done[slot] = 0u;
+        if (A.stage_items && seq + lag < nseq) {
+            const uint4 s2 = __ldg(A.steps + (seq + lag) % n_steps);
+            uint4 *dst = S.sitems + size_t(slot) * A.stage_items;
+            for (uint32_t i = lane; i < s2.y - s2.x; i += 32u) dst[i] = __ldg(A.item_rec + s2.x + i);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            *reinterpret_cast<volatile uint32_t *>(&C.flushed) = seq + 1u;
+        }
+        __syncwarp();
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(1024) sig_pipe_kernel(const SigArgs A) {
+    extern __shared__ __align__(128) uint64_t smem[];
+    __shared__ PipeCtl C;
+    if (uint64_t(blockIdx.x) >= A.n_tiles) return;
+    const PipeSmem S = pipe_layout(smem, A, K);
+    const uint32_t tid = threadIdx.x, T_ = blockDim.x;
+    const uint32_t W = A.window_mask + 1u;
+    for (uint32_t i = tid; i < (W + 2u * A.n_obs) * uint32_t(K); i += T_) S.ring[i] = 0ull;
+    for (uint32_t i = tid; i < A.smem_tables * kTableWords; i += T_) S.stab[i] = __ldg(A.tables + i);
+    if (tid == 0) {
+        C.next = 0ull;
+        C.flushed = 0u;
+        C.abort = 0u;
+    }
+    for (uint32_t i = tid; i < uint32_t(kSigMaxLag); i += T_) C.done[i] = 0u;
+    for (uint32_t i = tid; i < 32u * kSigMaxLag; i += T_) C.wdone[i] = 0u;
+    const uint64_t G = gridDim.x;
+    const uint32_t nt = uint32_t((A.n_tiles - blockIdx.x + G - 1) / G);
+    const uint64_t last = uint64_t(blockIdx.x) + uint64_t(nt - 1) * G;
+    const uint64_t rem = A.n_cols - last * K;
+    const uint32_t nv_last = rem < uint64_t(K) ? uint32_t(rem) : uint32_t(K);
+    if (A.stage_items) {
+        const uint32_t nseq = nt * A.n_steps;
+        for (uint32_t j = 0; j < A.lag && j < nseq; j++) {
+            const uint4 st = __ldg(A.steps + j % A.n_steps);
+            for (uint32_t i = tid; i < st.y - st.x; i += T_)
+                S.sitems[size_t(j) * A.stage_items + i] = __ldg(A.item_rec + st.x + i);
+        }
+    }
+    __syncthreads();
+    if ((tid >> 5) == (T_ >> 5) - 1u) pipe_flush<K>(A, S, C, nt, nv_last);
+    else if (A.smem_tables) pipe_walk<true, K>(A, S, C, nt, nv_last, S.stab);
+    else pipe_walk<false, K>(A, S, C, nt, nv_last, A.tables);
+}
+
 // Many circuits in one persistent launch: work items (job, tile) in job
 // order, taken from a device counter; a CTA re-lays its shared memory out
 // (and reloads gap tables) only when it moves to another job. The job table
@@ -952,17 +1294,24 @@ constexpr uint32_t kSigQueueMin = 256;
 
 static size_t sig_table_bytes(const SigProgram &G) { return G.tables.size() * 4; }
 
-// Step item records staged in shared memory: the largest step's, if that
-// is at most 1024 records.
+// Step item records staged in shared memory per staging buffer (one for a
+// barrier schedule, lag for a pipelined one): the largest step's, if all
+// buffers together hold at most 1024 records.
 static uint32_t sig_stage_items(const SigProgram &G, int sched) {
+    const SigSchedule &S = G.sched[sched];
     uint32_t m = 0;
-    for (const SigStep &st : G.sched[sched].steps) m = std::max(m, st.item_end - st.item_begin);
-    return m <= 1024 ? m : 0u;
+    for (const SigStep &st : S.steps) m = std::max(m, st.item_end - st.item_begin);
+    return m * std::max<uint32_t>(S.lag, 1u) <= 1024 ? m : 0u;
 }
 
-// ring and observables, padded to 16 bytes
+static size_t sig_stage_bytes(const SigProgram &G, int sched) {
+    return size_t(sig_stage_items(G, sched)) * std::max<uint32_t>(G.sched[sched].lag, 1u) * 16;
+}
+
+// ring and observables (two buffers when pipelined), padded to 16 bytes
 static size_t sig_ring_bytes(const SigProgram &G, int sched, uint64_t n_obs, int K) {
-    return ((size_t(G.sched[sched].window) + size_t(n_obs)) * size_t(K) * 8 + 15) & ~size_t(15);
+    const size_t nob = G.sched[sched].lag ? 2 : 1;
+    return ((size_t(G.sched[sched].window) + nob * size_t(n_obs)) * size_t(K) * 8 + 15) & ~size_t(15);
 }
 
 // Ring + observables + event queue: the queue takes what is left of `budget`
@@ -970,15 +1319,15 @@ static size_t sig_ring_bytes(const SigProgram &G, int sched, uint64_t n_obs, int
 static uint32_t sig_queue_cap(const SigProgram &G, int sched, uint64_t n_obs, int K, size_t budget,
                               bool smem_tables) {
     const size_t ring = sig_ring_bytes(G, sched, n_obs, K) + (smem_tables ? sig_table_bytes(G) : 0) +
-                        size_t(sig_stage_items(G, sched)) * 16;
+                        sig_stage_bytes(G, sched);
     const size_t left = budget > ring ? (budget - ring) / 8 : 0;
     return uint32_t(std::min<size_t>(kSigQueueMax, std::max<size_t>(kSigQueueMin, left & ~size_t(255))));
 }
 
 static size_t sig_smem_bytes(const SigProgram &G, int sched, uint64_t n_obs, int K, uint32_t qcap,
                              bool smem_tables) {
-    return sig_ring_bytes(G, sched, n_obs, K) + (smem_tables ? sig_table_bytes(G) : 0) +
-           size_t(sig_stage_items(G, sched)) * 16 + size_t(qcap) * 8;
+    return sig_ring_bytes(G, sched, n_obs, K) + (smem_tables ? sig_table_bytes(G) : 0) + sig_stage_bytes(G, sched) +
+           size_t(qcap) * 8;
 }
 
 // ---------------------------------------------------------------------------
@@ -1438,7 +1787,7 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
         b_steps[k] = align256(G.sched[k].steps.size() * sizeof(SigStep));
         b_sched += b_items[k] + b_steps[k];
     }
-    const size_t b_ent = align256(G.unit_ent.size() * 4);
+    const size_t b_ent = align256(G.ev_ent.size() * 4);
     const size_t total = std::max<size_t>(b_noise + b_tables + b_sched + b_ent, 256);
     std::vector<uint8_t> host(total, 0);
     size_t o = 0;
@@ -1449,7 +1798,7 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
         return at;
     };
     std::vector<NoiseDesc> dn = G.noise;
-    for (size_t i = 0; i < dn.size(); i++) dn[i].tgt_off = G.unit_base[i];
+    for (size_t i = 0; i < dn.size(); i++) dn[i].tgt_off = G.ev_base[i];
     const size_t o_noise = put(dn.data(), dn.size() * sizeof(NoiseDesc), b_noise);
     const size_t o_tables = put(G.tables.data(), G.tables.size() * 4, b_tables);
     size_t o_items[kSigMaxSchedules] = {}, o_steps[kSigMaxSchedules] = {};
@@ -1458,7 +1807,7 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
         o_items[k] = put(S.item_rec.data(), S.item_rec.size() * 4, b_items[k]);
         o_steps[k] = put(S.steps.data(), S.steps.size() * sizeof(SigStep), b_steps[k]);
     }
-    const size_t o_ent = put(G.unit_ent.data(), G.unit_ent.size() * 4, b_ent);
+    const size_t o_ent = put(G.ev_ent.data(), G.ev_ent.size() * 4, b_ent);
     void *base = nullptr;
     e = cudaMalloc(&base, total);
     if (e != cudaSuccess) {
@@ -1481,7 +1830,7 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
         ds.items[k] = reinterpret_cast<const uint32_t *>(b + o_items[k]);
         ds.steps[k] = reinterpret_cast<const SigStep *>(b + o_steps[k]);
     }
-    ds.unit_ent = reinterpret_cast<const uint32_t *>(b + o_ent);
+    ds.ev_ent = reinterpret_cast<const uint32_t *>(b + o_ent);
     auto ins = c->dev_sig.emplace(dev, ds);
     *out = &ins.first->second;
     return TMCS_OK;
@@ -1531,7 +1880,8 @@ static int device_limits(DeviceLimits *lim) {
 
 struct LaunchShape {
     int mode = 3;      // 3: CTA-wide layers (frame_kernel), 4: warp-owned chunks (frame_kernel_w),
-                       // 5: event signatures (sig_kernel; tiles = resident CTAs)
+                       // 5: event signatures (sig_kernel; tiles = resident CTAs),
+                       // 6: pipelined event signatures (sig_pipe_kernel; tiles = resident CTAs)
     int K = 1;         // chunks per CTA (mode 3) or per consumer warp (mode 4)
     int warps = 0;     // chunk groups (mode 4)
     int group = 1;     // warps per chunk group (mode 4)
@@ -1541,7 +1891,7 @@ struct LaunchShape {
     int sms = 0;       // mode 5: SM count (grid = SMs x resident CTAs per SM)
     uint32_t qcap = 0; // mode 5: event-queue capacity
     bool smem_tables = false;  // mode 5: gap tables staged in shared memory
-    int sched = 0;     // mode 5: schedule (ring window) of the signature program
+    int sched = 0;     // mode 5, 6: schedule of the signature program (lag 0 for mode 5, > 0 for 6)
 };
 
 static int env_int(const char *name, int dflt) {
@@ -1603,7 +1953,7 @@ static bool sig_fits(const tmcs_circuit *c, const DeviceLimits &lim, int K, int 
 static LaunchShape make_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const DeviceLimits &lim, int K,
                                   int threads, int sched = 0) {
     LaunchShape s;
-    s.mode = 5;
+    s.mode = c->sig.sched[sched].lag ? 6 : 5;
     s.sched = sched;
     s.K = K;
     s.threads = threads;
@@ -1618,8 +1968,9 @@ static LaunchShape make_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const 
     s.qcap = sig_queue_cap(c->sig, sched, c->n_obs, K, budget, s.smem_tables);
     const int qforce = env_int("TMCS_SIG_QUEUE", 0);  // tuning/testing knob: queue capacity
     if (qforce > 0) s.qcap = uint32_t(std::min<int>(qforce, int(kSigQueueMax)));
-    // every warp's slice holds at least one ballot's worth (32 events)
-    s.qcap = std::max<uint32_t>(s.qcap, uint32_t(threads));
+    // every warp's slice holds at least one ballot's worth (32 events); a
+    // pipelined walker's slice at least one iteration's worth (64)
+    s.qcap = std::max<uint32_t>(s.qcap, uint32_t(s.mode == 6 ? 2 * threads : threads));
     s.smem = sig_smem_bytes(c->sig, sched, c->n_obs, K, s.qcap, s.smem_tables);
     const uint64_t n_tiles = (n_cols + K - 1) / K;
     s.tiles = std::min<uint64_t>(n_tiles, uint64_t(lim.sms) * ctas);
@@ -1699,9 +2050,26 @@ static cudaError_t launch_sig(const SigArgs &a, const LaunchShape &s, cudaStream
 
 // Mode 5 takes the event-signature program (device copy ds, host G); its
 // output, seed and chunk range come from a0 like the frame kernels'.
+template <int K>
+static cudaError_t launch_pipe(const SigArgs &a, const LaunchShape &s, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(sig_pipe_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sig_pipe_kernel<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             int(cudaSharedmemCarveoutMaxShared));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sig_pipe_kernel<K>, s.threads, s.smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(a.n_tiles, uint64_t(s.sms) * uint64_t(std::max(per_sm, 1))));
+    // steps are counted per CTA in 32 bits
+    if ((a.n_tiles / grid + 1) * uint64_t(a.n_steps) >= (uint64_t(1) << 31)) return cudaErrorInvalidValue;
+    sig_pipe_kernel<K><<<unsigned(grid), s.threads, s.smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream_t st,
                           const DeviceSig *ds = nullptr, const SigProgram *G = nullptr, uint32_t n_obs = 0) {
-    if (s.mode == 5) {
+    if (s.mode == 5 || s.mode == 6) {
         if (!ds || !G || s.sched < 0 || size_t(s.sched) >= G->sched.size()) return cudaErrorInvalidValue;
         const SigSchedule &S = G->sched[s.sched];
         SigArgs a{};
@@ -1709,13 +2077,12 @@ static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream
         a.tables = ds->tables;
         a.item_rec = reinterpret_cast<const uint4 *>(ds->items[s.sched]);
         a.steps = reinterpret_cast<const uint4 *>(ds->steps[s.sched]);
-        a.unit_ent = ds->unit_ent;
+        a.ev_ent = ds->ev_ent;
         a.n_steps = uint32_t(S.steps.size());
         a.window_mask = S.window - 1u;
         a.n_obs = n_obs;
         a.queue_cap = s.qcap;
         a.smem_tables = s.smem_tables ? uint32_t(G->tables.size() / kTableWords) : 0u;
-        a.slot_words = G->slot_words;
         a.stage_items = sig_stage_items(*G, s.sched);
         a.key0 = a0.key0;
         a.key1 = a0.key1;
@@ -1727,6 +2094,20 @@ static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream
         a.obs = a0.obs;
         LaunchShape t = s;
         t.tiles = std::min<uint64_t>(s.tiles, a.n_tiles);
+        if (s.mode == 6) {
+            if (!S.lag || s.threads < 64) return cudaErrorInvalidValue;
+            a.lag = S.lag;
+            a.n_items = uint32_t(S.items.size() / 2);
+            a.n_det = G->n_det;
+            a.vec_out = (reinterpret_cast<uintptr_t>(a0.det) % 16 == 0 && a0.n_cols % 2 == 0) ? 1u : 0u;
+            a.status = a0.status;
+            switch (s.K) {
+            case 8: return launch_pipe<8>(a, t, st);
+            case 4: return launch_pipe<4>(a, t, st);
+            case 2: return launch_pipe<2>(a, t, st);
+            default: return launch_pipe<1>(a, t, st);
+            }
+        }
         switch (s.K) {
         case 8: return launch_sig<8>(a, t, st);
         case 4: return launch_sig<4>(a, t, st);
@@ -1777,6 +2158,8 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
                     cudaStream_t st, LaunchShape *best, const DeviceSig *ds) {
     const Program &P = c->prog;
     std::vector<LaunchShape> cands;
+    // every schedule of the signature program (barrier kernel for lag 0,
+    // pipelined kernel otherwise) x chunks per CTA x CTA size
     if (ds)
         for (int sched = 0; sched < int(c->sig.sched.size()); sched++)
             for (int K = 1; K <= 8; K *= 2) {
@@ -1859,8 +2242,14 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
 // leaves room for two CTAs per SM and still gives every SM two tiles.
 static LaunchShape choose_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const DeviceLimits &lim) {
     const int kcap = env_int("TMCS_TILE_K", 0);
-    // tuning/testing knob: schedule index (0 = largest ring window)
-    const int sched = std::min(std::max(env_int("TMCS_SIG_SCHED", 0), 0), int(c->sig.sched.size()) - 1);
+    // tuning/testing knobs: TMCS_SIG_SCHED = schedule index among the barrier
+    // schedules (0 = largest ring window), or among the pipelined ones with
+    // TMCS_KERNEL=6
+    int n_barrier = 0;
+    while (n_barrier < int(c->sig.sched.size()) && !c->sig.sched[n_barrier].lag) n_barrier++;
+    const bool pipe = env_int("TMCS_KERNEL", 0) == 6 && n_barrier < int(c->sig.sched.size());
+    const int lo = pipe ? n_barrier : 0, hi = pipe ? int(c->sig.sched.size()) - 1 : n_barrier - 1;
+    const int sched = std::min(std::max(lo + env_int("TMCS_SIG_SCHED", 0), lo), hi);
     int K = kcap > 0 ? std::min(kcap, 8) : 4;
     while (K > 1 && (K & (K - 1))) K--;
     while (K > 1 && !sig_fits(c, lim, K, sched)) K >>= 1;
@@ -1909,13 +2298,15 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
     if (!fault_mode && c->sig.ok && sig_fits(c, lim, 1) && kmode != 3 && kmode != 4) {
         if ((rc = device_sig(c, &ds))) return rc;
     }
-    if (kmode == 5 && !ds && !fault_mode)
-        return fail(TMCS_E_INVALID, "TMCS_KERNEL=5: no event-signature program for this circuit (" +
+    if ((kmode == 5 || kmode == 6) && !ds && !fault_mode)
+        return fail(TMCS_E_INVALID, "TMCS_KERNEL=5/6: no event-signature program for this circuit (" +
                                         (c->sig.ok ? std::string("ring does not fit") : c->sig.why) + ")");
+    if (kmode == 6 && ds && !c->sig.sched.back().lag)
+        return fail(TMCS_E_INVALID, "TMCS_KERNEL=6: the event-signature program has no pipelined schedule");
     LaunchShape s = ds ? choose_shape_sig(c, n_cols, lim) : choose_shape(P, n_cols, lim);
     if (ds && !sig_shape_fits(s, lim)) {  // no signature shape fits: frame kernels
-        if (kmode == 5 && !fault_mode)
-            return fail(TMCS_E_INVALID, "TMCS_KERNEL=5: the signature kernel's shared memory does not fit");
+        if ((kmode == 5 || kmode == 6) && !fault_mode)
+            return fail(TMCS_E_INVALID, "TMCS_KERNEL=5/6: the signature kernel's shared memory does not fit");
         ds = nullptr;
         s = choose_shape(P, n_cols, lim);
     }
@@ -1927,7 +2318,7 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
         DeviceProgram &mdp = c->dev[dp->device];
         if (mdp.tuned_mode == 3) s = make_shape(P, n_cols, mdp.tuned_K, mdp.tuned_threads);
         if (mdp.tuned_mode == 4) s = make_shape_w(P, n_cols, mdp.tuned_K, mdp.tuned_warps, mdp.tuned_group);
-        if (mdp.tuned_mode == 5 && ds)
+        if ((mdp.tuned_mode == 5 || mdp.tuned_mode == 6) && ds)
             s = make_shape_sig(c, n_cols, lim, mdp.tuned_K, mdp.tuned_threads, mdp.tuned_sched);
     }
     if (fault_mode) s = choose_shape(P, n_cols, lim);
@@ -2159,13 +2550,12 @@ static int sig_batch_sample(const tmcs_job *jobs, size_t n_jobs, cudaStream_t st
                 a.tables = ds->tables;
                 a.item_rec = reinterpret_cast<const uint4 *>(ds->items[0]);
                 a.steps = reinterpret_cast<const uint4 *>(ds->steps[0]);
-                a.unit_ent = ds->unit_ent;
+                a.ev_ent = ds->ev_ent;
                 a.n_steps = uint32_t(G.sched[0].steps.size());
                 a.window_mask = G.sched[0].window - 1u;
                 a.n_obs = uint32_t(J.c->n_obs);
                 a.smem_tables = tabs ? uint32_t(G.tables.size() / kTableWords) : 0u;
                 a.queue_cap = std::max(qmin, sig_queue_cap(G, 0, J.c->n_obs, C.K, C.budget, tabs));
-                a.slot_words = G.slot_words;
                 a.stage_items = sig_stage_items(G, 0);
                 a.key0 = uint32_t(J.seed);
                 a.key1 = uint32_t(J.seed >> 32);
@@ -2491,7 +2881,9 @@ int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *thread
     if (threads) *threads = dp ? dp->tuned_threads : 0;
     if (ring_window) {
         const int k = dp ? dp->tuned_sched : 0;
-        *ring_window = (dp && dp->tuned_mode == 5 && size_t(k) < c->sig.sched.size()) ? int(c->sig.sched[k].window) : 0;
+        *ring_window = (dp && (dp->tuned_mode == 5 || dp->tuned_mode == 6) && size_t(k) < c->sig.sched.size())
+                           ? int(c->sig.sched[k].window)
+                           : 0;
     }
     return TMCS_OK;
 }

@@ -87,6 +87,7 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
         G.why = "too many outputs";
         return TMCS_OK;
     }
+    G.n_det = uint32_t(D);
 
     // ---- noise descriptors and generator ids (every noise op with p > 0)
     std::vector<uint32_t> op_desc(n_ops, 0xFFFFFFFFu);
@@ -285,71 +286,70 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
     }
     edges.clear();
 
-    // ---- device layout: one fixed-size slot of S words per unit (S = 8 or
-    // 16, the smaller one that holds 99% of the units whole), so an event's
-    // data is one aligned load at unit * S: word 0 = entry count n; if
-    // n < S the entries follow in words 1..n, else word 1 is the offset of
-    // the n entries in the overflow area after all slots. Each entry is
-    // generator << 30 | observable flag << 29 | output index.
+    // ---- device layout: one 8-byte slot per (unit, Pauli index) in fault
+    // order (descriptor, unit, Pauli index - 1), holding the output list of
+    // that event: the symmetric difference of its generators' lists. Word 0
+    // = the first entry, kEvNone (no outputs) or kEvOverflow | offset (the
+    // list lies in the overflow area after the slots and word 1 is its
+    // length); word 1 = the second entry or kEvNone. An entry is observable
+    // flag << 29 | output index. Most events flip at most two outputs, so an
+    // event is one aligned 8-byte load.
     {
-        uint64_t units = 0;
-        for (const NoiseDesc &nd : G.noise) {
-            G.unit_base.push_back(uint32_t(units));
-            units += nd.n_units;
-        }
         if (D >= (1u << 29) || O >= (1u << 29)) {
             G.why = "too many outputs for the device layout";
             return TMCS_OK;
         }
-        uint64_t fit8 = 0, fit16 = 0, with = 0;
+        uint64_t slots = 0;
         for (const NoiseDesc &nd : G.noise) {
-            const uint32_t ng = sig_gens(nd.kind);
-            for (uint32_t u = 0; u < nd.n_units; u++) {
-                const uint32_t g0 = nd.tgt_off + u * ng;
-                const uint32_t cnt = G.gen_off[g0 + ng] - G.gen_off[g0];
-                if (!cnt) continue;
-                with++;
-                fit8 += cnt < 8;
-                fit16 += cnt < 16;
+            G.ev_base.push_back(uint32_t(slots));
+            slots += uint64_t(nd.n_units) * sig_paulis(nd.kind);
+            if (slots >= (uint64_t(1) << 31)) {
+                G.why = "too many noise events for the device layout";
+                return TMCS_OK;
             }
         }
-        const uint32_t S = (with == 0 || fit8 * 100 >= with * 99) ? 8u : 16u;
-        (void)fit16;
-        if (units * S >= 0xFFFFFFFFull) {
-            G.why = "too many noise units for the device layout";
-            return TMCS_OK;
-        }
-        G.slot_words = S;
-        G.unit_ent.assign(units * S, 0u);
+        G.ev_ent.assign(2 * slots, kEvNone);
+        std::vector<uint32_t> v;
         for (uint32_t di = 0; di < G.noise.size(); di++) {
             const NoiseDesc &nd = G.noise[di];
-            const uint32_t ng = sig_gens(nd.kind);
+            const uint32_t ng = sig_gens(nd.kind), KP = sig_paulis(nd.kind);
             for (uint32_t u = 0; u < nd.n_units; u++) {
                 const uint32_t g0 = nd.tgt_off + u * ng;
-                const uint32_t cnt = G.gen_off[g0 + ng] - G.gen_off[g0];
-                const size_t slot = size_t(G.unit_base[di] + u) * S;
-                G.unit_ent[slot] = cnt;
-                if (!cnt) continue;
-                std::vector<uint32_t> tagged;
-                for (uint32_t g = 0; g < ng; g++)
-                    for (uint32_t k = G.gen_off[g0 + g]; k < G.gen_off[g0 + g + 1]; k++) {
-                        const uint32_t v = G.gen_ent[k];
-                        const uint32_t idx = v & ~kSigObsFlag, obs = (v & kSigObsFlag) ? 1u : 0u;
-                        tagged.push_back((g << 30) | (obs << 29) | idx);
+                if (G.gen_off[g0] == G.gen_off[g0 + ng]) continue;  // every event of the unit flips nothing
+                for (uint32_t pk = 1; pk <= KP; pk++) {
+                    const uint32_t mask = sig_mask(nd.kind, pk);
+                    v.clear();
+                    for (uint32_t g = 0; g < ng; g++)
+                        if (mask >> g & 1u)
+                            for (uint32_t k = G.gen_off[g0 + g]; k < G.gen_off[g0 + g + 1]; k++) {
+                                const uint32_t e = G.gen_ent[k];
+                                v.push_back((e & kSigObsFlag) ? ((1u << 29) | (e & ~kSigObsFlag)) : e);
+                            }
+                    std::sort(v.begin(), v.end());
+                    size_t n = 0;  // XOR: keep entries that occur an odd number of times
+                    for (size_t i = 0; i < v.size();) {
+                        size_t j = i;
+                        while (j < v.size() && v[j] == v[i]) j++;
+                        if ((j - i) & 1) v[n++] = v[i];
+                        i = j;
                     }
-                if (cnt < S) {
-                    std::copy(tagged.begin(), tagged.end(), G.unit_ent.begin() + slot + 1);
-                } else {
-                    if (G.unit_ent.size() + cnt >= 0xFFFFFFFFull) {
-                        G.why = "too many signature entries";
-                        return TMCS_OK;
+                    const size_t slot = 2 * (size_t(G.ev_base[di]) + size_t(u) * KP + (pk - 1));
+                    if (n <= 2) {
+                        for (size_t i = 0; i < n; i++) G.ev_ent[slot + i] = v[i];
+                    } else {
+                        const size_t off = G.ev_ent.size();
+                        if (off + n >= size_t(kEvNone & ~kEvOverflow)) {
+                            G.why = "too many signature entries";
+                            return TMCS_OK;
+                        }
+                        G.ev_ent[slot] = kEvOverflow | uint32_t(off);
+                        G.ev_ent[slot + 1] = uint32_t(n);
+                        G.ev_ent.insert(G.ev_ent.end(), v.begin(), v.begin() + n);
                     }
-                    G.unit_ent[slot + 1] = uint32_t(G.unit_ent.size());
-                    G.unit_ent.insert(G.unit_ent.end(), tagged.begin(), tagged.end());
                 }
             }
         }
-        while (G.unit_ent.size() % 4) G.unit_ent.push_back(0u);
+        while (G.ev_ent.size() % 4) G.ev_ent.push_back(kEvNone);
     }
 
     // ---- items: segments whose events flip anything; detector span per item
@@ -442,12 +442,12 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
             const uint32_t units = std::min(kSegUnits, nd.n_units - sg * kSegUnits);
             S.item_rec.push_back(nd.op_index);
             S.item_rec.push_back(sg);
-            S.item_rec.push_back(G.unit_base[di] + sg * kSegUnits);
+            S.item_rec.push_back(G.ev_base[di] + sg * kSegUnits * sig_paulis(nd.kind));
             S.item_rec.push_back(nd.kind | (nd.table << 3) | ((units - 1) << 16) | (di << 22));
         }
         return true;
     };
-    for (uint64_t W = W0; W >= Wmin && G.sched.size() < kSigMaxSchedules; W >>= 1) {
+    for (uint64_t W = W0; W >= Wmin && G.sched.size() < 3; W >>= 1) {
         G.sched.emplace_back();
         if (!build_schedule(W, G.sched.back())) {
             G.why = "internal: schedule";
@@ -455,6 +455,45 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
             return TMCS_OK;
         }
         if (W == 1024) break;
+    }
+
+    // ---- pipelined schedules: steps of window Ws, up to L of them in
+    // flight. The ring must hold, for every run of L consecutive steps (the
+    // next tile's steps follow this tile's, D detectors further on), every
+    // detector from the first step's flush point up to the highest detector
+    // any of the L steps touches or flushes.
+    auto ring_for = [&](const SigSchedule &S, uint32_t L) {
+        const size_t ns = S.steps.size();
+        std::vector<uint64_t> hi(ns);
+        for (size_t t = 0; t < ns; t++) {
+            hi[t] = S.steps[t].flush_hi;
+            for (uint32_t i = S.steps[t].item_begin; i < S.steps[t].item_end; i++)
+                if (dmin[i] != 0xFFFFFFFFu) hi[t] = std::max<uint64_t>(hi[t], uint64_t(dmax[i]) + 1);
+        }
+        uint64_t span = 0;
+        for (size_t v = 0; v < 2 * ns; v++) {
+            const size_t v0 = v + 1 >= L ? v + 1 - L : 0;
+            uint64_t h = 0;
+            for (size_t u = v0; u <= v; u++) h = std::max<uint64_t>(h, hi[u % ns] + (u / ns) * D);
+            span = std::max<uint64_t>(span, h - (S.steps[v0 % ns].flush_lo + (v0 / ns) * D));
+        }
+        uint64_t R = 256;
+        while (R < span) R <<= 1;
+        return R;
+    };
+    uint64_t Wp = 256;
+    while (Wp < need) Wp <<= 1;
+    for (int w = 0; w < 2; w++, Wp <<= 1) {
+        SigSchedule base;
+        if (!build_schedule(Wp, base)) continue;
+        for (uint32_t L = 2; L <= uint32_t(kSigMaxLag) && G.sched.size() < size_t(kSigMaxSchedules); L++) {
+            if (L > base.steps.size() + 1) break;  // the two observable buffers need L <= steps + 1
+            const uint64_t R = ring_for(base, L);
+            if (R > 16384) break;
+            G.sched.push_back(base);
+            G.sched.back().window = uint32_t(R);
+            G.sched.back().lag = L;
+        }
     }
     G.ok = true;
     G.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();

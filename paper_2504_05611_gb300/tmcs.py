@@ -35,7 +35,7 @@ assert OP_DTYPE.itemsize == 32
 STATS_FIELDS = ("n_layers", "n_slots", "n_xor", "n_zero", "n_copy", "n_noise_ops", "n_noise_units",
                 "n_noise_segments", "n_parity_terms", "live_components", "pruned_updates",
                 "sig_ok", "sig_window", "sig_steps", "sig_items", "sig_generators", "sig_entries",
-                "sig_build_us", "sig_max_step_items", "sig_schedules", "sig_min_window")
+                "sig_build_us", "sig_max_step_items", "sig_schedules", "sig_min_window", "sig_pipe_schedules")
 
 
 class TmcsError(RuntimeError):
@@ -325,7 +325,7 @@ def tmcs_sample_measurements(handle: int, first_chunk: int, shots: int, seed: in
                                           _dev_ptr(meas), _stream_ptr(stream)))
 
 
-KERNEL_NAMES = {3: "frame_kernel", 4: "frame_kernel_w", 5: "sig_kernel"}
+KERNEL_NAMES = {3: "frame_kernel", 4: "frame_kernel_w", 5: "sig_kernel", 6: "sig_pipe_kernel"}
 
 
 def tmcs_launch_shape(handle: int) -> Dict[str, object]:

@@ -237,6 +237,79 @@ def test_signature_schedules_are_bit_exact(monkeypatch, sched, tile_k, threads):
     assert_parity(circ, 64 * 19 + 45, seed=29, first_chunk=3)
 
 
+@pytest.mark.parametrize("sched", range(6))
+@pytest.mark.parametrize("tile_k,threads", [(4, 1024), (8, 512), (1, 256), (2, 128)])
+def test_pipelined_kernel_is_bit_exact(monkeypatch, sched, tile_k, threads):
+    """The pipelined event-signature kernel under each of its schedules (step
+    window x steps in flight) and launch shapes reproduces the oracle: ragged
+    tail, nonzero first chunk, many flush steps per tile."""
+    monkeypatch.setenv("TMCS_KERNEL", "6")
+    monkeypatch.setenv("TMCS_SIG_SCHED", str(sched))
+    monkeypatch.setenv("TMCS_TILE_K", str(tile_k))
+    monkeypatch.setenv("TMCS_THREADS", str(threads))
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc11"), 11, 11, C.NoiseModel(0.003, 0.02))
+    h = tmcs.tmcs_circuit_build(circ)
+    st = tmcs.tmcs_circuit_stats(h)
+    tmcs.tmcs_circuit_free(h)
+    assert st["sig_pipe_schedules"] == 6
+    assert_parity(circ, 64 * 19 + 45, seed=29, first_chunk=3)
+
+
+@pytest.mark.parametrize("sched", range(3))
+@pytest.mark.parametrize("tile_k,threads,shots", [(1, 1024, 64 * 1000 + 37), (2, 512, 64 * 1000 + 37),
+                                                  (2, 512, 64 * 1000), (4, 256, 64 * 2002 - 5)])
+def test_pipelined_kernel_many_tiles_per_cta(monkeypatch, sched, tile_k, threads, shots):
+    """Several tiles per CTA: the ring offset and the observable buffer of
+    each tile alternate while steps of two tiles are in flight. Odd and even
+    column counts take the scalar and the 16-byte output paths."""
+    monkeypatch.setenv("TMCS_KERNEL", "6")
+    monkeypatch.setenv("TMCS_SIG_SCHED", str(sched))
+    monkeypatch.setenv("TMCS_TILE_K", str(tile_k))
+    monkeypatch.setenv("TMCS_THREADS", str(threads))
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc5"), 6, 6, C.NoiseModel(0.01, 0.05))
+    h = tmcs.tmcs_circuit_build(circ)
+    st = tmcs.tmcs_circuit_stats(h)
+    tmcs.tmcs_circuit_free(h)
+    assert st["sig_pipe_schedules"] == 3
+    gd, go = assert_parity(circ, shots, seed=41, first_chunk=11)
+    assert gd.any() and go.any()
+
+
+@pytest.mark.parametrize("queue", [1, 64])
+def test_pipelined_kernel_small_queue(monkeypatch, queue):
+    """The smallest queue slices (64 events per walker warp) under heavy
+    noise: the queue is applied almost every iteration."""
+    monkeypatch.setenv("TMCS_KERNEL", "6")
+    monkeypatch.setenv("TMCS_SIG_QUEUE", str(queue))
+    circ = C.teleport_circuit(C.code_by_name("bb18"), 2, 2, C.NoiseModel(0.03, 0.1))
+    assert_parity(circ, 64 * 23 + 5, seed=31)
+
+
+def test_pipelined_kernel_observables_only(monkeypatch):
+    """No detectors: the pipelined kernel writes every observable word."""
+    monkeypatch.setenv("TMCS_KERNEL", "6")
+    circ = C.Circuit()
+    circ.append("R", [0, 1, 2])
+    circ.append("X_ERROR", [0, 1, 2], p=0.2)
+    circ.append("CX", [0, 1])
+    circ.append("DEPOLARIZE2", [0, 1], p=0.1)
+    circ.append("M", [0, 1, 2])
+    circ.append("OBSERVABLE", [0, 2], arg=0)
+    circ.append("OBSERVABLE", [1], arg=1)
+    _, go = assert_parity(circ, 64 * 300 + 3, seed=3)
+    assert go.any()
+
+
+def test_pipelined_kernel_long_detector_span(monkeypatch):
+    """A fault flipping detectors 1501 apart: the pipelined schedules size
+    their ring for it."""
+    from test_abi import _long_span_circuit
+    monkeypatch.setenv("TMCS_KERNEL", "6")
+    circ = _long_span_circuit(1500)
+    gd, _ = assert_parity(circ, 64 * 9 + 3, seed=8)
+    assert gd.any()
+
+
 @pytest.mark.parametrize("queue", [1, 64])
 def test_signature_kernel_queue_overflow(monkeypatch, queue):
     """Events that find the shared event queue full are applied directly:
