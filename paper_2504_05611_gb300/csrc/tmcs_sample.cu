@@ -697,12 +697,20 @@ __device__ __forceinline__ void sig_warp_apply(const SigArgs &A, const uint64_t 
     __syncwarp();
 }
 
+// events a lane applies at once when a warp's queue slice fills during the
+// walk (the walk's state stays live across it)
+#ifndef TMCS_WALK_APPLY
+#define TMCS_WALK_APPLY 2
+#endif
+constexpr int kWalkApply = TMCS_WALK_APPLY;
+
 // Walk phase of one step for one warp: every lane holds one (segment, chunk)
 // stream and runs one Philox call (two draws) of it per iteration; a lane
 // whose stream ends takes the next from the step's counter, so the warp stays
 // converged on the generator. Events go to the warp's own queue slice at
-// offsets from a ballot (no atomics); events that find the slice full are
-// applied at once by their lanes. Returns the number of queued events.
+// offsets from a ballot (no atomics); when the slice would overflow, the
+// warp first applies it together and starts it again. Returns the number of
+// queued events.
 // tabs: the gap tables, in shared memory when SMT.
 template <bool SMT>
 __device__ __forceinline__ uint32_t sig_walk(const SigArgs &A, const uint4 st, uint32_t n, uint32_t nvalid,
@@ -768,13 +776,14 @@ __device__ __forceinline__ uint32_t sig_walk(const SigArgs &A, const uint4 st, u
             const uint32_t m = __ballot_sync(0xFFFFFFFFu, ev);
             if (m) {
                 const uint32_t c = uint32_t(__popc(m));
-                if (qn + c <= wcap) {
-                    if (ev) wq[qn + uint32_t(__popc(m & lt))] = q;
-                    qn += c;
-                } else if (ev) {
-                    const uint64_t q1[1] = {q};
-                    sig_apply_events<1>(A, q1, 1, ring, oacc, K);
+                if (qn + c > wcap) {
+                    // slice full: the warp applies it together (slot loads
+                    // overlapped) and starts it again
+                    sig_warp_apply<kWalkApply>(A, wq, qn, ring, oacc, K);
+                    qn = 0;
                 }
+                if (ev) wq[qn + uint32_t(__popc(m & lt))] = q;
+                qn += c;
             }
         }
     }
