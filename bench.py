@@ -292,8 +292,11 @@ def main():
                 sampled[b].record(stream)
                 copy_stream.wait_event(sampled[b])
                 with torch.cuda.stream(copy_stream):
-                    hd[b][:, :n].copy_(dbuf[b][:, :n], non_blocking=True)
-                    ho[b][:, :n].copy_(obuf[b][:, :n], non_blocking=True)
+                    # the call writes rows of n words (row stride n), so a
+                    # short last slice is the first n_det * n words
+                    nd, no = info["n_det"] * n, max(info["n_obs"], 1) * n
+                    hd[b].view(-1)[:nd].copy_(dbuf[b].view(-1)[:nd], non_blocking=True)
+                    ho[b].view(-1)[:no].copy_(obuf[b].view(-1)[:no], non_blocking=True)
                 done[b].record(copy_stream)
                 d2h += (info["n_det"] + info["n_obs"]) * n * 8
             return d2h
@@ -308,9 +311,21 @@ def main():
         torch.cuda.synchronize()
         barrier()
         e2e_s = max_over_ranks((time.perf_counter() - w0) / args.e2e_steps, dev)
+        # the device-to-host copy rate alone (one full slice, best of 3), the
+        # ceiling of this end-to-end path
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        link_ms = []
+        for _ in range(3):
+            c0.record(copy_stream)
+            with torch.cuda.stream(copy_stream):
+                hd[0].copy_(dbuf[0], non_blocking=True)
+            c1.record(copy_stream)
+            c1.synchronize()
+            link_ms.append(c0.elapsed_time(c1))
         e2e = {"value": total_shots * info["n_det"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": d2h_bytes, "shots_per_s": total_shots / e2e_s,
-               "launches_per_step": nslices}
+               "launches_per_step": nslices,
+               "d2h_copy_gbs": hd[0].numel() * 8 / (min(link_ms) * 1e-3) / 1e9}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
