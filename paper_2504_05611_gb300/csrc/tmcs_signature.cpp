@@ -377,6 +377,29 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
         }
     }
     const size_t n_items = dmin.size();
+    // Items in order of their highest detector: the items that fit a step's
+    // window above its flush point are then always a prefix of the items
+    // left, so the greedy cut below takes every item that fits (events XOR
+    // into the ring, so the order of items does not change the output).
+    {
+        std::vector<uint32_t> ord(n_items);
+        for (size_t k = 0; k < n_items; k++) ord[k] = uint32_t(k);
+        std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) {
+            const uint64_t ax = dmin[x] == 0xFFFFFFFFu ? 0 : uint64_t(dmax[x]) + 1;
+            const uint64_t ay = dmin[y] == 0xFFFFFFFFu ? 0 : uint64_t(dmax[y]) + 1;
+            return ax < ay;
+        });
+        std::vector<uint32_t> it2(2 * n_items), dmin2(n_items), dmax2(n_items);
+        for (size_t k = 0; k < n_items; k++) {
+            it2[2 * k] = items[2 * ord[k]];
+            it2[2 * k + 1] = items[2 * ord[k] + 1];
+            dmin2[k] = dmin[ord[k]];
+            dmax2[k] = dmax[ord[k]];
+        }
+        items.swap(it2);
+        dmin.swap(dmin2);
+        dmax.swap(dmax2);
+    }
     std::vector<uint64_t> sufmin(n_items + 1, D);
     for (size_t i = n_items; i-- > 0;) sufmin[i] = std::min<uint64_t>(sufmin[i + 1], dmin[i]);
     if (G.noise.size() > 1024 || G.tables.size() / kTableWords > 8192) {
