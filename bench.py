@@ -405,6 +405,9 @@ def batch_bench(args):
     stream = torch.cuda.Stream(device=dev)
     jl = [(s.handle, w.shots, w.seed, d, o if s.info["n_obs"] else None)
           for s, w, (d, o) in zip(samplers, jobs, outs)]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    n_large = sum(1 for s, w in zip(samplers, jobs)
+                  if (w.shots + 63) // 64 >= 16 * sms and tmcs.tmcs_circuit_stats(s.handle)["sig_ok"])
 
     def timed(fn, steps):
         t0 = torch.cuda.Event(enable_timing=True)
@@ -456,7 +459,10 @@ def batch_bench(args):
                           "64 SC d=3..9 NL/teleport jobs, 1e4..1e5 shots (seed 3)"},
         "batched_ms": ms_batch, "graph_replay_ms": ms_graph, "solo_calls_ms": ms_solo,
         "batched_vs_solo": ms_solo / min(ms_batch, ms_graph), "clocks": clk,
-        "gpu_launches": 1,
+        # jobs of at least 16 chunks per SM run as their own tuned launch;
+        # the others share one persistent launch per size class (1 or 2)
+        "gpu_launches": n_large + (1 if n_large < len(jobs) else 0),
+        "gpu_launches_note": f"{n_large} GPU-filling jobs as single launches + the shared launches (1 per size class)",
     }
     print(json.dumps(line), flush=True)
     for s in cache.values():

@@ -274,8 +274,12 @@ typedef struct {
 } tmcs_job;
 
 /*
- * Sample many circuits of uneven size in one persistent launch on `stream`:
- * resident CTAs pull (job, tile) work items from a device queue. Each job's
+ * Sample many circuits of uneven size on `stream`: the jobs share persistent
+ * launches whose resident CTAs pull (job, tile) work items from a device
+ * queue; a job that fills the GPU by itself (at least 16 chunks per SM) with
+ * an event-signature program instead runs as its own tmcs_sample call, with
+ * the launch shape tuned for its circuit (that call may tune synchronously,
+ * as tmcs_sample does, unless the stream is being captured). Each job's
  * output equals its own tmcs_sample call bit for bit.
  * Errors: as tmcs_sample; TMCS_E_INVALID if any job is invalid.
  */

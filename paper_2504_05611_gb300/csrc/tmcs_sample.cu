@@ -2594,8 +2594,36 @@ static int sig_batch_sample(const tmcs_job *jobs, size_t n_jobs, cudaStream_t st
     return TMCS_OK;
 }
 
+static int batch_sample_shared(const tmcs_job *jobs, size_t n_jobs, void *stream);
+
+// Jobs that fill the GPU on their own (at least 16 chunks per SM) and have
+// an event-signature program run as single calls, with the launch shape
+// tuned for their circuit (tuned on their first call, outside graph
+// capture); the others share the persistent batch launches. Same bits
+// either way.
 static int batch_sample(const tmcs_job *jobs, size_t n_jobs, void *stream) {
     if (n_jobs && !jobs) return fail(TMCS_E_INVALID, "jobs is NULL");
+    if (n_jobs == 0) return TMCS_OK;
+    DeviceLimits lim;
+    int rc = device_limits(&lim);
+    if (rc) return rc;
+    std::vector<tmcs_job> rest;
+    rest.reserve(n_jobs);
+    for (size_t j = 0; j < n_jobs; j++) {
+        const tmcs_job &J = jobs[j];
+        const bool large = J.c && J.c->sig.ok && J.shots > 0 && (J.shots + 63) / 64 >= uint64_t(16) * lim.sms &&
+                           env_int("TMCS_KERNEL", 0) != 3 && env_int("TMCS_KERNEL", 0) != 4;
+        if (!large) {
+            rest.push_back(J);
+            continue;
+        }
+        if ((rc = sample_range(J.c, 0, J.shots, J.seed, J.det, J.obs, stream)))
+            return fail(rc, "job " + std::to_string(j) + ": " + tmcs_last_error());
+    }
+    return batch_sample_shared(rest.data(), rest.size(), stream);
+}
+
+static int batch_sample_shared(const tmcs_job *jobs, size_t n_jobs, void *stream) {
     if (n_jobs == 0) return TMCS_OK;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -156,6 +156,39 @@ def test_batch_equals_solo(kernel, monkeypatch):
         s.close()
 
 
+@pytest.mark.parametrize("capture", [False, True])
+def test_batch_with_gpu_filling_job(capture):
+    """A job of at least 16 chunks per SM runs as its own tuned call inside
+    tmcs_batch_sample; every job still equals its solo call, also when the
+    batch is captured in a CUDA graph and replayed."""
+    circs = [C.nonlocal_cnot_circuit(C.code_by_name("sc5"), 3, 3, C.NoiseModel(0.003, 0.03)),
+             C.teleport_circuit(C.code_by_name("bb18"), 1, 1, C.NoiseModel(0.003, 0.03)),
+             C.nonlocal_cnot_circuit(C.code_by_name("sc3"), 2, 2, C.NoiseModel(0.01, 0.1))]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    shots = [64 * 16 * sms + 5, 64 * 20 + 7, 999]
+    samplers = [tmcs.Sampler(c) for c in circs]
+    outs = [s.alloc(n) for s, n in zip(samplers, shots)]
+    jobs = [(s.handle, n, 60 + i, d, o) for i, (s, n, (d, o)) in enumerate(zip(samplers, shots, outs))]
+    tmcs.tmcs_batch_sample(jobs)
+    torch.cuda.synchronize()
+    if capture:
+        for d, o in outs:
+            d.zero_()
+            o.zero_()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            tmcs.tmcs_batch_sample(jobs)
+        g.replay()
+        torch.cuda.synchronize()
+    for i, (circ, n) in enumerate(zip(circs, shots)):
+        d, o = outs[i]
+        sd, so = gpu_sample(circ, n, 60 + i)
+        assert np.array_equal(d.cpu().numpy().view(np.uint64), sd)
+        assert np.array_equal(o[: circ.n_obs].cpu().numpy().view(np.uint64), so)
+    for s in samplers:
+        s.close()
+
+
 def test_headline_full_size_sampled_chunks():
     """Distance-29 SC non-local CNOT, 29/29 rounds, 1e7 shots: sampled chunks
     (first, middle, last with its ragged tail) against the oracle."""
