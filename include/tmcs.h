@@ -164,6 +164,9 @@ int tmcs_reference_sample(const tmcs_circuit *c, uint8_t *meas_bits);
  * kernel, 5 event-signature kernel, 6 pipelined event-signature kernel),
  * TMCS_TILE_K, TMCS_THREADS, TMCS_SIG_SCHED (signature schedule index),
  * TMCS_SIG_WINDOW (read by tmcs_circuit_build), TMCS_AUTOTUNE=0.
+ * Testing: TMCS_TEST_STALL_FLUSH=1 makes the pipelined kernel's flusher wait
+ * for a stream count that never arrives, so its bounded wait (2 s) expires,
+ * every warp leaves and tmcs_check_device reports TMCS_E_TIMEOUT.
  * Errors: TMCS_E_INVALID (NULL circuit/buffer, shots == 0), TMCS_E_CUDA,
  * TMCS_E_OOM (program upload).
  */

@@ -604,6 +604,8 @@ struct SigArgs {
     uint32_t n_det;           // detectors (tile T's ring offset is T * n_det)
     uint32_t vec_out;         // det is 16-byte aligned and n_cols even: 16-byte output stores
     uint32_t *status;         // device status word (bit 0: a bounded wait expired)
+    uint32_t stall_flush;     // testing: the flusher waits for one stream more than step 0 has
+                              // (a count nothing reaches), so its bounded wait expires
 };
 
 // Draws of one (segment, chunk) stream from its start; sink(pos, pauli) per
@@ -1132,7 +1134,7 @@ __device__ __forceinline__ void pipe_flush(const SigArgs &A, const PipeSmem &S, 
         const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(T) * gridDim.x;
         const uint32_t nv = T == nt - 1 ? nv_last : uint32_t(K);
         const uint4 st = __ldg(A.steps + s);
-        const uint32_t need = (st.y - st.x) * nv;
+        const uint32_t need = (st.y - st.x) * nv + ((seq == 0 && A.stall_flush) ? 1u : 0u);
         const uint32_t slot = seq % lag;
         uint32_t ok = 1;
         if (lane == 0 && ld_shared_volatile(&C.done[slot]) != need) {
@@ -2110,6 +2112,9 @@ static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream
             a.n_det = G->n_det;
             a.vec_out = (reinterpret_cast<uintptr_t>(a0.det) % 16 == 0 && a0.n_cols % 2 == 0) ? 1u : 0u;
             a.status = a0.status;
+            // testing knob: make the flusher's bounded wait run out (the
+            // kernel then reports TMCS_E_TIMEOUT through the status word)
+            a.stall_flush = env_int("TMCS_TEST_STALL_FLUSH", 0) > 0 ? 1u : 0u;
             switch (s.K) {
             case 8: return launch_pipe<8>(a, t, st);
             case 4: return launch_pipe<4>(a, t, st);
