@@ -85,6 +85,27 @@ def test_rejects_nondeterministic_detector(tmcs):
     tmcs.tmcs_circuit_free(h)
 
 
+def test_sample_rejects_bad_arguments_before_device_work(tmcs):
+    """Argument errors come back before any device call, so these run
+    without a GPU: misaligned or missing output buffers (TMCS_E_BUFFER = 6,
+    TMCS_E_INVALID = 1), zero shots, a chunk range past 2^32, a NULL circuit
+    or job list."""
+    h = tmcs.tmcs_circuit_build(C.WORKLOADS["nl_sc3"].circuit())
+    L = tmcs.lib()
+    try:
+        assert L.tmcs_sample(h, 64, 1, 0x1001, 0x2000, None) == 6
+        assert "aligned" in tmcs.tmcs_last_error()
+        assert L.tmcs_sample(h, 64, 1, 0x1000, 0x2004, None) == 6
+        assert L.tmcs_sample(h, 0, 1, 0x1000, 0x2000, None) == 1
+        assert L.tmcs_sample(h, 64, 1, None, 0x2000, None) == 1
+        assert L.tmcs_sample(h, 64, 1, 0x1000, None, None) == 1
+        assert L.tmcs_sample_range(h, (1 << 32) - 1, 128, 1, 0x1000, 0x2000, None) == 1
+        assert L.tmcs_sample(None, 64, 1, 0x1000, 0x2000, None) == 1
+        assert L.tmcs_batch_sample(None, 3, None) == 1
+    finally:
+        tmcs.tmcs_circuit_free(h)
+
+
 def test_rejects_invalid_ops(tmcs):
     arr = np.zeros(1, dtype=tmcs.OP_DTYPE)
     arr["code"] = 99
