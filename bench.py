@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -586,12 +587,39 @@ def peaks_bench(args):
                       "sms": best["sms"], "sm_clock_mhz_attribute": best["sm_clock_mhz"], "runs": 3}), flush=True)
 
 
+def _strip_comments(src: str) -> str:
+    """C/C++/CUDA source without // and /* */ comments (string and character
+    literals kept) and without whitespace."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return re.sub(r"\s+", "", "".join(out))
+
+
 def _kernel_sha():
+    """Hash of the sampler's device and host sources, comments and
+    whitespace excluded: a committed traffic figure stays attached to the
+    kernel build it was measured on."""
     import hashlib
     h = hashlib.sha256()
     for f in ("tmcs_sample.cu", "tmcs_internal.h", "tmcs_host.cpp", "tmcs_signature.cpp"):
-        with open(os.path.join(ROOT, "paper_2504_05611_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2504_05611_gb300", "csrc", f)) as fh:
+            h.update(_strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -170,9 +170,9 @@ struct SigSchedule {
     uint32_t window = 0;
     uint32_t lag = 0;
     std::vector<uint32_t> items;     // (descriptor, segment) pairs, 2 words per item
-    // Device item records, 4 words per item: op index, segment, global index
-    // of the segment's first unit, kind | table << 3 | (units - 1) << 16 |
-    // descriptor << 22 (descriptor < 1024, table < 8192).
+    // Device item records, 4 words per item: op index, segment, event slot
+    // of the segment's first unit and Pauli index 1, kind | table << 3 |
+    // (units - 1) << 16 | descriptor << 22 (descriptor < 1024, table < 8192).
     std::vector<uint32_t> item_rec;
     std::vector<SigStep> steps;
 };

@@ -582,9 +582,9 @@ __global__ void __launch_bounds__(512) frame_kernel(const KernelArgs P) {
 // accumulate in a small array written once per tile.
 
 struct SigArgs {
-    const NoiseDesc *noise;   // tgt_off = first global unit index of the descriptor
+    const NoiseDesc *noise;   // tgt_off = the descriptor's first event slot
     const uint32_t *tables;
-    const uint4 *item_rec;    // per item: op index, segment, first unit, kind | table << 3 | (units-1) << 16 | desc << 22
+    const uint4 *item_rec;    // per item: op index, segment, first event slot, kind | table << 3 | (units-1) << 16 | desc << 22
     const uint4 *steps;       // SigStep: item_begin, item_end, flush_lo, flush_hi
     const uint32_t *ev_ent;   // two words per event slot (see SigProgram), then the overflow lists
     uint32_t n_steps;
@@ -918,7 +918,9 @@ __global__ void __launch_bounds__(1024) sig_kernel(const SigArgs A) {
 // observables in buffer T mod 2. Every wait is bounded (kWaitNs); on expiry
 // the kernel sets the status bit and every warp leaves.
 
-// events a walker lane applies at once (their slot loads overlap)
+// events a walker lane applies per pass (build-time tuning value): the
+// walk's state stays live across the apply, and batches of 2 or 4 measured
+// slower than 1 on every workload
 #ifndef TMCS_PIPE_APPLY
 #define TMCS_PIPE_APPLY 1
 #endif
@@ -998,8 +1000,9 @@ __device__ __forceinline__ void pipe_walk(const SigArgs &A, const PipeSmem &S, P
     uint32_t qn = 0, unpub = 0;  // warp-uniform
     bool have = false, pend = false, exhausted = false, waiting = false;
     // the lane's stream: Philox counter words (call, chunk, op, seg), first
-    // unit, event tag (chunk k, kind, ring offset, observable buffer), gap
-    // table (word offset), position and length in trials
+    // event slot of the segment, event tag (chunk k, kind, ring offset,
+    // observable buffer), gap table (word offset), position and length in
+    // trials
     uint32_t call = 0, seg = 0, op = 0, chunk = 0, ubase = 0, tag = 0, toff = 0, t1 = 0, t2 = 0;
     int pos = -1, n_trials = 0;
     float inv = 0.f;
