@@ -18,8 +18,10 @@
 // The pass for a group starts at the last op holding one of its records and
 // stops as soon as no mask and no pending record sensitivity is left.
 #include <algorithm>
+#include <cstdint>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <system_error>
 #include <thread>
@@ -76,6 +78,114 @@ struct Pass {
 };
 
 }  // namespace
+
+// Checks every invariant the signature kernels rely on, after each build:
+// the memory safety of each index they form from the program (event slots
+// and overflow lists, observable and detector ids, gap tables, item
+// records) and the schedules' rules (steps partition the items and the
+// detectors; in a barrier schedule every item's detectors lie in its step's
+// window above the flush point; in a pipelined one every run of `lag`
+// consecutive steps, of this tile and the next, fits the ring). Returns an
+// empty string or the first violation.
+static std::string validate_signature_program(const SigProgram &G, uint64_t D, uint64_t O) {
+    const size_t n_tables = G.tables.size() / kTableWords;
+    if (G.ev_base.size() != G.noise.size()) return "event bases";
+    uint64_t slots = 0;
+    for (size_t di = 0; di < G.noise.size(); di++) {
+        const NoiseDesc &nd = G.noise[di];
+        if (nd.kind > N_PC1 || nd.table >= n_tables) return "noise descriptor";
+        if (nd.n_seg != (nd.n_units + kSegUnits - 1) / kSegUnits) return "segment count";
+        if (G.ev_base[di] != slots) return "event slots out of order";
+        slots += uint64_t(nd.n_units) * sig_paulis(nd.kind);
+    }
+    if (G.ev_ent.size() < 2 * slots) return "event table too short";
+    auto entry_ok = [&](uint32_t e) {
+        const uint32_t idx = e & 0x1FFFFFFFu;
+        return (e >> 30) == 0u && ((e & (1u << 29)) ? idx < O : idx < D);
+    };
+    for (size_t k = 0; k < slots; k++) {
+        const uint32_t w0 = G.ev_ent[2 * k], w1 = G.ev_ent[2 * k + 1];
+        if (w0 == kEvNone) {
+            if (w1 != kEvNone) return "event slot";
+        } else if (w0 & kEvOverflow) {
+            const uint64_t off = w0 & ~kEvOverflow;
+            if (off < 2 * slots || w1 < 3 || off + w1 > G.ev_ent.size()) return "overflow list";
+            for (uint32_t x = 0; x < w1; x++)
+                if (!entry_ok(G.ev_ent[off + x])) return "overflow entry";
+        } else if (!entry_ok(w0) || (w1 != kEvNone && !entry_ok(w1))) {
+            return "event entry";
+        }
+    }
+    // detector span [lo, hi) of every segment (first segment of descriptor
+    // di at seg0[di]): the union of its single-generator events' lists, i.e.
+    // of all its events' entries
+    std::vector<uint64_t> seg0(G.noise.size() + 1, 0);
+    for (size_t di = 0; di < G.noise.size(); di++) seg0[di + 1] = seg0[di] + G.noise[di].n_seg;
+    std::vector<uint64_t> seg_lo(seg0.back(), UINT64_MAX), seg_hi(seg0.back(), 0);
+    for (size_t di = 0; di < G.noise.size(); di++) {
+        const NoiseDesc &nd = G.noise[di];
+        const uint32_t KP = sig_paulis(nd.kind);
+        for (uint64_t k = G.ev_base[di]; k < G.ev_base[di] + uint64_t(nd.n_units) * KP; k++) {
+            const uint64_t sg = seg0[di] + (k - G.ev_base[di]) / KP / kSegUnits;
+            auto see = [&](uint32_t e) {
+                if (e & (1u << 29)) return;
+                seg_lo[sg] = std::min<uint64_t>(seg_lo[sg], e & 0x1FFFFFFFu);
+                seg_hi[sg] = std::max<uint64_t>(seg_hi[sg], uint64_t(e & 0x1FFFFFFFu) + 1);
+            };
+            const uint32_t w0 = G.ev_ent[2 * k], w1 = G.ev_ent[2 * k + 1];
+            if (w0 == kEvNone) continue;
+            if (w0 & kEvOverflow) {
+                for (uint32_t x = 0; x < w1; x++) see(G.ev_ent[(w0 & ~kEvOverflow) + x]);
+            } else {
+                see(w0);
+                if (w1 != kEvNone) see(w1);
+            }
+        }
+    }
+    for (const SigSchedule &S : G.sched) {
+        const size_t n_items = S.items.size() / 2;
+        const uint32_t W = S.window;
+        if (W < 256 || (W & (W - 1)) || S.lag > uint32_t(kSigMaxLag) || (S.lag && W > 16384)) return "schedule shape";
+        if (S.item_rec.size() != 4 * n_items || S.steps.empty()) return "schedule size";
+        std::vector<uint64_t> lo(n_items), hi(n_items);
+        for (size_t k = 0; k < n_items; k++) {
+            const uint32_t di = S.items[2 * k], sg = S.items[2 * k + 1];
+            if (di >= G.noise.size() || sg >= G.noise[di].n_seg) return "item";
+            const NoiseDesc &nd = G.noise[di];
+            const uint32_t units = std::min(kSegUnits, nd.n_units - sg * kSegUnits);
+            const uint32_t *r = &S.item_rec[4 * k];
+            if (r[0] != nd.op_index || r[1] != sg || r[2] != G.ev_base[di] + sg * kSegUnits * sig_paulis(nd.kind) ||
+                r[3] != (nd.kind | (nd.table << 3) | ((units - 1) << 16) | (di << 22)))
+                return "item record";
+            lo[k] = seg_lo[seg0[di] + sg];
+            hi[k] = seg_hi[seg0[di] + sg];
+        }
+        const size_t ns = S.steps.size();
+        std::vector<uint64_t> shi(ns);
+        for (size_t t = 0; t < ns; t++) {
+            const SigStep &st = S.steps[t];
+            const uint32_t b0 = t ? S.steps[t - 1].item_end : 0u, f0 = t ? S.steps[t - 1].flush_hi : 0u;
+            if (st.item_begin != b0 || st.item_end < st.item_begin || st.flush_lo != f0 || st.flush_hi < st.flush_lo)
+                return "steps not contiguous";
+            shi[t] = st.flush_hi;
+            for (uint32_t k = st.item_begin; k < st.item_end; k++) {
+                if (lo[k] == UINT64_MAX) continue;
+                if (lo[k] < st.flush_lo) return "item below its step's flush point";
+                if (!S.lag && hi[k] > uint64_t(st.flush_lo) + W) return "item beyond its step's window";
+                shi[t] = std::max(shi[t], hi[k]);
+            }
+        }
+        if (S.steps.back().item_end != n_items || S.steps.back().flush_hi != D) return "steps do not cover";
+        if (S.lag)
+            for (size_t v = 0; v < 2 * ns; v++) {
+                const size_t v0 = v + 1 >= S.lag ? v + 1 - S.lag : 0;
+                uint64_t h = 0;
+                for (size_t u = v0; u <= v; u++) h = std::max<uint64_t>(h, shi[u % ns] + (u / ns) * D);
+                if (h - (S.steps[v0 % ns].flush_lo + (v0 / ns) * D) > W) return "ring too small for its lag";
+            }
+    }
+    return std::string();
+}
 
 int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
     const auto t_start = std::chrono::steady_clock::now();
@@ -517,6 +627,28 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
             G.sched.back().window = uint32_t(R);
             G.sched.back().lag = L;
         }
+    }
+    // testing knob: plant one mistake before validation (the host-side
+    // validator must then refuse the program; sampling uses the frame kernels)
+    if (const char *v = std::getenv("TMCS_TEST_CORRUPT_SIG")) {
+        const std::string what(v);
+        if (what == "observable") {
+            for (size_t k = 0; k + 1 < G.ev_ent.size(); k += 2)
+                if (G.ev_ent[k] != kEvNone && !(G.ev_ent[k] & kEvOverflow)) {
+                    G.ev_ent[k] = (1u << 29) | uint32_t(O);  // one past the last observable
+                    break;
+                }
+        } else if (what == "record" && !G.sched.empty() && !G.sched[0].item_rec.empty()) {
+            G.sched[0].item_rec[2] += 1;  // first item's event slot
+        } else if (what == "window" && !G.sched.empty()) {
+            G.sched[0].window = 256;  // steps cut for a larger ring
+        }
+    }
+    const std::string bad = validate_signature_program(G, D, O);
+    if (!bad.empty()) {
+        G.why = "internal: " + bad;
+        G.sched.clear();
+        return TMCS_OK;
     }
     G.ok = true;
     G.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();

@@ -263,6 +263,28 @@ def test_signature_single_schedule_at_the_floor(tmcs, monkeypatch):
         tmcs.tmcs_circuit_free(h)
 
 
+@pytest.mark.parametrize("mistake,reason", [("observable", "event entry"), ("record", "item record"),
+                                            ("window", "window")])
+def test_signature_validator_refuses_planted_mistakes(tmcs, monkeypatch, mistake, reason):
+    """The host-side validator of the event-signature program refuses a
+    program with an out-of-range observable id, a wrong item record or a
+    ring too small for its steps; the circuit then has no signature program
+    (sampling runs on the frame kernels)."""
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc11"), 11, 11, C.NoiseModel(0.001, 0.01))
+    h = tmcs.tmcs_circuit_build(circ)
+    assert tmcs.tmcs_circuit_stats(h)["sig_ok"] == 1
+    tmcs.tmcs_circuit_free(h)
+    monkeypatch.setenv("TMCS_TEST_CORRUPT_SIG", mistake)
+    h = tmcs.tmcs_circuit_build(circ)
+    try:
+        assert tmcs.tmcs_circuit_stats(h)["sig_ok"] == 0
+        with pytest.raises(tmcs.TmcsError) as err:
+            tmcs.tmcs_fault_outputs(h, 0)
+        assert "internal" in str(err.value) and reason in str(err.value)
+    finally:
+        tmcs.tmcs_circuit_free(h)
+
+
 def _long_span_circuit(n_mid):
     """An X error on qubit 0 flips detector 0 (first measurement) and the last
     detector (second measurement, after n_mid other detectors)."""
