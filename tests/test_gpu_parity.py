@@ -308,6 +308,38 @@ def test_pipelined_kernel_many_tiles_per_cta(monkeypatch, sched, tile_k, threads
     assert gd.any() and go.any()
 
 
+_NL7_CACHE = {}
+
+
+def _nl7_oracle(shots, seed, first_chunk):
+    """NL(7), 7/7 rounds (720 detectors): five pipelined schedules, lags 2 to
+    4; the oracle's output is computed once per (shots, seed, chunk)."""
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc7"), 7, 7, C.NoiseModel(0.005, 0.03))
+    key = (shots, seed, first_chunk)
+    if key not in _NL7_CACHE:
+        _NL7_CACHE[key] = oracle.sample(circ, shots, seed, first_chunk=first_chunk, threads=8)
+    return circ, _NL7_CACHE[key]
+
+
+@pytest.mark.parametrize("sched", range(5))
+@pytest.mark.parametrize("tile_k,threads", [(1, 1024), (2, 512)])
+def test_pipelined_kernel_every_lag_many_tiles(monkeypatch, sched, tile_k, threads):
+    """Every pipelined schedule of NL(7) (lags 2, 3 and 4) over several
+    tiles per CTA, so runs of `lag` steps cross tile boundaries."""
+    monkeypatch.setenv("TMCS_KERNEL", "6")
+    monkeypatch.setenv("TMCS_SIG_SCHED", str(sched))
+    monkeypatch.setenv("TMCS_TILE_K", str(tile_k))
+    monkeypatch.setenv("TMCS_THREADS", str(threads))
+    shots, seed, first_chunk = 64 * 1000 + 37, 53, 5
+    circ, (od, oo) = _nl7_oracle(shots, seed, first_chunk)
+    h = tmcs.tmcs_circuit_build(circ)
+    st = tmcs.tmcs_circuit_stats(h)
+    tmcs.tmcs_circuit_free(h)
+    assert st["sig_pipe_schedules"] == 5
+    gd, go = gpu_sample(circ, shots, seed, first_chunk)
+    assert np.array_equal(gd, od) and np.array_equal(go, oo)
+
+
 @pytest.mark.parametrize("queue", [1, 64])
 def test_pipelined_kernel_small_queue(monkeypatch, queue):
     """The smallest queue slices (64 events per walker warp) under heavy
