@@ -646,15 +646,16 @@ __device__ __forceinline__ void sig_apply_events(const SigArgs &A, const uint64_
         const uint32_t hi = uint32_t(q[j] >> 32);
         const uint32_t lane = hi & 63u, k = (hi >> 6) & 7u;
         const uint32_t roff = (hi >> 16) & 0x3FFFu;
+        // the observable accumulators follow the ring in shared memory, so
+        // an entry becomes one word row: detector d at (d + roff) mod W,
+        // observable o of buffer b at W + b * n_obs + o
         unsigned int *ring32 = reinterpret_cast<unsigned int *>(ring + k) + (lane >> 5);
-        unsigned int *obs32 =
-            reinterpret_cast<unsigned int *>(oacc + k + size_t((hi >> 30) & 1u) * A.n_obs * K) + (lane >> 5);
+        const uint32_t obase = A.window_mask + 1u + ((hi >> 30) & 1u) * A.n_obs;
         const uint32_t bit = 1u << (lane & 31u);
         auto put = [&](uint32_t w) {
             const uint32_t idx = w & 0x1FFFFFFFu;
-            unsigned int *p = (w & (1u << 29)) ? obs32 + size_t(idx) * 2 * K
-                                                : ring32 + size_t((idx + roff) & A.window_mask) * 2 * K;
-            atomicXor(p, bit);
+            const uint32_t row = (w & (1u << 29)) ? obase + idx : ((idx + roff) & A.window_mask);
+            atomicXor(ring32 + size_t(row) * 2 * K, bit);
         };
         if (v[j].x & kEvOverflow) {
             const uint32_t *ov = A.ev_ent + (v[j].x & ~kEvOverflow);
