@@ -231,11 +231,12 @@ int tmcs_fault_count(const tmcs_circuit *c, uint64_t *n_faults);
 
 /*
  * Outputs flipped by elementary fault `fault` (enumeration of
- * tmcs_fault_count), from the host event-signature table: detector indices,
- * then 0x80000000 | observable index, ascending. The table holds, per noise
- * unit, the outputs flipped by X and by Z on each of its qubits (DEM columns,
- * Methods "Decoding"), found by running the transposed frame maps backwards
- * over the op list; the signature sampler XORs these lists per event.
+ * tmcs_fault_count), read from the event table the signature samplers apply:
+ * detector indices, then 0x80000000 | observable index, ascending. The table
+ * holds, per event (noise unit and Pauli index, in fault order), the outputs
+ * it flips (a DEM column, Methods "Decoding"): the XOR of the lists of X and
+ * Z on each of its qubits, found by running the transposed frame maps
+ * backwards over the op list.
  * out: host, cap entries; *n_out = number of outputs (may exceed cap, then
  * only cap are written). Errors: TMCS_E_INVALID (fault out of range, no
  * table: sig_ok = 0 in tmcs_circuit_stats).
@@ -300,9 +301,10 @@ int tmcs_check_device(void);
  * The launch shape the autotuner chose for this circuit on the current
  * device (for reports): *mode = 0 if it has not run yet (first large call),
  * 3 = CTA-wide frame kernel, 4 = warp-group frame kernel, 5 = event-signature
- * kernel, 6 = pipelined event-signature kernel; *chunks = 64-shot chunks per CTA (mode 3, 5) or per warp group
- * (mode 4); *threads = CTA size; *ring_window = detector ring of the chosen
- * event-signature schedule (modes 5, 6; 0 otherwise). Any pointer may be NULL.
+ * kernel, 6 = pipelined event-signature kernel; *chunks = 64-shot chunks per
+ * CTA (modes 3, 5, 6) or per warp group (mode 4); *threads = CTA size;
+ * *ring_window = detector ring of the chosen event-signature schedule
+ * (modes 5, 6; 0 otherwise). Any pointer may be NULL.
  * Errors: TMCS_E_INVALID (NULL circuit), TMCS_E_CUDA (no current device).
  */
 int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *threads, int *ring_window);
