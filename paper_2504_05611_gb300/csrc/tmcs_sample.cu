@@ -628,9 +628,9 @@ __device__ __forceinline__ void walk_stream(const NoiseDesc &nd, const uint32_t 
     }
 }
 
-// Queued events: event slot index (low word), and lane | chunk k << 6 |
-// ring offset << 16 | observable buffer << 30 (high word; the last two are
-// zero in the barrier kernel; bits 9-15 are not read here). A thread
+// Queued events: event slot index (low word), and lane | chunk k << 6 (4
+// bits, K <= 16) | ring offset << 16 | observable buffer << 30 (high word;
+// the last two are zero in the barrier kernel; bits 10-15 are not read here). A thread
 // applies up to N at once, all N slot loads issued before any is used so
 // their latencies overlap.
 template <int N>
@@ -644,7 +644,7 @@ __device__ __forceinline__ void sig_apply_events(const SigArgs &A, const uint64_
     for (int j = 0; j < N; j++) {
         if (v[j].x == kEvNone) continue;
         const uint32_t hi = uint32_t(q[j] >> 32);
-        const uint32_t lane = hi & 63u, k = (hi >> 6) & 7u;
+        const uint32_t lane = hi & 63u, k = (hi >> 6) & 15u;
         const uint32_t roff = (hi >> 16) & 0x3FFFu;
         // the observable accumulators follow the ring in shared memory, so
         // an entry becomes one word row: detector d at (d + roff) mod W,
@@ -2120,6 +2120,7 @@ static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream
             // kernel then reports TMCS_E_TIMEOUT through the status word)
             a.stall_flush = env_int("TMCS_TEST_STALL_FLUSH", 0) > 0 ? 1u : 0u;
             switch (s.K) {
+            case 16: return launch_pipe<16>(a, t, st);
             case 8: return launch_pipe<8>(a, t, st);
             case 4: return launch_pipe<4>(a, t, st);
             case 2: return launch_pipe<2>(a, t, st);
@@ -2127,6 +2128,7 @@ static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream
             }
         }
         switch (s.K) {
+        case 16: return launch_sig<16>(a, t, st);
         case 8: return launch_sig<8>(a, t, st);
         case 4: return launch_sig<4>(a, t, st);
         case 2: return launch_sig<2>(a, t, st);
@@ -2180,7 +2182,7 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
     // pipelined kernel otherwise) x chunks per CTA x CTA size
     if (ds)
         for (int sched = 0; sched < int(c->sig.sched.size()); sched++)
-            for (int K = 1; K <= 8; K *= 2) {
+            for (int K = 1; K <= 16; K *= 2) {
                 if (!sig_fits(c, lim, K, sched)) break;
                 for (int threads : {256, 512, 1024}) {
                     const LaunchShape cs = make_shape_sig(c, n_cols, lim, K, threads, sched);
@@ -2268,7 +2270,7 @@ static LaunchShape choose_shape_sig(const tmcs_circuit *c, uint64_t n_cols, cons
     const bool pipe = env_int("TMCS_KERNEL", 0) == 6 && n_barrier < int(c->sig.sched.size());
     const int lo = pipe ? n_barrier : 0, hi = pipe ? int(c->sig.sched.size()) - 1 : n_barrier - 1;
     const int sched = std::min(std::max(lo + env_int("TMCS_SIG_SCHED", 0), lo), hi);
-    int K = kcap > 0 ? std::min(kcap, 8) : 4;
+    int K = kcap > 0 ? std::min(kcap, 16) : 4;
     while (K > 1 && (K & (K - 1))) K--;
     while (K > 1 && !sig_fits(c, lim, K, sched)) K >>= 1;
     if (kcap <= 0) {

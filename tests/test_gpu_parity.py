@@ -234,7 +234,8 @@ def test_every_launch_shape_is_bit_exact(monkeypatch, kernel, tile_k, threads, w
     assert_parity(circ, 64 * 53 + 17, seed=21)
 
 
-@pytest.mark.parametrize("tile_k,threads", [(1, 256), (1, 1024), (2, 512), (4, 256), (4, 1024), (8, 512)])
+@pytest.mark.parametrize("tile_k,threads", [(1, 256), (1, 1024), (2, 512), (4, 256), (4, 1024), (8, 512),
+                                           (16, 1024), (16, 512)])
 @pytest.mark.parametrize("window", [0, 1024])
 def test_signature_kernel_shapes_are_bit_exact(monkeypatch, tile_k, threads, window):
     """The event-signature kernel under every chunks-per-CTA / CTA-size
@@ -271,7 +272,7 @@ def test_signature_schedules_are_bit_exact(monkeypatch, sched, tile_k, threads):
 
 
 @pytest.mark.parametrize("sched", range(6))
-@pytest.mark.parametrize("tile_k,threads", [(4, 1024), (8, 512), (1, 256), (2, 128)])
+@pytest.mark.parametrize("tile_k,threads", [(4, 1024), (8, 512), (1, 256), (2, 128), (16, 1024)])
 def test_pipelined_kernel_is_bit_exact(monkeypatch, sched, tile_k, threads):
     """The pipelined event-signature kernel under each of its schedules (step
     window x steps in flight) and launch shapes reproduces the oracle: ragged
