@@ -54,6 +54,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_philox4x32_10.restype = None
         L.oracle_gap_table.argtypes = [ctypes.c_double, P]
         L.oracle_gap_table.restype = None
+        L.oracle_pauli_channel.argtypes = [ctypes.c_double] * 3 + [P, P, P]
+        L.oracle_pauli_channel.restype = ctypes.c_int
         L.oracle_sample.argtypes = [I64, P, P, P, P, P, P, I64, I64, I64, I64, U64, U64, U64, P, P, ctypes.c_int]
         L.oracle_sample.restype = ctypes.c_int
         L.oracle_sample_measurements.argtypes = [I64, P, P, P, P, P, P, I64, I64, I64, I64, P, U64, U64, U64, P,
@@ -78,7 +80,13 @@ class Marshalled:
         self.codes = np.array([_CODES[o.name] for o in ops], dtype=np.int32)
         self.ps = np.array([o.p for o in ops], dtype=np.float64)
         self.args = np.array([o.arg for o in ops], dtype=np.uint32)
-        self.args2 = np.array([getattr(o, "arg2", 0) for o in ops], dtype=np.uint32)
+        self.args2 = np.zeros(self.n_ops, dtype=np.uint32)
+        # PAULI_CHANNEL_1: the oracle derives the event probability and the
+        # X/Y/Z thresholds from (px, py, pz) itself; the generator's copies
+        # (op.p, op.arg, op.arg2) are not read
+        for i, o in enumerate(ops):
+            if o.name == "PAULI_CHANNEL_1":
+                self.ps[i], self.args[i], self.args2[i] = pauli_channel(*o.channel)
         lens = np.array([o.targets.size for o in ops], dtype=np.int64)
         self.toff = np.zeros(self.n_ops + 1, dtype=np.int64)
         np.cumsum(lens, out=self.toff[1:])
@@ -102,6 +110,17 @@ def philox4x32_10(ctr: Sequence[int], key: Sequence[int]) -> Tuple[int, int, int
     out = np.zeros(4, dtype=np.uint32)
     lib().oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
     return tuple(int(v) for v in out)
+
+
+def pauli_channel(px: float, py: float, pz: float) -> Tuple[float, int, int]:
+    """PAULI_CHANNEL_1(px, py, pz) as (p, t1, t2): event probability and the
+    Pauli-word thresholds of X and Y (``oracle_pauli_channel``)."""
+    p = np.zeros(1, dtype=np.float64)
+    t = np.zeros(2, dtype=np.uint32)
+    rc = lib().oracle_pauli_channel(float(px), float(py), float(pz), _ptr(p), _ptr(t), _ptr(t[1:]))
+    if rc != 0:
+        raise ValueError(f"PAULI_CHANNEL_1({px}, {py}, {pz}): invalid probabilities")
+    return float(p[0]), int(t[0]), int(t[1])
 
 
 def gap_table(p: float) -> np.ndarray:

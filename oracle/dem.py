@@ -138,6 +138,32 @@ def columns(circuit) -> List[Tuple[int, int]]:
     return sorted({(d, o) for d, o in zip(dets, obss) if d or o})
 
 
+def column_probabilities(circuit) -> Dict[Tuple[int, int], Tuple[float, int]]:
+    """Per distinct non-empty signature (detector mask, observable mask): the
+    probability that an odd number of its elementary faults occur in a shot,
+    and how many faults it merges. Faults of one channel (noise op, target
+    unit) exclude one another, so they add within the channel; channels are
+    independent, so a signature's parity over channels XOR-combines:
+    P = (1 - prod_channels (1 - 2 P_channel)) / 2."""
+    dets, obss, chans, probs = signatures(circuit)
+    per: Dict[Tuple[int, int], Dict[int, float]] = {}
+    count: Dict[Tuple[int, int], int] = {}
+    for d, o, c, p in zip(dets, obss, chans, probs):
+        if not (d or o):
+            continue
+        key = (d, o)
+        per.setdefault(key, {})
+        per[key][c] = per[key].get(c, 0.0) + p
+        count[key] = count.get(key, 0) + 1
+    out = {}
+    for key, by_chan in per.items():
+        prod = 1.0
+        for p in by_chan.values():
+            prod *= 1.0 - 2.0 * p
+        out[key] = ((1.0 - prod) / 2.0, count[key])
+    return out
+
+
 def circuit_distance(circuit, max_weight: int = 3) -> int:
     """Smallest number of elementary faults whose combined signature flips no
     detector but some observable (brute force up to ``max_weight``; returns

@@ -33,8 +33,9 @@
  *   Pauli index bits: x = bit 0, z = bit 1 (X=1, Z=2, Y=3); DEPOLARIZE2 puts
  *   k>>2 on the first target and k&3 on the second. PAULI_CHANNEL_1 (event
  *   probability p = px + py + pz, Methods "Decoherence") picks X if
- *   w_pauli < t1, Y if w_pauli < t2, else Z, with the op's thresholds
- *   t1 = floor(2^32 px / p), t2 = floor(2^32 (px + py) / p).
+ *   w_pauli < t1, Y if w_pauli < t2, else Z, with t1 = floor(2^32 px / p),
+ *   t2 = floor(2^32 (px + py) / p); the oracle derives p, t1 and t2 from
+ *   (px, py, pz) itself (oracle_pauli_channel).
  *
  * Build: gcc -O2 -ffp-contract=off -shared -fPIC -pthread (see oracle/build.py).
  */
@@ -93,6 +94,31 @@ static uint32_t to_u32_fraction(double x)
     if (!(v > 0.0)) return 0u;
     if (v >= 4294967295.0) return 0xFFFFFFFFu;
     return (uint32_t)v;
+}
+
+/* PAULI_CHANNEL_1(px, py, pz) (Methods "Decoherence": X and Y with the
+ * amplitude-damping share, Z with the dephasing share of an aged ebit): an
+ * event happens with probability p = px + py + pz (a sum up to 1e-12 above 1
+ * is rounding and is taken as 1); given an event, the uniform Pauli word w
+ * of the sampling specification picks X when w < t1, Y when t1 <= w < t2
+ * and Z otherwise, with t1 = floor(2^32 px / p) and t2 = floor(2^32 (px + py)
+ * / p), so that X, Y, Z occur with probabilities px/p, py/p, pz/p up to
+ * 2^-32. Returns -1 for probabilities outside [0, 1] or summing above 1. */
+int oracle_pauli_channel(double px, double py, double pz, double *p, uint32_t *t1, uint32_t *t2)
+{
+    if (!(px >= 0.0 && px <= 1.0 && py >= 0.0 && py <= 1.0 && pz >= 0.0 && pz <= 1.0)) return -1;
+    double sum = px + py + pz;
+    if (sum > 1.0 + 1e-12) return -1;
+    if (sum > 1.0) sum = 1.0;
+    *p = sum;
+    if (sum == 0.0) {
+        *t1 = 0u;
+        *t2 = 0u;
+        return 0;
+    }
+    *t1 = to_u32_fraction(px / sum);
+    *t2 = to_u32_fraction((px + py) / sum);
+    return 0;
 }
 
 /* t[0..4095] hold T[1..4096] = floor(2^32 (1-p)^g). p must be in (0, 1]. */

@@ -54,3 +54,28 @@ def test_marginals_match_samples(kind):
     pab = dem.pair_flip_probability(c, a, b)
     emp = np.mean(np.logical_xor(bd[a], bd[b]))
     assert abs(emp - pab) < 5.5 * math.sqrt(pab * (1 - pab) / shots)
+
+
+def test_column_probabilities_closed_forms():
+    """Column probabilities against closed forms: one X_ERROR(p) before M is
+    one column of probability p; DEPOLARIZE1(p) before M has X and Y flip the
+    record (one column, mutually exclusive faults: 2p/3); two independent
+    X_ERROR sites with the same signature XOR-combine to 2p(1-p); Z_ERROR
+    before M flips nothing (no column)."""
+    from paper_2504_05611_gb300.circuits import Circuit
+    p = 0.1
+    c = Circuit()
+    c.append("R", [0, 1, 2, 3])
+    c.append("X_ERROR", [0], p=p)
+    c.append("DEPOLARIZE1", [1], p=p)
+    c.append("X_ERROR", [2], p=p)
+    c.append("X_ERROR", [2], p=p)
+    c.append("Z_ERROR", [3], p=p)
+    c.append("M", [0, 1, 2, 3])
+    for r in range(4):
+        c.append("DETECTOR", [r])
+    cols = dem.column_probabilities(c)
+    assert set(cols) == {(1, 0), (2, 0), (4, 0)}
+    assert abs(cols[(1, 0)][0] - p) < 1e-15 and cols[(1, 0)][1] == 1
+    assert abs(cols[(2, 0)][0] - 2 * p / 3) < 1e-15 and cols[(2, 0)][1] == 2
+    assert abs(cols[(4, 0)][0] - 2 * p * (1 - p)) < 1e-15 and cols[(4, 0)][1] == 2

@@ -187,3 +187,45 @@ def test_pauli_channel_1_edges():
         c.append("DETECTOR", [r])
     b = bits(c, 640)
     assert not b[0].any() and b[1].sum() >= 639 and not b[2].any()
+
+
+def test_pauli_channel_1_thresholds_oracle_vs_generator():
+    """The oracle derives PAULI_CHANNEL_1's event probability and X/Y
+    thresholds from (px, py, pz) itself; the op-list generator computes the
+    copies the library receives (op.p, op.arg, op.arg2). The two must agree
+    exactly, or the oracle and the CUDA sampler would split X/Y/Z differently.
+    The split itself is pinned by test_pauli_channel_1_distribution."""
+    from paper_2504_05611_gb300.circuits import pauli_channel_thresholds
+    rng = np.random.default_rng(77)
+    cases = [(0.0, 0.0, 0.0), (1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0), (0.1, 0.2, 0.7),
+             (1 / 3, 1 / 3, 1 / 3), (1e-9, 1e-9, 1e-9), (0.25, 0.25, 0.5), (2.5e-5, 2.5e-5, 4.9e-5)]
+    for _ in range(2000):
+        v = rng.random(3) * rng.choice([1e-6, 1e-3, 0.1, 0.33])
+        cases.append(tuple(float(x) for x in v))
+    for ch in cases:
+        assert oracle.pauli_channel(*ch) == pauli_channel_thresholds(*ch), ch
+    # PAULI_CHANNEL_1 with p = 1 and a pure X split: every word is below t1
+    p, t1, t2 = oracle.pauli_channel(1.0, 0.0, 0.0)
+    assert p == 1.0 and t1 == t2 == 2 ** 32 - 1
+    with pytest.raises(ValueError):
+        oracle.pauli_channel(0.6, 0.6, 0.0)
+
+
+def test_oracle_reads_channel_not_generator_copy():
+    """Planted mismatch: an op whose generator copies (p, arg, arg2) are
+    wrong still samples with the oracle's own derivation from (px, py, pz)."""
+    def circ(corrupt):
+        c = Circuit()
+        c.append("R", [0, 1])
+        c.append("RX", [2])
+        c.append("PAULI_CHANNEL_1", [0], p=(0.3, 0.0, 0.0))
+        if corrupt:
+            op = c.ops[-1]
+            op.p, op.arg, op.arg2 = 0.9, 0, 0    # would mean "Z with probability 0.9"
+        readout_xz(c, 0, 1, 2)
+        c.append("M", [1])
+        c.append("MX", [2])
+        c.append("DETECTOR", [0])
+        c.append("DETECTOR", [1])
+        return c
+    assert np.array_equal(bits(circ(False), 2000), bits(circ(True), 2000))

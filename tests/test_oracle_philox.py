@@ -1,12 +1,15 @@
 """Pins of the oracle's Philox4x32-10 and gap tables.
 
-Philox4x32-10 (Salmon et al., SC'11) is a bijection of the 128-bit counter
-for a fixed key: this test inverts the published round structure (the
-multipliers are odd, so each low product is invertible mod 2^32) and checks
-that the inverse of the oracle's output returns the counter; a wrong
-multiplier, key schedule or output wiring in the oracle breaks the round
-trip. Output statistics are checked too. (An independent implementation on
-the GPU, cuRAND's Philox4_32_10, is compared in tests/test_gpu_rng.py.)
+Philox4x32-10 (Salmon et al., SC'11) is pinned three ways: (1) the
+known-answer vectors published with the generator's reference library
+(``tests/golden/philox4x32_10_kat.txt``), which fix every output word for
+three counter/key pairs; (2) the round structure is inverted (the
+multipliers are odd, so each low product is invertible mod 2^32) and the
+inverse of the oracle's output must return the counter, so a wrong
+multiplier, key schedule or output wiring breaks the round trip; (3) output
+statistics. An independent implementation, cuRAND's device Philox4x32-10, is
+compared with the oracle on many random counter/key pairs in
+``tests/test_gpu_rng.py``.
 
 The gap table is pinned by the distribution it induces: P(G >= g) read off
 the table must equal the geometric tail (1-p)^g to within the 2^-32
@@ -38,6 +41,15 @@ def philox_inverse(out, key):
         c3 = n2 ^ hi0 ^ k1
         n0, n1, n2, n3 = c0, c1, c2, c3
     return (n0, n1, n2, n3)
+
+
+def test_philox_known_answer_vectors():
+    from conftest import golden_rows
+    rows = golden_rows("philox4x32_10_kat.txt")
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        assert oracle.philox4x32_10(v[0:4], v[4:6]) == tuple(v[6:10])
 
 
 def test_philox_is_the_published_bijection():
