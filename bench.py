@@ -617,7 +617,8 @@ def _kernel_sha():
     kernel build it was measured on."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("tmcs_sample.cu", "tmcs_internal.h", "tmcs_host.cpp", "tmcs_signature.cpp"):
+    for f in ("tmcs_sample.cu", "tmcs_flow.cu", "tmcs_device.cuh", "tmcs_internal.h", "tmcs_host.cpp",
+              "tmcs_signature.cpp"):
         with open(os.path.join(ROOT, "paper_2504_05611_gb300", "csrc", f)) as fh:
             h.update(_strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]

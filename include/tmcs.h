@@ -89,6 +89,12 @@ typedef struct tmcs_circuit tmcs_circuit; /* opaque; owned by the library */
 
 /*
  * Validate and compile an op list (host only; no CUDA call).
+ * Defining passages: the op list is the noisy circuit of Methods
+ * "Simulation" (reset flips, 1- and 2-qubit depolarizing after gates,
+ * measurement flips, depolarized ebit pairs, classically conditioned
+ * operations) built for the protocols of Methods "Non-local CNOT circuit" and
+ * "State teleportation circuit" (Fig. 1b, c); its DETECTOR and OBSERVABLE
+ * ops are the rows and logical observables of Methods "Decoding".
  * Compiles to a straight-line program over frame-component slots: liveness
  * pruning drops every x/z component that cannot reach a detector or
  * observable, components get shared-memory slots by interval allocation, and
@@ -149,6 +155,10 @@ int tmcs_reference_sample(const tmcs_circuit *c, uint8_t *meas_bits);
 
 /*
  * Sample `shots` shots with global 64-shot chunks 0 .. ceil(shots/64)-1.
+ * Defining passages: the Monte Carlo sampling of the noisy circuit in
+ * Methods "Simulation" (each shot runs the circuit with independently drawn
+ * noise), producing per shot the syndrome vector of detector values and the
+ * logical-observable flips that Methods "Decoding" hands to the decoder.
  * detector_bits:   device, n_det * ceil(shots/64) uint64, 8-byte aligned
  * observable_bits: device, n_obs * ceil(shots/64) uint64 (may be NULL if n_obs == 0)
  * Asynchronous on `stream`, with two one-time exceptions per circuit and
@@ -161,12 +171,17 @@ int tmcs_reference_sample(const tmcs_circuit *c, uint8_t *meas_bits);
  * event-signature program (tmcs_circuit_stats sig_ok), else the frame
  * kernels; both give the same bits. Tuning knobs in the environment change
  * only the schedule: TMCS_KERNEL (3 CTA frame kernel, 4 warp-group frame
- * kernel, 5 event-signature kernel, 6 pipelined event-signature kernel),
- * TMCS_TILE_K, TMCS_THREADS, TMCS_SIG_SCHED (signature schedule index),
+ * kernel, 5 event-signature kernel, 6 pipelined event-signature kernel,
+ * 7 decoupled event-signature kernel: walker warps append events to a
+ * shared-memory arena, applier warps apply whole steps), TMCS_TILE_K,
+ * TMCS_THREADS, TMCS_SIG_SCHED (signature schedule index), TMCS_FLOW_APPLIERS
+ * and TMCS_FLOW_ARENA (kernel 7: applier warps, arena entries),
  * TMCS_SIG_WINDOW (read by tmcs_circuit_build), TMCS_AUTOTUNE=0.
  * Testing: TMCS_TEST_STALL_FLUSH=1 makes the pipelined kernel's flusher wait
  * for a stream count that never arrives, so its bounded wait (2 s) expires,
  * every warp leaves and tmcs_check_device reports TMCS_E_TIMEOUT.
+ * TMCS_TEST_FLOW_CAP=n gives every step of kernel 7 an arena region of n
+ * events, so most events take its overflow path (same bits).
  * Errors: TMCS_E_INVALID (NULL circuit/buffer, shots == 0), TMCS_E_CUDA,
  * TMCS_E_OOM (program upload).
  */
@@ -175,6 +190,9 @@ int tmcs_sample(const tmcs_circuit *c, uint64_t shots, uint64_t seed,
 
 /*
  * Resumable / shardable form: shots 64*first_chunk .. 64*first_chunk+shots-1
+ * (Methods "Simulation": the paper spreads the shots of one circuit over
+ * hundreds to thousands of CPU cores with MPI; a chunk range is that unit of
+ * independent work, here one per GPU or per call)
  * of the stream defined by `seed`. Outputs have ceil(shots/64) words per
  * detector; word j is global chunk first_chunk + j. Concatenating the outputs
  * of disjoint ranges reproduces one tmcs_sample call bit for bit.
@@ -191,22 +209,26 @@ int tmcs_sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shot
  * request path, code that must not let cudaMalloc/cudaFree synchronise the
  * device -- it calls no cudaMalloc, cudaFree or other allocating routine.
  * Its scratch is one file-scope device array of 8 MiB (every GPU that loads
- * libtmcs.so holds it until the process exits): each call clears the status
- * word in it, copies the circuit's compiled frame program into it
- * (stream-ordered on `stream`) and launches the CTA-wide frame kernel on it.
+ * libtmcs.so holds it until the process exits): a status word (256 bytes)
+ * followed by the circuit's compiled frame program, which each call copies
+ * into it (stream-ordered on `stream`) before launching a frame kernel on it.
  * Every sampling kernel draws the same noise streams, so outputs are
  * bit-identical to tmcs_sample_range with the same arguments, whichever
  * kernel that call uses.
  *   - Circuits whose compiled program exceeds the array (device_bytes of
  *     tmcs_circuit_info plus 256) are rejected with TMCS_E_INVALID.
  *   - The first call on each device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *     that device current and clears the status word (synchronously); make
+ *     that first call before any stream capture.
  *   - All calls share the array and it keeps the last call's contents: calls
  *     that overlap on the GPU (other streams, other host threads) race; the
  *     caller must serialise them (e.g. one stream).
- *   - Launch shape: the heuristic (or TMCS_TILE_K / TMCS_THREADS); no timing.
- *   - A device-side bounded wait that expires is not reported here (the
- *     status word is cleared by the next call).
+ *   - Launch shape: the frame kernels' heuristic, or the knobs TMCS_KERNEL=3/4,
+ *     TMCS_TILE_K, TMCS_THREADS, TMCS_WARPS, TMCS_GROUP; no timing.
+ *   - A device-side bounded wait that expires sets the array's status word,
+ *     which stays set until tmcs_check_device reports TMCS_E_TIMEOUT and
+ *     clears it. Testing: TMCS_TEST_NOALLOC_EXPIRED=1 sets that word as an
+ *     expired wait would.
  * Arguments and errors as tmcs_sample_range.
  */
 int tmcs_sample_noalloc(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
@@ -244,6 +266,34 @@ int tmcs_fault_count(const tmcs_circuit *c, uint64_t *n_faults);
 int tmcs_fault_outputs(const tmcs_circuit *c, uint64_t fault, uint32_t *out, uint32_t cap, uint32_t *n_out);
 
 /*
+ * Detector error model columns (Methods "Decoding": the parity-check matrix
+ * derived from the detector error model has one row per detector and one
+ * column per distinct error mechanism, a fault class that flips one or more
+ * detectors and possibly observables; Table III "cols" counts them). Single
+ * faults are enumerated as in tmcs_fault_count and read from the same
+ * event-signature table the samplers apply (tmcs_fault_outputs); faults with
+ * equal non-empty signatures merge into one column. Host only (no CUDA
+ * call); built on the first call and kept with the circuit.
+ *   n_cols, n_entries: in/out. Call with every array NULL to get the sizes;
+ *     then pass arrays of at least those sizes (their capacities in *n_cols,
+ *     *n_entries; TMCS_E_BUFFER if smaller).
+ *   col_off:    n_cols + 1 uint64: column c's entries are
+ *               entries[col_off[c] .. col_off[c+1]), sorted ascending
+ *   entries:    detector id, or 0x80000000 | observable id
+ *   col_p:      n_cols doubles: probability that an odd number of the
+ *               column's faults occur in one shot (faults of one noise unit
+ *               are mutually exclusive, units independent:
+ *               (1 - prod_u (1 - 2 P_u)) / 2 with P_u the unit's share)
+ *   col_faults: n_cols uint64: single faults merged into the column
+ * Columns come in ascending order of their entry lists. Any of the four
+ * arrays may be NULL. Errors: TMCS_E_INVALID (NULL circuit or sizes, no
+ * event-signature program: tmcs_circuit_stats sig_ok = 0), TMCS_E_BUFFER,
+ * TMCS_E_OOM.
+ */
+int tmcs_dem_columns(const tmcs_circuit *c, uint64_t *n_cols, uint64_t *n_entries, uint64_t *col_off,
+                     uint32_t *entries, double *col_p, uint64_t *col_faults);
+
+/*
  * Raw measurement records of noisy executions (Methods "Decoding": detector
  * values are parities of the measurement outcomes of one noisy run; this
  * returns the outcomes themselves). Shots 64*first_chunk .. +shots-1 of the
@@ -278,6 +328,11 @@ typedef struct {
 } tmcs_job;
 
 /*
+ * Defining passages: the paper's results are sweeps of many circuits -- codes,
+ * distances, rounds and physical error rates (Results "Distributed
+ * operations thresholds and scaling", Methods "Simulation" and
+ * "Statistics": each point needs enough shots to see logical errors) -- each
+ * sampled as in tmcs_sample. This call samples such a set of jobs together.
  * Sample many circuits of uneven size on `stream`: the jobs share persistent
  * launches whose resident CTAs pull (job, tile) work items from a device
  * queue; a job that fills the GPU by itself (at least 16 chunks per SM) with
@@ -291,9 +346,13 @@ int tmcs_batch_sample(const tmcs_job *jobs, size_t n_jobs, void *stream);
 
 /*
  * Synchronous device-side error check for the current device: returns
- * TMCS_E_TIMEOUT (and clears the flag) if any sampling kernel since the last
+ * TMCS_E_TIMEOUT (and clears the flags) if any sampling kernel since the last
  * check gave up on a bounded wait (its outputs are then incomplete), else
- * TMCS_OK. Blocks until prior work on the device's legacy stream is done.
+ * TMCS_OK. It reads the library's per-device status word and, once
+ * tmcs_sample_noalloc has run on the device, that entry point's status word
+ * too. Blocks until prior work on the device's legacy stream is done. This
+ * call stands in for a per-stream status query: the status words are per
+ * device, so one check covers every stream.
  */
 int tmcs_check_device(void);
 

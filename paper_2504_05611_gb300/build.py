@@ -21,7 +21,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtmcs.so")
-SOURCES = ["tmcs_host.cpp", "tmcs_signature.cpp", "tmcs_sample.cu", "tmcs_server.cu", "tmcs_peaks.cu"]
+SOURCES = ["tmcs_host.cpp", "tmcs_signature.cpp", "tmcs_sample.cu", "tmcs_flow.cu", "tmcs_server.cu",
+           "tmcs_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,624 @@
+// Decoupled event-signature sampler (sm_103a): the walk of the noise streams
+// and the application of their events to the detector words run in
+// different warps, joined by a shared-memory event arena instead of CTA
+// barriers.
+//
+// What it computes is what sig_kernel computes (Methods "Simulation":
+// detector and observable flips as XORs of the output lists of the sampled
+// noise events, each event drawn from the Philox4x32-10 streams of the
+// sampling specification), with the same schedule: items (64-unit noise
+// segments) in steps whose detectors lie in a ring window above the step's
+// flush point. The difference is the execution:
+//
+//  * Walker warps take (tile, step, item, chunk) streams in CTA order from
+//    one shared counter, across step and tile boundaries, and append every
+//    event as one 32-bit word (event slot, chunk, lane) to their step's
+//    region of a circular arena. No lane waits for the end of a step.
+//  * Applier warps take steps in order: once every stream of step Q has
+//    finished, they apply its events to the ring (shared-memory atomic XORs
+//    of the event's output list), write the detectors the step finalises to
+//    HBM, clear them, and free the step's arena region.
+//
+// A step's region has a capacity fixed at launch from the expected number
+// of its events (mean + 6 sigma + 64, at most the arena). A walker may start
+// a stream of step Q only when Q's region no longer overlaps an unapplied
+// step's; an event beyond its region's capacity is held by its lane, which
+// stops walking until Q is the step being applied and then XORs the event
+// into the ring itself before reporting its stream finished. The ring is
+// therefore only ever touched for the step being applied, so it needs one
+// window of detectors, while the arena keeps several steps of walking in
+// flight. All waits are bounded (kWaitNs); on expiry the kernel sets bit 0
+// of the status word and every warp leaves.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+#include "tmcs_device.cuh"
+#include "tmcs_internal.h"
+
+namespace tmcs {
+
+constexpr uint32_t kFlowSlots = 64;       // steps in flight (done / count slots)
+constexpr uint32_t kFlowApplyBatch = 4;   // events an applier lane loads at once
+constexpr uint32_t kFlowMinArena = 1024;  // smallest useful arena (entries)
+constexpr uint32_t kFlowMaxArena = 65536;
+
+struct FlowArgs {
+    const NoiseDesc *noise;
+    const uint32_t *tables;
+    const uint4 *item_rec;      // op, segment, first event slot, kind | table << 3 | (units-1) << 16 | desc << 22
+    const uint4 *steps;         // item_begin, item_end, flush_lo, flush_hi
+    const float *step_events;   // expected events per chunk of each step
+    const uint32_t *ev_ent;     // two words per event slot, then the overflow lists
+    uint32_t n_steps, n_items, window_mask, n_obs;
+    uint32_t arena;             // arena entries (power of two)
+    uint32_t test_cap;          // testing: capacity of every step's region (0: from step_events)
+    uint32_t smem_tables;       // gap tables staged in shared memory (count), 0: read from global
+    uint32_t walkers;           // walker warps; the CTA's other warps apply
+    uint32_t key0, key1, first_chunk;
+    uint32_t vec_out;           // det 16-byte aligned and n_cols even: 16-byte output stores
+    uint64_t n_cols, last_mask, n_tiles;
+    uint64_t *det;
+    uint64_t *obs;
+    uint32_t *status;
+};
+
+struct FlowCtl {
+    unsigned long long next;       // streams handed out (CTA sequence)
+    unsigned long long u_applied;  // arena position (unwrapped) of the first unapplied step
+    uint32_t applied;              // steps applied (CTA sequence)
+    uint32_t abort;                // a bounded wait expired
+    uint32_t app_stop;             // appliers leave (written by applier thread 0 before a barrier)
+    uint32_t done[kFlowSlots];     // finished streams of step Q (slot Q mod kFlowSlots)
+    uint32_t cnt[kFlowSlots];      // arena entries reserved by step Q's events
+};
+
+// Shared-memory regions (same order and sizes as flow_smem_bytes): ring and
+// observable rows, step table (item end, region capacity, region offset per
+// step, then the tile's total), gap tables, arena.
+struct FlowSmem {
+    uint64_t *ring;
+    uint32_t *send, *scap, *soff;
+    uint32_t *stab;
+    uint32_t *arena;
+};
+
+__host__ __device__ inline size_t flow_ring_bytes(uint32_t W, uint32_t n_obs, int K) {
+    return ((size_t(W) + n_obs) * size_t(K) * 8 + 15) & ~size_t(15);
+}
+__host__ __device__ inline size_t flow_step_bytes(uint32_t n_steps) {
+    return ((3 * size_t(n_steps) + 1) * 4 + 15) & ~size_t(15);
+}
+
+__device__ __forceinline__ FlowSmem flow_layout(uint64_t *smem, const FlowArgs &A, int K) {
+    FlowSmem S;
+    unsigned char *b = reinterpret_cast<unsigned char *>(smem);
+    S.ring = smem;
+    b += flow_ring_bytes(A.window_mask + 1u, A.n_obs, K);
+    S.send = reinterpret_cast<uint32_t *>(b);
+    S.scap = S.send + A.n_steps;
+    S.soff = S.scap + A.n_steps;
+    b += flow_step_bytes(A.n_steps);
+    S.stab = reinterpret_cast<uint32_t *>(b);
+    b += size_t(A.smem_tables) * kTableWords * 4;
+    S.arena = reinterpret_cast<uint32_t *>(b);
+    return S;
+}
+
+template <int K>
+struct FlowLog {
+    static constexpr uint32_t v = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : 4;
+};
+
+__device__ __forceinline__ unsigned long long ld_shared_volatile64(const unsigned long long *p) {
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+
+// XORs one event into the ring: word wv = event slot << (6 + log2 K) |
+// chunk << 6 | lane, v = the slot's two words (an entry is observable flag
+// << 29 | output index; observables are the rows after the ring).
+template <int K>
+__device__ __forceinline__ void flow_put(const FlowArgs &A, uint64_t *ring, uint32_t wv, uint2 v) {
+    if (v.x == kEvNone) return;
+    const uint32_t lane = wv & 63u, k = (wv >> 6) & uint32_t(K - 1);
+    uint32_t *base = reinterpret_cast<uint32_t *>(ring) + 2u * k + (lane >> 5);
+    const uint32_t bit = 1u << (lane & 31u);
+    const uint32_t obs_row = A.window_mask + 1u;
+    auto put = [&](uint32_t e) {
+        const uint32_t idx = e & 0x1FFFFFFFu;
+        const uint32_t row = (e & (1u << 29)) ? obs_row + idx : (idx & A.window_mask);
+        atomicXor(base + size_t(row) * (2u * uint32_t(K)), bit);
+    };
+    if (v.x & kEvOverflow) {
+        const uint32_t *ov = A.ev_ent + (v.x & ~kEvOverflow);
+        for (uint32_t x = 0; x < v.y; x++) put(__ldg(ov + x));
+    } else {
+        put(v.x);
+        if (v.y != kEvNone) put(v.y);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void flow_put_word(const FlowArgs &A, uint64_t *ring, uint32_t wv) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(A.ev_ent) + (wv >> (6u + FlowLog<K>::v)));
+    flow_put<K>(A, ring, wv, v);
+}
+
+// Walker warps. Every lane holds at most one stream; streams are handed out
+// in CTA order (tile, step, item, chunk). Per iteration a walking lane runs
+// one Philox call (two draws) and reserves arena entries for its events
+// together with the lanes of its warp whose streams belong to the same
+// step (one shared atomic per step and warp).
+template <int K, bool SMT>
+__device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, FlowCtl &C, uint32_t nt,
+                                          uint32_t nv_last, const uint32_t *tabs) {
+    constexpr uint32_t LK = FlowLog<K>::v;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t n_steps = A.n_steps, amask = A.arena - 1u;
+    const uint64_t per_tile = uint64_t(A.n_items) << LK;
+    const uint64_t total = uint64_t(nt) * per_tile;
+    const uint64_t c_tile = S.soff[n_steps];
+    bool have = false, live = false, ended = false, exhausted = false;
+    uint32_t npend = 0, pend0 = 0, pend1 = 0;
+    uint32_t tcur = 0xFFFFFFFFu, qcur = 0;
+    uint64_t tbase = 0;
+    // the lane's stream: step Q, its region (capacity, low word of its
+    // unwrapped arena position, gate), Philox stream words, call counter,
+    // first event slot, kind, Pauli counts, gap table offset, position and
+    // length in trials
+    uint32_t Q = 0, cap = 0, uq = 0;
+    long long gate = 0;
+    PhiloxStream ps{0u, 0u, 0u};
+    uint32_t call = 0, ubase = 0, kind = 0, npauli = 1, kp = 1, toff = 0, t1 = 0, t2 = 0, ktag = 0;
+    int pos = -1, n_trials = 0;
+    float inv = 0.f;
+    uint32_t t_wait = 0;
+    bool waiting = false;
+    for (;;) {
+        if (__any_sync(0xFFFFFFFFu, ld_shared_volatile(&C.abort) != 0u)) return;
+        if (!have && !exhausted) {
+            const uint64_t g = grab_index64(&C.next);
+            if (g >= total) {
+                exhausted = true;
+            } else {
+                if (tcur == 0xFFFFFFFFu || g - tbase >= per_tile) {
+                    tcur = uint32_t(g / per_tile);
+                    tbase = uint64_t(tcur) * per_tile;
+                    qcur = 0;
+                }
+                const uint32_t sl = uint32_t(g - tbase);
+                const uint32_t it = sl >> LK, k = sl & uint32_t(K - 1);
+                while (it >= S.send[qcur]) qcur++;
+                Q = tcur * n_steps + qcur;
+                const uint64_t U = uint64_t(tcur) * c_tile + S.soff[qcur];
+                cap = S.scap[qcur];
+                gate = (long long)(U + cap) - (long long)A.arena;
+                uq = uint32_t(U);
+                const uint4 rec = __ldg(A.item_rec + it);
+                kind = rec.w & 7u;
+                npauli = npauli_of(kind);
+                kp = sig_paulis(kind);
+                toff = ((rec.w >> 3) & 0x1FFFu) * kTableWords;
+                inv = __uint_as_float(tabs[toff + kGapLen]);
+                if (kind == N_PC1) {
+                    t1 = __ldg(&A.noise[rec.w >> 22].t1);
+                    t2 = __ldg(&A.noise[rec.w >> 22].t2);
+                }
+                const uint32_t nv = tcur == nt - 1u ? nv_last : uint32_t(K);
+                const uint64_t col = (uint64_t(blockIdx.x) + uint64_t(tcur) * gridDim.x) * uint64_t(K) + k;
+                ps = philox_stream(A.first_chunk + uint32_t(col), rec.x, rec.y, A.key0, A.key1);
+                ubase = rec.z;
+                ktag = k << 6;
+                // chunks past the end of the call (ragged last tile): no trials
+                n_trials = k < nv ? 64 * int(((rec.w >> 16) & 63u) + 1u) : 0;
+                call = 0;
+                pos = -1;
+                have = true;
+                live = false;
+                ended = false;
+            }
+        }
+        // the stream may start once its step's arena region is free and the
+        // step is within the slots in flight
+        if (have && !live) {
+            const long long ua = (long long)ld_shared_volatile64(&C.u_applied);
+            if (ua >= gate && Q - ld_shared_volatile(&C.applied) < kFlowSlots) {
+                __threadfence_block();  // the appliers' reads of the region precede our writes
+                live = true;
+            }
+        }
+        // events held back by a full region: once step Q is the one being
+        // applied, XOR them into the ring directly
+        if (npend && ld_shared_volatile(&C.applied) == Q) {
+            __threadfence_block();
+            flow_put_word<K>(A, S.ring, pend0);
+            if (npend > 1) flow_put_word<K>(A, S.ring, pend1);
+            npend = 0;
+        }
+        const bool walk = live && !ended && npend == 0;
+        const uint32_t wm = __ballot_sync(0xFFFFFFFFu, walk);
+        if (wm) {
+            uint32_t e0 = 0, e1 = 0;
+            bool v0 = false, v1 = false;
+            if (walk) {
+                const uint4 w = philox_call(ps, call, A.key0, A.key1);
+                call++;
+                pos += 1 + gap_count_t<SMT>(tabs + toff, inv, w.x);
+                if (pos >= n_trials) {
+                    ended = true;
+                } else {
+                    const uint32_t pk = kind == N_PC1 ? (w.y < t1 ? 1u : w.y < t2 ? 3u : 2u) : 1u + __umulhi(w.y, npauli);
+                    e0 = ((ubase + uint32_t(pos >> 6) * kp + (pk - 1u)) << (6u + LK)) | ktag | uint32_t(pos & 63);
+                    v0 = true;
+                    pos += 1 + gap_count_t<SMT>(tabs + toff, inv, w.z);
+                    if (pos >= n_trials) {
+                        ended = true;
+                    } else {
+                        const uint32_t pk1 =
+                            kind == N_PC1 ? (w.w < t1 ? 1u : w.w < t2 ? 3u : 2u) : 1u + __umulhi(w.w, npauli);
+                        e1 = ((ubase + uint32_t(pos >> 6) * kp + (pk1 - 1u)) << (6u + LK)) | ktag | uint32_t(pos & 63);
+                        v1 = true;
+                    }
+                }
+            }
+            const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, v0);
+            const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, v1);
+            if (v0) {  // v1 implies v0
+                const uint32_t peers = __match_any_sync(b0, Q);
+                const uint32_t leader = uint32_t(__ffs(peers)) - 1u;
+                const uint32_t n = uint32_t(__popc(b0 & peers) + __popc(b1 & peers));
+                uint32_t idx = uint32_t(__popc(b0 & peers & lt) + __popc(b1 & peers & lt));
+                uint32_t base = 0;
+                if (lane == leader) base = atomicAdd(&C.cnt[Q & (kFlowSlots - 1u)], n);
+                idx += __shfl_sync(peers, base, int(leader));
+                if (idx < cap) {
+                    S.arena[(uq + idx) & amask] = e0;
+                } else {
+                    pend0 = e0;
+                    npend = 1;
+                }
+                if (v1) {
+                    idx++;
+                    if (idx < cap) {
+                        S.arena[(uq + idx) & amask] = e1;
+                    } else if (npend) {
+                        pend1 = e1;
+                        npend = 2;
+                    } else {
+                        pend0 = e1;
+                        npend = 1;
+                    }
+                }
+            }
+        }
+        // a stream whose walk ended and whose events are all stored or
+        // applied is reported to its step
+        const bool complete = have && ended && npend == 0;
+        const uint32_t cm = __ballot_sync(0xFFFFFFFFu, complete);
+        if (complete) {
+            __threadfence_block();  // its events precede the count
+            const uint32_t peers = __match_any_sync(cm, Q);
+            const uint32_t leader = uint32_t(__ffs(peers)) - 1u;
+            if (lane == leader) atomicAdd(&C.done[Q & (kFlowSlots - 1u)], uint32_t(__popc(peers)));
+            have = false;
+            live = false;
+            ended = false;
+        }
+        if (wm | cm) {
+            waiting = false;
+            continue;
+        }
+        // nothing to walk: every lane is done, gated or holding events
+        if (!__any_sync(0xFFFFFFFFu, have)) return;
+        if (!waiting) {
+            t_wait = uint32_t(globaltimer_ns());
+            waiting = true;
+        } else if (uint32_t(globaltimer_ns()) - t_wait > uint32_t(kWaitNs)) {
+            if (lane == 0) {
+                C.abort = 1u;
+                atomicOr(A.status, 1u);
+            }
+            return;
+        }
+        __nanosleep(64);
+    }
+}
+
+__device__ __forceinline__ void flow_bar(uint32_t nthreads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Applier warps: steps in CTA order.
+template <int K>
+__device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S, FlowCtl &C, uint32_t nt,
+                                           uint32_t nv_last) {
+    constexpr uint32_t LK = FlowLog<K>::v;
+    const uint32_t nthr = blockDim.x - 32u * A.walkers;
+    const uint32_t at = threadIdx.x - 32u * A.walkers;
+    const uint32_t amask = A.arena - 1u, mask = A.window_mask;
+    const uint32_t obs_row = A.window_mask + 1u;
+    const uint2 *ev2 = reinterpret_cast<const uint2 *>(A.ev_ent);
+    uint64_t U = 0;
+    for (uint32_t T = 0; T < nt; T++) {
+        const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(T) * gridDim.x;
+        const uint64_t col0 = tile * uint64_t(K);
+        const uint32_t nv = T == nt - 1u ? nv_last : uint32_t(K);
+        for (uint32_t q = 0; q < A.n_steps; q++) {
+            const uint32_t Q = T * A.n_steps + q;
+            const uint4 st = __ldg(A.steps + q);
+            const uint32_t need = (st.y - st.x) << LK;
+            const uint32_t slot = Q & (kFlowSlots - 1u);
+            // thread 0 waits for the step's streams and decides for all
+            // appliers whether they go on (one value read after the barrier,
+            // so every applier thread leaves or none does)
+            if (at == 0) {
+                uint32_t stop = ld_shared_volatile(&C.abort);
+                if (!stop && ld_shared_volatile(&C.done[slot]) != need) {
+                    const uint64_t t0 = globaltimer_ns();
+                    while (ld_shared_volatile(&C.done[slot]) != need) {
+                        if (ld_shared_volatile(&C.abort)) {
+                            stop = 1u;
+                            break;
+                        }
+                        if (globaltimer_ns() - t0 > kWaitNs) {
+                            C.abort = 1u;
+                            atomicOr(A.status, 1u);
+                            stop = 1u;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                }
+                C.app_stop = stop;
+            }
+            flow_bar(nthr);
+            if (C.app_stop) return;
+            __threadfence_block();  // the walkers' events precede the reads below
+            const uint32_t n = min(ld_shared_volatile(&C.cnt[slot]), S.scap[q]);
+            const uint32_t u0 = uint32_t(U);
+            for (uint32_t e = at; e < n; e += nthr * kFlowApplyBatch) {
+                uint32_t wv[kFlowApplyBatch];
+                uint2 v[kFlowApplyBatch];
+#pragma unroll
+                for (uint32_t j = 0; j < kFlowApplyBatch; j++) {
+                    const uint32_t i = e + j * nthr;
+                    wv[j] = i < n ? S.arena[(u0 + i) & amask] : 0u;
+                }
+#pragma unroll
+                for (uint32_t j = 0; j < kFlowApplyBatch; j++)
+                    v[j] = e + j * nthr < n ? __ldg(ev2 + (wv[j] >> (6u + LK))) : make_uint2(kEvNone, kEvNone);
+#pragma unroll
+                for (uint32_t j = 0; j < kFlowApplyBatch; j++) flow_put<K>(A, S.ring, wv[j], v[j]);
+            }
+            flow_bar(nthr);
+            // detectors [flush_lo, flush_hi) are final: write and clear them
+            const uint32_t nd = st.w - st.z;
+            bool vec_done = false;
+            if constexpr (K % 2 == 0) {
+                if (A.vec_out) {
+                    vec_done = true;
+                    constexpr uint32_t H = uint32_t(K) / 2u;
+                    for (uint32_t i = at; i < nd * H; i += nthr) {
+                        const uint32_t d = st.z + i / H, k = 2u * (i % H);
+                        ulonglong2 *r = reinterpret_cast<ulonglong2 *>(S.ring + size_t(d & mask) * K + k);
+                        ulonglong2 v = *r;
+                        *r = make_ulonglong2(0ull, 0ull);
+                        if (k >= nv) continue;
+                        const uint64_t col = col0 + k;
+                        if (col == A.n_cols - 1) v.x &= A.last_mask;
+                        if (col + 1 == A.n_cols - 1) v.y &= A.last_mask;
+                        unsigned long long *out =
+                            reinterpret_cast<unsigned long long *>(A.det + uint64_t(d) * A.n_cols + col);
+                        if (k + 1 < nv) __stcs(reinterpret_cast<ulonglong2 *>(out), v);
+                        else __stcs(out, v.x);
+                    }
+                }
+            }
+            if (!vec_done) {
+                for (uint32_t i = at; i < nd * uint32_t(K); i += nthr) {
+                    const uint32_t d = st.z + i / uint32_t(K), k = i % uint32_t(K);
+                    uint64_t *r = S.ring + size_t(d & mask) * K + k;
+                    uint64_t v = *r;
+                    *r = 0ull;
+                    if (k >= nv) continue;
+                    const uint64_t col = col0 + k;
+                    if (col == A.n_cols - 1) v &= A.last_mask;
+                    __stcs(reinterpret_cast<unsigned long long *>(A.det + uint64_t(d) * A.n_cols + col), v);
+                }
+            }
+            if (q == A.n_steps - 1u) {
+                uint64_t *ob = S.ring + size_t(obs_row) * K;
+                for (uint32_t i = at; i < A.n_obs * uint32_t(K); i += nthr) {
+                    const uint32_t o = i / uint32_t(K), k = i % uint32_t(K);
+                    uint64_t v = ob[i];
+                    ob[i] = 0ull;
+                    if (k >= nv) continue;
+                    const uint64_t col = col0 + k;
+                    if (col == A.n_cols - 1) v &= A.last_mask;
+                    A.obs[uint64_t(o) * A.n_cols + col] = v;
+                }
+            }
+            flow_bar(nthr);
+            U += S.scap[q];
+            if (at == 0) {
+                C.done[slot] = 0u;
+                C.cnt[slot] = 0u;
+                __threadfence_block();
+                *reinterpret_cast<volatile unsigned long long *>(&C.u_applied) = U;
+                *reinterpret_cast<volatile uint32_t *>(&C.applied) = Q + 1u;
+            }
+        }
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(1024, 1) flow_kernel(const FlowArgs A) {
+    extern __shared__ __align__(128) uint64_t smem[];
+    __shared__ FlowCtl C;
+    if (uint64_t(blockIdx.x) >= A.n_tiles) return;
+    const FlowSmem S = flow_layout(smem, A, K);
+    const uint32_t tid = threadIdx.x, T_ = blockDim.x;
+    const uint32_t W = A.window_mask + 1u;
+    for (uint32_t i = tid; i < (W + A.n_obs) * uint32_t(K); i += T_) S.ring[i] = 0ull;
+    for (uint32_t i = tid; i < A.smem_tables * kTableWords; i += T_) S.stab[i] = __ldg(A.tables + i);
+    // region capacities: mean + 6 sigma + 64 of the step's events over K
+    // chunks (Poisson-like counts), at most the arena; steps without items
+    // hold none
+    for (uint32_t i = tid; i < A.n_steps; i += T_) {
+        const uint4 st = __ldg(A.steps + i);
+        const float mu = __ldg(A.step_events + i) * float(K);
+        uint32_t cap = A.test_cap ? A.test_cap : uint32_t(ceilf(mu + 6.0f * sqrtf(mu) + 64.0f));
+        cap = st.y > st.x ? min(cap, A.arena) : 0u;
+        S.send[i] = st.y;
+        S.scap[i] = cap;
+    }
+    if (tid < kFlowSlots) {
+        C.done[tid] = 0u;
+        C.cnt[tid] = 0u;
+    }
+    if (tid == 0) {
+        C.next = 0ull;
+        C.u_applied = 0ull;
+        C.applied = 0u;
+        C.abort = 0u;
+        C.app_stop = 0u;
+    }
+    __syncthreads();
+    // region offsets: exclusive prefix sum of the capacities (warp 0)
+    if (tid < 32) {
+        const uint32_t per = (A.n_steps + 31u) / 32u, lo = tid * per, hi = min(A.n_steps, lo + per);
+        uint32_t sum = 0;
+        for (uint32_t i = lo; i < hi; i++) sum += S.scap[i];
+        uint32_t incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (int(tid) >= o) incl += v;
+        }
+        uint32_t run = incl - sum;
+        for (uint32_t i = lo; i < hi; i++) {
+            S.soff[i] = run;
+            run += S.scap[i];
+        }
+        if (tid == 31) S.soff[A.n_steps] = incl;
+    }
+    const uint64_t G = gridDim.x;
+    const uint32_t nt = uint32_t((A.n_tiles - blockIdx.x + G - 1) / G);
+    const uint64_t last = uint64_t(blockIdx.x) + uint64_t(nt - 1) * G;
+    const uint64_t rem = A.n_cols - last * K;
+    const uint32_t nv_last = rem < uint64_t(K) ? uint32_t(rem) : uint32_t(K);
+    __syncthreads();
+    if ((tid >> 5) >= A.walkers) flow_apply<K>(A, S, C, nt, nv_last);
+    else if (A.smem_tables) flow_walk<K, true>(A, S, C, nt, nv_last, S.stab);
+    else flow_walk<K, false>(A, S, C, nt, nv_last, A.tables);
+}
+
+// ------------------------------------------------------------------- host
+
+static int env_int_flow(const char *name, int dflt) {
+    const char *v = std::getenv(name);
+    return (v && *v) ? std::atoi(v) : dflt;
+}
+
+static size_t flow_fixed_bytes(const SigProgram &G, int sched, uint32_t n_obs, int K) {
+    const SigSchedule &S = G.sched[sched];
+    return flow_ring_bytes(S.window, n_obs, K) + flow_step_bytes(uint32_t(S.steps.size()));
+}
+
+bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int appliers, size_t budget, FlowShape *out) {
+    const SigProgram &G = c->sig;
+    if (!G.ok || sched < 0 || size_t(sched) >= G.sched.size()) return false;
+    const SigSchedule &S = G.sched[sched];
+    if (S.lag || S.steps.empty() || S.steps.size() > kFlowMaxSteps || S.step_events.size() != S.steps.size())
+        return false;
+    if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16) return false;
+    if (threads < 64 || threads > 1024 || threads % 32 || appliers < 1 || appliers >= threads / 32) return false;
+    // event words: slot << (6 + log2 K) | chunk << 6 | lane must fit 32 bits
+    if (uint64_t(G.n_event_slots) * 64u * uint64_t(K) > (uint64_t(1) << 32)) return false;
+    const size_t fixed = flow_fixed_bytes(G, sched, uint32_t(c->n_obs), K);
+    const size_t tabs = G.tables.size() * 4;
+    auto arena_for = [&](size_t used) {
+        uint32_t a = kFlowMaxArena;
+        while (a >= kFlowMinArena && used + size_t(a) * 4 > budget) a >>= 1;
+        return a;
+    };
+    FlowShape s;
+    s.sched = sched;
+    s.K = K;
+    s.threads = threads;
+    s.appliers = appliers;
+    // gap tables in shared memory when that still leaves an arena of 8192
+    // entries, else read through L1
+    s.smem_tables = arena_for(fixed + tabs) >= 8192u;
+    s.arena = arena_for(fixed + (s.smem_tables ? tabs : 0));
+    const int aforce = env_int_flow("TMCS_FLOW_ARENA", 0);  // tuning/testing knob: arena entries
+    if (aforce >= int(kFlowMinArena) && !(aforce & (aforce - 1)) && uint32_t(aforce) < s.arena)
+        s.arena = uint32_t(aforce);
+    if (s.arena < kFlowMinArena) return false;
+    s.smem = fixed + (s.smem_tables ? tabs : 0) + size_t(s.arena) * 4;
+    if (s.smem > budget) return false;
+    *out = s;
+    return true;
+}
+
+template <int K>
+static cudaError_t flow_go(const FlowArgs &a, const FlowShape &s, int sms, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(flow_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(flow_kernel<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             int(cudaSharedmemCarveoutMaxShared));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flow_kernel<K>, s.threads, s.smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(a.n_tiles, uint64_t(sms) * uint64_t(per_sm)));
+    // steps are counted per CTA in 32 bits
+    if ((a.n_tiles / grid + 1) * uint64_t(a.n_steps) >= (uint64_t(1) << 31)) return cudaErrorInvalidValue;
+    flow_kernel<K><<<unsigned(grid), s.threads, s.smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t flow_launch(const SigProgram &G, uint32_t n_obs, const DeviceSig *ds, const FlowShape &s,
+                        const FlowCall &call, int sms, cudaStream_t st) {
+    if (!ds || s.sched < 0 || size_t(s.sched) >= G.sched.size() || !ds->step_events[s.sched])
+        return cudaErrorInvalidValue;
+    const SigSchedule &S = G.sched[s.sched];
+    FlowArgs a{};
+    a.noise = ds->noise;
+    a.tables = ds->tables;
+    a.item_rec = reinterpret_cast<const uint4 *>(ds->items[s.sched]);
+    a.steps = reinterpret_cast<const uint4 *>(ds->steps[s.sched]);
+    a.step_events = ds->step_events[s.sched];
+    a.ev_ent = ds->ev_ent;
+    a.n_steps = uint32_t(S.steps.size());
+    a.n_items = uint32_t(S.items.size() / 2);
+    a.window_mask = S.window - 1u;
+    a.n_obs = n_obs;
+    a.arena = s.arena;
+    a.test_cap = uint32_t(std::max(0, env_int_flow("TMCS_TEST_FLOW_CAP", 0)));
+    a.smem_tables = s.smem_tables ? uint32_t(G.tables.size() / kTableWords) : 0u;
+    a.walkers = uint32_t(s.threads / 32 - s.appliers);
+    a.key0 = call.key0;
+    a.key1 = call.key1;
+    a.first_chunk = call.first_chunk;
+    a.vec_out = (reinterpret_cast<uintptr_t>(call.det) % 16 == 0 && call.n_cols % 2 == 0) ? 1u : 0u;
+    a.n_cols = call.n_cols;
+    a.last_mask = call.last_mask;
+    a.n_tiles = (call.n_cols + uint64_t(s.K) - 1) / uint64_t(s.K);
+    a.det = call.det;
+    a.obs = call.obs;
+    a.status = call.status;
+    switch (s.K) {
+    case 16: return flow_go<16>(a, s, sms, st);
+    case 8: return flow_go<8>(a, s, sms, st);
+    case 4: return flow_go<4>(a, s, sms, st);
+    case 2: return flow_go<2>(a, s, sms, st);
+    default: return flow_go<1>(a, s, sms, st);
+    }
+}
+
+}  // namespace tmcs

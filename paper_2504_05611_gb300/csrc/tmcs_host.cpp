@@ -1034,6 +1034,112 @@ int build_measurement_program(tmcs_circuit *c) {
     return TMCS_OK;
 }
 
+// Detector error model columns (Methods "Decoding"): single faults in the
+// order of tmcs_fault_count, each read from the event-signature table the
+// samplers apply, merged by signature. Faults of one noise unit are mutually
+// exclusive and units are independent, so a column fires (an odd number of
+// its faults occur) with probability (1 - prod_u (1 - 2 P_u)) / 2, P_u the
+// summed probability of the unit's faults in the column.
+namespace {
+struct VecHash {
+    size_t operator()(const std::vector<uint32_t> &v) const {
+        uint64_t h = 0x9E3779B97F4A7C15ull ^ v.size();
+        for (uint32_t x : v) h = (h ^ x) * 0x100000001B3ull;
+        return size_t(h ^ (h >> 29));
+    }
+};
+}  // namespace
+
+// Output list of one event slot, as sorted ids (detector, or kSigObsFlag |
+// observable); empty if the event flips nothing.
+static void slot_outputs(const SigProgram &G, size_t slot, std::vector<uint32_t> &w) {
+    w.clear();
+    const uint32_t w0 = G.ev_ent[2 * slot], w1 = G.ev_ent[2 * slot + 1];
+    if (w0 == kEvNone) return;
+    if (w0 & kEvOverflow) {
+        w.assign(G.ev_ent.begin() + (w0 & ~kEvOverflow), G.ev_ent.begin() + (w0 & ~kEvOverflow) + w1);
+    } else {
+        w.push_back(w0);
+        if (w1 != kEvNone) w.push_back(w1);
+    }
+    for (uint32_t &e : w) e = (e & (1u << 29)) ? (kSigObsFlag | (e & 0x1FFFFFFFu)) : e;
+    std::sort(w.begin(), w.end());
+}
+
+static void build_dem(const tmcs_circuit *c) {
+    const SigProgram &G = c->sig;
+    std::unordered_map<std::vector<uint32_t>, uint32_t, VecHash> index;
+    std::vector<std::vector<uint32_t>> cols;
+    std::vector<double> prod;
+    std::vector<uint64_t> nf;
+    struct UnitCol {
+        std::vector<uint32_t> sig;
+        double p;
+        uint32_t n;
+    };
+    std::vector<UnitCol> unit;  // this unit's non-empty faults, by signature
+    std::vector<uint32_t> w;
+    for (uint32_t di = 0; di < G.noise.size(); di++) {
+        const NoiseDesc &nd = G.noise[di];
+        const uint32_t KP = sig_paulis(nd.kind);
+        const double p = c->ops[nd.op_index].p;
+        for (uint32_t u = 0; u < nd.n_units; u++) {
+            unit.clear();
+            for (uint32_t k = 1; k <= KP; k++) {
+                slot_outputs(G, size_t(G.ev_base[di]) + size_t(u) * KP + (k - 1), w);
+                if (w.empty()) continue;
+                double pf = p / double(KP);
+                if (nd.kind == N_PC1) {
+                    // the sampled split: X below t1, Y in [t1, t2), Z from t2
+                    // (Pauli index 1 = X, 3 = Y, 2 = Z)
+                    const double lo = k == 1 ? 0.0 : k == 3 ? double(nd.t1) : double(nd.t2);
+                    const double hi = k == 1 ? double(nd.t1) : k == 3 ? double(nd.t2) : 4294967296.0;
+                    pf = p * (hi - lo) / 4294967296.0;
+                }
+                bool merged = false;
+                for (UnitCol &e : unit)
+                    if (e.sig == w) {
+                        e.p += pf;
+                        e.n++;
+                        merged = true;
+                        break;
+                    }
+                if (!merged) unit.push_back({w, pf, 1u});
+            }
+            for (const UnitCol &e : unit) {
+                auto it = index.find(e.sig);
+                uint32_t col;
+                if (it == index.end()) {
+                    col = uint32_t(cols.size());
+                    index.emplace(e.sig, col);
+                    cols.push_back(e.sig);
+                    prod.push_back(1.0);
+                    nf.push_back(0);
+                } else {
+                    col = it->second;
+                }
+                prod[col] *= 1.0 - 2.0 * e.p;
+                nf[col] += e.n;
+            }
+        }
+    }
+    // canonical order: columns sorted by their entry lists
+    std::vector<uint32_t> ord(cols.size());
+    for (size_t i = 0; i < ord.size(); i++) ord[i] = uint32_t(i);
+    std::sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) { return cols[a] < cols[b]; });
+    c->dem_off.assign(1, 0);
+    c->dem_ent.clear();
+    c->dem_p.clear();
+    c->dem_nf.clear();
+    for (uint32_t i : ord) {
+        c->dem_ent.insert(c->dem_ent.end(), cols[i].begin(), cols[i].end());
+        c->dem_off.push_back(c->dem_ent.size());
+        c->dem_p.push_back((1.0 - prod[i]) / 2.0);
+        c->dem_nf.push_back(nf[i]);
+    }
+    c->dem_built = true;
+}
+
 }  // namespace tmcs
 
 using namespace tmcs;
@@ -1191,6 +1297,33 @@ int tmcs_circuit_stats(const tmcs_circuit *c, tmcs_stats *out) {
         for (const SigStep &st : S.steps)
             out->sig_max_step_items = std::max<uint64_t>(out->sig_max_step_items, st.item_end - st.item_begin);
     }
+    return TMCS_OK;
+}
+
+int tmcs_dem_columns(const tmcs_circuit *c, uint64_t *n_cols, uint64_t *n_entries, uint64_t *col_off,
+                     uint32_t *entries, double *col_p, uint64_t *col_faults) {
+    if (!c || !n_cols || !n_entries) return fail(TMCS_E_INVALID, "NULL argument");
+    const SigProgram &G = c->sig;
+    if (!G.ok) return fail(TMCS_E_INVALID, "no event-signature table: " + G.why);
+    std::lock_guard<std::mutex> lock(c->mu);
+    if (!c->dem_built) {
+        try {
+            build_dem(c);
+        } catch (const std::bad_alloc &) {
+            return fail(TMCS_E_OOM, "detector error model: out of host memory");
+        }
+    }
+    const uint64_t nc = c->dem_p.size(), ne = c->dem_ent.size();
+    const bool fill = col_off || entries || col_p || col_faults;
+    if (fill && (*n_cols < nc || *n_entries < ne))
+        return fail(TMCS_E_BUFFER, "column buffers smaller than the model (" + std::to_string(nc) + " columns, " +
+                                       std::to_string(ne) + " entries)");
+    *n_cols = nc;
+    *n_entries = ne;
+    if (col_off) std::memcpy(col_off, c->dem_off.data(), (nc + 1) * sizeof(uint64_t));
+    if (entries && ne) std::memcpy(entries, c->dem_ent.data(), ne * sizeof(uint32_t));
+    if (col_p && nc) std::memcpy(col_p, c->dem_p.data(), nc * sizeof(double));
+    if (col_faults && nc) std::memcpy(col_faults, c->dem_nf.data(), nc * sizeof(uint64_t));
     return TMCS_OK;
 }
 

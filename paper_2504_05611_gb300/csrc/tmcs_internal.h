@@ -127,7 +127,32 @@ struct DeviceSig {
     const uint32_t *tables = nullptr;
     const uint32_t *items[kSigMaxSchedules] = {};  // item records of each schedule
     const SigStep *steps[kSigMaxSchedules] = {};
+    const float *step_events[kSigMaxSchedules] = {};
     const uint32_t *ev_ent = nullptr;
+};
+
+// ------------------------------------------ decoupled event-signature kernel
+//
+// flow_kernel (tmcs_flow.cu): walker warps append events to a shared-memory
+// arena, applier warps apply whole steps to the detector ring. Runs barrier
+// schedules (lag 0) of at most kFlowMaxSteps steps.
+constexpr uint32_t kFlowMaxSteps = 1024;
+
+struct FlowShape {
+    int sched = 0;            // barrier schedule of the signature program
+    int K = 4;                // chunks per tile
+    int threads = 1024;
+    int appliers = 8;         // applier warps (the other warps walk)
+    uint32_t arena = 0;       // event arena entries (power of two)
+    bool smem_tables = false; // gap tables staged in shared memory
+    size_t smem = 0;          // dynamic shared memory
+};
+
+struct FlowCall {
+    uint32_t key0 = 0, key1 = 0, first_chunk = 0;
+    uint64_t n_cols = 0, last_mask = 0;
+    uint64_t *det = nullptr, *obs = nullptr;
+    uint32_t *status = nullptr;
 };
 
 // Per-device scratch of the library: a status word that kernels set when a
@@ -175,6 +200,9 @@ struct SigSchedule {
     // (units - 1) << 16 | descriptor << 22 (descriptor < 1024, table < 8192).
     std::vector<uint32_t> item_rec;
     std::vector<SigStep> steps;
+    // Expected events per 64-shot chunk of each step (sum over its items of
+    // 64 x units x p); the decoupled kernel sizes its event regions by it.
+    std::vector<float> step_events;
 };
 
 struct SigProgram {
@@ -197,6 +225,7 @@ struct SigProgram {
     // entry or kEvNone. An entry is observable flag << 29 | output index.
     std::vector<uint32_t> ev_base;   // per descriptor: index of its first event slot
     std::vector<uint32_t> ev_ent;
+    uint32_t n_event_slots = 0;      // event slots (the overflow lists follow them in ev_ent)
     double build_seconds = 0;
 };
 
@@ -242,6 +271,12 @@ struct tmcs_circuit {
     // event-signature program (built with the circuit; ok = false if unusable)
     tmcs::SigProgram sig;
     mutable std::map<int, tmcs::DeviceSig> dev_sig;
+    // detector error model columns, built on the first tmcs_dem_columns call
+    mutable bool dem_built = false;
+    mutable std::vector<uint64_t> dem_off;   // column c's entries: dem_ent[dem_off[c] .. dem_off[c+1])
+    mutable std::vector<uint32_t> dem_ent;   // detector id, or 0x80000000 | observable id
+    mutable std::vector<double> dem_p;       // probability that an odd number of its faults occurs
+    mutable std::vector<uint64_t> dem_nf;    // single faults merged into the column
     mutable std::mutex mu;
     mutable std::map<int, tmcs::DeviceProgram> dev;
 };
@@ -262,5 +297,14 @@ int table_for_p(std::vector<uint32_t> &tables, std::vector<double> &table_p, dou
 
 // Device side (tmcs_sample.cu)
 void free_device_programs(tmcs_circuit *c);
+
+// Decoupled event-signature kernel (tmcs_flow.cu). flow_shape fills *out for
+// the given schedule, chunks per tile, CTA size and applier warps if that
+// shape fits `budget` bytes of dynamic shared memory.
+bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int appliers, size_t budget, FlowShape *out);
+#ifdef __CUDACC__
+cudaError_t flow_launch(const SigProgram &G, uint32_t n_obs, const DeviceSig *ds, const FlowShape &s,
+                        const FlowCall &call, int sms, cudaStream_t st);
+#endif
 
 }  // namespace tmcs

@@ -26,74 +26,12 @@
 #include <string>
 #include <vector>
 
+#include "tmcs_device.cuh"
 #include "tmcs_internal.h"
 
 namespace tmcs {
 
 // ------------------------------------------------------------ device code
-
-__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                                uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; r++) {
-        if (r > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-        const uint32_t n0 = hi1 ^ c1 ^ k0;
-        const uint32_t n2 = hi0 ^ c3 ^ k1;
-        c0 = n0;
-        c1 = lo1;
-        c2 = n2;
-        c3 = lo0;
-    }
-    return make_uint4(c0, c1, c2, c3);
-}
-
-// Gap of the sampling specification: G = #{g in 1..4096 : w < T[g]} for the
-// non-increasing table T (T + i holds T[i+1]). A float estimate of
-// log((w+1) 2^-32) / log(1-p) lands within one step of the count; the two
-// loops then move it to the exact count by comparing against the table, so
-// the result never depends on the estimate's rounding.
-__device__ __forceinline__ int gap_count(const uint32_t *__restrict__ T, float inv_log2, uint32_t w) {
-    const float lg = __log2f(__uint2float_rn(w) + 1.0f) - 32.0f;
-    const float est = lg * inv_log2;
-    int g = est >= float(kGapLen) ? int(kGapLen) : (est > 0.0f ? int(est) : 0);
-    // both neighbours of the estimate at once (T[kGapLen] is in bounds and
-    // used only below kGapLen); the loops run only when the estimate is off
-    const uint32_t at = __ldg(T + g), below = __ldg(T + (g > 0 ? g - 1 : 0));
-    if (g < int(kGapLen) && w < at) {
-        g++;
-        while (g < int(kGapLen) && w < __ldg(T + g)) g++;
-    } else if (g > 0 && w >= below) {
-        g--;
-        while (g > 0 && w >= __ldg(T + g - 1)) g--;
-    }
-    return g;
-}
-
-// gap_count on a table in shared memory (SMT) or global memory.
-template <bool SMT>
-__device__ __forceinline__ int gap_count_t(const uint32_t *__restrict__ T, float inv_log2, uint32_t w) {
-    if constexpr (!SMT) return gap_count(T, inv_log2, w);
-    const float lg = __log2f(__uint2float_rn(w) + 1.0f) - 32.0f;
-    const float est = lg * inv_log2;
-    int g = est >= float(kGapLen) ? int(kGapLen) : (est > 0.0f ? int(est) : 0);
-    // both neighbours of the estimate at once (a table row has more than
-    // kGapLen + 1 words, so T[kGapLen] is in bounds; it is used only below
-    // kGapLen); the correction loops run only when the estimate is off
-    const uint32_t at = T[g], below = T[g > 0 ? g - 1 : 0];
-    if (g < int(kGapLen) && w < at) {
-        g++;
-        while (g < int(kGapLen) && w < T[g]) g++;
-    } else if (g > 0 && w >= below) {
-        g--;
-        while (g > 0 && w >= T[g - 1]) g--;
-    }
-    return g;
-}
 
 struct KernelArgs {
     const Layer *layers;
@@ -131,7 +69,6 @@ struct EvUnit {
 };
 static_assert(sizeof(EvUnit) == 24, "EvUnit layout");
 
-constexpr uint64_t kWaitNs = 2000000000ull;  // bounded mbarrier waits: 2 s of wall time
 
 // ---- PTX wrappers: mbarrier + bulk asynchronous copy (TMA, 1-D)
 
@@ -169,11 +106,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 // Waits for phase `parity` of `bar`; gives up after kWaitNs of wall time.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -210,10 +142,6 @@ __device__ __forceinline__ void apply_event(uint64_t *F, const uint32_t *__restr
         if (pa & 1u) xor_bit(F, c0 & 0xFFFFu, K, k, bit);
         if (pa & 2u) xor_bit(F, c0 >> 16, K, k, bit);
     }
-}
-
-__device__ __forceinline__ uint32_t npauli_of(uint32_t kind) {
-    return kind == N_DEP2 ? 15u : kind == N_DEP1 ? 3u : 1u;
 }
 
 // Pauli index (x = bit 0, z = bit 1) of an event from its Pauli word.
@@ -954,21 +882,6 @@ __device__ __forceinline__ PipeSmem pipe_layout(uint64_t *smem, const SigArgs &A
     S.sitems = reinterpret_cast<uint4 *>(S.stab + size_t(A.smem_tables) * kTableWords);
     S.queue = reinterpret_cast<uint64_t *>(S.sitems + size_t(A.stage_items) * A.lag);
     return S;
-}
-
-__device__ __forceinline__ uint32_t ld_shared_volatile(const uint32_t *p) {
-    return *reinterpret_cast<const volatile uint32_t *>(p);
-}
-
-// 64-bit warp-aggregated counter (see grab_index).
-__device__ __forceinline__ uint64_t grab_index64(unsigned long long *ctr) {
-    const uint32_t mask = __activemask();
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t leader = uint32_t(__ffs(mask)) - 1u;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
-    base = __shfl_sync(mask, base, int(leader));
-    return uint64_t(base) + uint64_t(__popc(mask & ((1u << lane) - 1u)));
 }
 
 // Adds this warp's finished-stream counts to the step totals. All 32 lanes;
@@ -1796,11 +1709,12 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
     const size_t b_noise = align256(G.noise.size() * sizeof(NoiseDesc));
     const size_t b_tables = align256(G.tables.size() * 4);
     const size_t n_sched = G.sched.size();
-    size_t b_items[kSigMaxSchedules] = {}, b_steps[kSigMaxSchedules] = {}, b_sched = 0;
+    size_t b_items[kSigMaxSchedules] = {}, b_steps[kSigMaxSchedules] = {}, b_sev[kSigMaxSchedules] = {}, b_sched = 0;
     for (size_t k = 0; k < n_sched; k++) {
         b_items[k] = align256(G.sched[k].item_rec.size() * 4);
         b_steps[k] = align256(G.sched[k].steps.size() * sizeof(SigStep));
-        b_sched += b_items[k] + b_steps[k];
+        b_sev[k] = align256(G.sched[k].step_events.size() * sizeof(float));
+        b_sched += b_items[k] + b_steps[k] + b_sev[k];
     }
     const size_t b_ent = align256(G.ev_ent.size() * 4);
     const size_t total = std::max<size_t>(b_noise + b_tables + b_sched + b_ent, 256);
@@ -1816,11 +1730,12 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
     for (size_t i = 0; i < dn.size(); i++) dn[i].tgt_off = G.ev_base[i];
     const size_t o_noise = put(dn.data(), dn.size() * sizeof(NoiseDesc), b_noise);
     const size_t o_tables = put(G.tables.data(), G.tables.size() * 4, b_tables);
-    size_t o_items[kSigMaxSchedules] = {}, o_steps[kSigMaxSchedules] = {};
+    size_t o_items[kSigMaxSchedules] = {}, o_steps[kSigMaxSchedules] = {}, o_sev[kSigMaxSchedules] = {};
     for (size_t k = 0; k < n_sched; k++) {
         const SigSchedule &S = G.sched[k];
         o_items[k] = put(S.item_rec.data(), S.item_rec.size() * 4, b_items[k]);
         o_steps[k] = put(S.steps.data(), S.steps.size() * sizeof(SigStep), b_steps[k]);
+        o_sev[k] = put(S.step_events.data(), S.step_events.size() * sizeof(float), b_sev[k]);
     }
     const size_t o_ent = put(G.ev_ent.data(), G.ev_ent.size() * 4, b_ent);
     void *base = nullptr;
@@ -1844,6 +1759,7 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
     for (size_t k = 0; k < n_sched; k++) {
         ds.items[k] = reinterpret_cast<const uint32_t *>(b + o_items[k]);
         ds.steps[k] = reinterpret_cast<const SigStep *>(b + o_steps[k]);
+        ds.step_events[k] = reinterpret_cast<const float *>(b + o_sev[k]);
     }
     ds.ev_ent = reinterpret_cast<const uint32_t *>(b + o_ent);
     auto ins = c->dev_sig.emplace(dev, ds);
@@ -1906,7 +1822,8 @@ struct LaunchShape {
     int sms = 0;       // mode 5: SM count (grid = SMs x resident CTAs per SM)
     uint32_t qcap = 0; // mode 5: event-queue capacity
     bool smem_tables = false;  // mode 5: gap tables staged in shared memory
-    int sched = 0;     // mode 5, 6: schedule of the signature program (lag 0 for mode 5, > 0 for 6)
+    int sched = 0;     // mode 5, 6, 7: schedule of the signature program (lag 0 for mode 5, 7; > 0 for 6)
+    FlowShape flow;    // mode 7: decoupled event-signature kernel (flow_kernel)
 };
 
 static int env_int(const char *name, int dflt) {
@@ -1989,6 +1906,27 @@ static LaunchShape make_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const 
     s.smem = sig_smem_bytes(c->sig, sched, c->n_obs, K, s.qcap, s.smem_tables);
     const uint64_t n_tiles = (n_cols + K - 1) / K;
     s.tiles = std::min<uint64_t>(n_tiles, uint64_t(lim.sms) * ctas);
+    return s;
+}
+
+// Decoupled event-signature kernel (mode 7): one CTA per SM, K chunks per
+// tile, `appliers` of its warps apply steps, the others walk. mode = 0 when
+// the shape does not fit.
+static LaunchShape make_shape_flow(const tmcs_circuit *c, uint64_t n_cols, const DeviceLimits &lim, int sched, int K,
+                                   int threads, int appliers) {
+    LaunchShape s;
+    s.mode = 0;
+    if (!flow_shape(c, sched, K, threads, appliers, lim.smem_optin - 1024, &s.flow)) return s;
+    s.mode = 7;
+    s.sched = sched;
+    s.K = K;
+    s.threads = threads;
+    s.warps = appliers;
+    s.sms = lim.sms;
+    s.smem = s.flow.smem;
+    s.smem_tables = s.flow.smem_tables;
+    s.qcap = s.flow.arena;
+    s.tiles = std::min<uint64_t>((n_cols + K - 1) / K, uint64_t(lim.sms));
     return s;
 }
 
@@ -2084,6 +2022,19 @@ static cudaError_t launch_pipe(const SigArgs &a, const LaunchShape &s, cudaStrea
 
 static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream_t st,
                           const DeviceSig *ds = nullptr, const SigProgram *G = nullptr, uint32_t n_obs = 0) {
+    if (s.mode == 7) {
+        if (!ds || !G) return cudaErrorInvalidValue;
+        FlowCall call;
+        call.key0 = a0.key0;
+        call.key1 = a0.key1;
+        call.first_chunk = a0.first_chunk;
+        call.n_cols = a0.n_cols;
+        call.last_mask = a0.last_mask;
+        call.det = a0.det;
+        call.obs = a0.obs;
+        call.status = a0.status;
+        return flow_launch(*G, n_obs, ds, s.flow, call, s.sms, st);
+    }
     if (s.mode == 5 || s.mode == 6) {
         if (!ds || !G || s.sched < 0 || size_t(s.sched) >= G->sched.size()) return cudaErrorInvalidValue;
         const SigSchedule &S = G->sched[s.sched];
@@ -2189,6 +2140,17 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
                     if (sig_shape_fits(cs, lim)) cands.push_back(cs);
                 }
             }
+    // decoupled kernel: every barrier schedule x chunks per tile x applier
+    // warps, 1024 threads
+    if (ds)
+        for (int sched = 0; sched < int(c->sig.sched.size()); sched++) {
+            if (c->sig.sched[sched].lag) continue;
+            for (int K = 1; K <= 8; K *= 2)
+                for (int app : {4, 8}) {
+                    const LaunchShape cs = make_shape_flow(c, n_cols, lim, sched, K, 1024, app);
+                    if (cs.mode == 7) cands.push_back(cs);
+                }
+        }
     // With a signature program the frame kernels are compared through their
     // heuristic shape only (they lost to kernel 4 on every measured
     // workload); without one, every feasible frame shape is timed.
@@ -2221,7 +2183,7 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
         const uint64_t cols = std::min<uint64_t>(n_cols, uint64_t(4) * lim.sms * per_tile);
         if (cols / per_tile < uint64_t(lim.sms)) continue;
         LaunchShape s = full;
-        if (s.mode != 5) s.tiles = (cols + per_tile - 1) / per_tile;
+        if (s.mode != 5 && s.mode != 7) s.tiles = (cols + per_tile - 1) / per_tile;
         KernelArgs t = a;
         t.n_cols = cols;
         t.last_mask = ~uint64_t(0);
@@ -2251,7 +2213,7 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
     DeviceProgram &mdp = c->dev[device];
     mdp.tuned_mode = chosen.mode;
     mdp.tuned_K = chosen.K;
-    mdp.tuned_warps = chosen.warps;
+    mdp.tuned_warps = chosen.warps;  // mode 7: applier warps
     mdp.tuned_group = chosen.group;
     mdp.tuned_threads = chosen.threads;
     mdp.tuned_sched = chosen.sched;
@@ -2262,6 +2224,20 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
 // leaves room for two CTAs per SM and still gives every SM two tiles.
 static LaunchShape choose_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const DeviceLimits &lim) {
     const int kcap = env_int("TMCS_TILE_K", 0);
+    if (env_int("TMCS_KERNEL", 0) == 7) {
+        // forced decoupled kernel: TMCS_SIG_SCHED picks among the barrier
+        // schedules, TMCS_TILE_K the chunks per tile (default 4),
+        // TMCS_FLOW_APPLIERS the applier warps (default 8), TMCS_THREADS the
+        // CTA size (default 1024); mode 0 if that shape does not fit
+        int n_barrier = 0;
+        while (n_barrier < int(c->sig.sched.size()) && !c->sig.sched[n_barrier].lag) n_barrier++;
+        const int sched = std::min(std::max(env_int("TMCS_SIG_SCHED", 0), 0), std::max(n_barrier - 1, 0));
+        int K = kcap > 0 ? std::min(kcap, 16) : 4;
+        while (K > 1 && (K & (K - 1))) K--;
+        const int tforce = env_int("TMCS_THREADS", 0);
+        const int threads = (tforce >= 64 && tforce <= 1024 && tforce % 32 == 0) ? tforce : 1024;
+        return make_shape_flow(c, n_cols, lim, sched, K, threads, env_int("TMCS_FLOW_APPLIERS", 8));
+    }
     // tuning/testing knobs: TMCS_SIG_SCHED = schedule index among the barrier
     // schedules (0 = largest ring window), or among the pipelined ones with
     // TMCS_KERNEL=6
@@ -2299,7 +2275,8 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
     if ((reinterpret_cast<uintptr_t>(det) & 7) || (reinterpret_cast<uintptr_t>(obs) & 7))
         return fail(TMCS_E_BUFFER, "output buffers must be 8-byte aligned");
     const uint64_t n_cols = (shots + 63) / 64;
-    if (first_chunk + n_cols > (uint64_t(1) << 32)) return fail(TMCS_E_INVALID, "chunk range beyond 2^32");
+    if (first_chunk >= (uint64_t(1) << 32) || n_cols > (uint64_t(1) << 32) - first_chunk)
+        return fail(TMCS_E_INVALID, "chunk range beyond 2^32");
     const DeviceProgram *dp = nullptr;
     int rc = device_program(c, &dp);
     if (rc) return rc;
@@ -2318,12 +2295,14 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
     if (!fault_mode && c->sig.ok && sig_fits(c, lim, 1) && kmode != 3 && kmode != 4) {
         if ((rc = device_sig(c, &ds))) return rc;
     }
-    if ((kmode == 5 || kmode == 6) && !ds && !fault_mode)
-        return fail(TMCS_E_INVALID, "TMCS_KERNEL=5/6: no event-signature program for this circuit (" +
+    if ((kmode == 5 || kmode == 6 || kmode == 7) && !ds && !fault_mode)
+        return fail(TMCS_E_INVALID, "TMCS_KERNEL=5/6/7: no event-signature program for this circuit (" +
                                         (c->sig.ok ? std::string("ring does not fit") : c->sig.why) + ")");
     if (kmode == 6 && ds && !c->sig.sched.back().lag)
         return fail(TMCS_E_INVALID, "TMCS_KERNEL=6: the event-signature program has no pipelined schedule");
     LaunchShape s = ds ? choose_shape_sig(c, n_cols, lim) : choose_shape(P, n_cols, lim);
+    if (ds && kmode == 7 && s.mode != 7 && !fault_mode)
+        return fail(TMCS_E_INVALID, "TMCS_KERNEL=7: the decoupled kernel's shape does not fit this circuit");
     if (ds && !sig_shape_fits(s, lim)) {  // no signature shape fits: frame kernels
         if ((kmode == 5 || kmode == 6) && !fault_mode)
             return fail(TMCS_E_INVALID, "TMCS_KERNEL=5/6: the signature kernel's shared memory does not fit");
@@ -2340,6 +2319,11 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
         if (mdp.tuned_mode == 4) s = make_shape_w(P, n_cols, mdp.tuned_K, mdp.tuned_warps, mdp.tuned_group);
         if ((mdp.tuned_mode == 5 || mdp.tuned_mode == 6) && ds)
             s = make_shape_sig(c, n_cols, lim, mdp.tuned_K, mdp.tuned_threads, mdp.tuned_sched);
+        if (mdp.tuned_mode == 7 && ds) {
+            const LaunchShape f =
+                make_shape_flow(c, n_cols, lim, mdp.tuned_sched, mdp.tuned_K, mdp.tuned_threads, mdp.tuned_warps);
+            if (f.mode == 7) s = f;
+        }
     }
     if (fault_mode) s = choose_shape(P, n_cols, lim);
     KernelArgs a{};
@@ -2391,7 +2375,8 @@ static int sample_measurements(const tmcs_circuit *c, uint64_t first_chunk, uint
     if (c->n_meas && !meas) return fail(TMCS_E_INVALID, "output buffer is NULL");
     if (reinterpret_cast<uintptr_t>(meas) & 7) return fail(TMCS_E_BUFFER, "output buffer must be 8-byte aligned");
     const uint64_t n_cols = (shots + 63) / 64;
-    if (first_chunk + n_cols > (uint64_t(1) << 32)) return fail(TMCS_E_INVALID, "chunk range beyond 2^32");
+    if (first_chunk >= (uint64_t(1) << 32) || n_cols > (uint64_t(1) << 32) - first_chunk)
+        return fail(TMCS_E_INVALID, "chunk range beyond 2^32");
     {
         std::lock_guard<std::mutex> lock(c->mu);
         int rc = build_measurement_program(const_cast<tmcs_circuit *>(c));
@@ -2784,8 +2769,11 @@ constexpr int kNoAllocMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static unsigned char *g_noalloc_addr[kNoAllocMaxDevices];  // device address of the array, per device
 
-// Device address of the array on the current device (looked up once per
-// device, with that device current).
+// Device address of the array on the current device: looked up once per
+// device, with that device current, when its status word (the first 256
+// bytes) is also cleared. Kernels only ever set bits of that word; it is
+// read and cleared by tmcs_check_device, so an expired wait of any call is
+// reported until then.
 static int noalloc_scratch(int dev, unsigned char **out) {
     if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(TMCS_E_INVALID, "device index out of range");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -2793,10 +2781,18 @@ static int noalloc_scratch(int dev, unsigned char **out) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the scratch array");
+        if ((e = cudaMemset(p, 0, kNoAllocStatusBytes)) != cudaSuccess) return cuda_fail(e, "status clear");
         g_noalloc_addr[dev] = static_cast<unsigned char *>(p);
     }
     *out = g_noalloc_addr[dev];
     return TMCS_OK;
+}
+
+// Status word in the array on device dev (nullptr before its first call).
+static uint32_t *noalloc_status(int dev) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    return reinterpret_cast<uint32_t *>(g_noalloc_addr[dev]);
 }
 
 static int sample_noalloc(const tmcs_circuit *c, uint64_t first_chunk, uint64_t shots, uint64_t seed,
@@ -2817,7 +2813,8 @@ static int sample_noalloc(const tmcs_circuit *c, uint64_t first_chunk, uint64_t 
     if ((reinterpret_cast<uintptr_t>(det) & 7) || (reinterpret_cast<uintptr_t>(obs) & 7))
         return fail(TMCS_E_BUFFER, "output buffers must be 8-byte aligned");
     const uint64_t n_cols = (shots + 63) / 64;
-    if (first_chunk + n_cols > (uint64_t(1) << 32)) return fail(TMCS_E_INVALID, "chunk range beyond 2^32");
+    if (first_chunk >= (uint64_t(1) << 32) || n_cols > (uint64_t(1) << 32) - first_chunk)
+        return fail(TMCS_E_INVALID, "chunk range beyond 2^32");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -2830,9 +2827,13 @@ static int sample_noalloc(const tmcs_circuit *c, uint64_t first_chunk, uint64_t 
         return fail(TMCS_E_INVALID, "circuit needs " + std::to_string(P.n_slots) +
                                         " frame slots; one 64-shot chunk does not fit in shared memory");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // status word starts at zero; program sections go after it
+    // program sections go after the status word (cleared at set-up)
     unsigned char *b = base + kNoAllocStatusBytes;
-    if ((e = cudaMemsetAsync(base, 0, kNoAllocStatusBytes, st)) != cudaSuccess) return cuda_fail(e, "status clear");
+    // testing knob: record an expired wait in the status word, as a kernel
+    // that gave up would, so the tests can check tmcs_check_device reports it
+    if (env_int("TMCS_TEST_NOALLOC_EXPIRED", 0) > 0 &&
+        (e = cudaMemsetAsync(base, 0x01, 1, st)) != cudaSuccess)
+        return cuda_fail(e, "status mark");
     const struct {
         const void *src;
         size_t bytes;
@@ -2909,10 +2910,14 @@ int tmcs_check_device(void) {
     if (!w) return fail(TMCS_E_OOM, "cannot allocate the device status word");
     uint32_t v = 0;
     if ((e = cudaMemcpy(&v, w, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e, "status read");
-    if (v) {
-        if ((e = cudaMemset(w, 0, 4)) != cudaSuccess) return cuda_fail(e, "status clear");
-        return fail(TMCS_E_TIMEOUT, "a kernel gave up waiting for a staged program block");
+    if (v && (e = cudaMemset(w, 0, 4)) != cudaSuccess) return cuda_fail(e, "status clear");
+    // the allocation-free entry point's own status word (in its array)
+    uint32_t v2 = 0;
+    if (uint32_t *w2 = noalloc_status(dev)) {
+        if ((e = cudaMemcpy(&v2, w2, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e, "status read");
+        if (v2 && (e = cudaMemset(w2, 0, 4)) != cudaSuccess) return cuda_fail(e, "status clear");
     }
+    if (v || v2) return fail(TMCS_E_TIMEOUT, "a kernel gave up on a bounded device-side wait");
     return TMCS_OK;
 }
 
@@ -2929,7 +2934,8 @@ int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *thread
     if (threads) *threads = dp ? dp->tuned_threads : 0;
     if (ring_window) {
         const int k = dp ? dp->tuned_sched : 0;
-        *ring_window = (dp && (dp->tuned_mode == 5 || dp->tuned_mode == 6) && size_t(k) < c->sig.sched.size())
+        *ring_window = (dp && (dp->tuned_mode == 5 || dp->tuned_mode == 6 || dp->tuned_mode == 7) &&
+                        size_t(k) < c->sig.sched.size())
                            ? int(c->sig.sched[k].window)
                            : 0;
     }

@@ -147,6 +147,7 @@ static std::string validate_signature_program(const SigProgram &G, uint64_t D, u
         const uint32_t W = S.window;
         if (W < 256 || (W & (W - 1)) || S.lag > uint32_t(kSigMaxLag) || (S.lag && W > 16384)) return "schedule shape";
         if (S.item_rec.size() != 4 * n_items || S.steps.empty()) return "schedule size";
+        if (S.step_events.size() != S.steps.size()) return "step event counts";
         std::vector<uint64_t> lo(n_items), hi(n_items);
         for (size_t k = 0; k < n_items; k++) {
             const uint32_t di = S.items[2 * k], sg = S.items[2 * k + 1];
@@ -418,6 +419,7 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
                 return TMCS_OK;
             }
         }
+        G.n_event_slots = uint32_t(slots);
         G.ev_ent.assign(2 * slots, kEvNone);
         std::vector<uint32_t> v;
         for (uint32_t di = 0; di < G.noise.size(); di++) {
@@ -567,6 +569,13 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
         for (size_t k = 0; k < n_items; k++) {
             S.items[2 * k] = items[2 * perm[k]];
             S.items[2 * k + 1] = items[2 * perm[k] + 1];
+        }
+        // expected events per chunk of each step: 64 trials per unit at the
+        // op's probability (the decoupled kernel sizes its event regions)
+        for (const SigStep &st : S.steps) {
+            double ev = 0;
+            for (uint32_t k = st.item_begin; k < st.item_end; k++) ev += 64.0 * cost(perm[k]);
+            S.step_events.push_back(float(ev));
         }
         // device item records (the walk reads one 16-byte record per stream)
         for (size_t k = 0; k < n_items; k++) {

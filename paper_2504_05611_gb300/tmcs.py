@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
         L.tmcs_fault_signatures.argtypes = [P, U64, U64, P, P, P]
         L.tmcs_sample_measurements.argtypes = [P, U64, U64, U64, P, P]
         L.tmcs_fault_outputs.argtypes = [P, U64, P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
+        L.tmcs_dem_columns.argtypes = [P, ctypes.POINTER(U64), ctypes.POINTER(U64), P, P, P, P]
         L.tmcs_launch_shape.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
         L.tmcs_measure_peaks.argtypes = [P]
         L.tmcs_server_open.argtypes = [P, ctypes.POINTER(P)]
@@ -114,7 +115,8 @@ def lib() -> ctypes.CDLL:
                   "tmcs_debug_gap_table", "tmcs_check_device", "tmcs_sample_noalloc", "tmcs_server_open",
                   "tmcs_server_submit", "tmcs_server_poll", "tmcs_server_fetch", "tmcs_server_release",
                   "tmcs_server_get_stats", "tmcs_server_close", "tmcs_fault_count", "tmcs_fault_signatures",
-                  "tmcs_sample_measurements", "tmcs_fault_outputs", "tmcs_launch_shape", "tmcs_measure_peaks"):
+                  "tmcs_sample_measurements", "tmcs_fault_outputs", "tmcs_launch_shape", "tmcs_measure_peaks",
+                  "tmcs_dem_columns"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -212,33 +214,25 @@ def tmcs_fault_signatures(handle: int, first_fault: int, n_faults: int, det, obs
                                        _dev_ptr(obs), _stream_ptr(stream)))
 
 
-def dem_columns(sampler: "Sampler", slice_faults: int = 1 << 20):
-    """Distinct non-empty (detector set, observable set) signatures of all
-    single faults, from tmcs_fault_signatures on the GPU; returns them as a
-    set of (detector bytes, observable bytes) keys."""
-    import torch
-    n = tmcs_fault_count(sampler.handle)
-    info = sampler.info
-    out = set()
-    zero_d = bytes((info["n_det"] + 7) // 8)
-    zero_o = bytes((info["n_obs"] + 7) // 8)
-    for f0 in range(0, n, slice_faults):
-        m = min(slice_faults, n - f0)
-        cols = (m + 63) // 64
-        det = torch.empty((info["n_det"], cols), dtype=torch.int64, device="cuda")
-        obs = torch.empty((max(info["n_obs"], 1), cols), dtype=torch.int64, device="cuda")
-        tmcs_fault_signatures(sampler.handle, f0, m, det, obs if info["n_obs"] else None)
-        d = np.unpackbits(det.cpu().numpy().view(np.uint8).reshape(info["n_det"], -1), axis=1,
-                          bitorder="little")[:, :m]
-        o = np.unpackbits(obs.cpu().numpy().view(np.uint8).reshape(max(info["n_obs"], 1), -1), axis=1,
-                          bitorder="little")[: info["n_obs"], :m]
-        dp = np.packbits(d.T, axis=1, bitorder="little")
-        op = np.packbits(o.T, axis=1, bitorder="little") if info["n_obs"] else np.zeros((m, 0), np.uint8)
-        for a, b in zip(dp, op):
-            ka, kb = a.tobytes(), b.tobytes()
-            if ka != zero_d or kb != zero_o:
-                out.add((ka, kb))
-    return out
+def tmcs_dem_columns(handle: int) -> Tuple[List[Tuple[List[int], List[int]]], np.ndarray, np.ndarray]:
+    """Detector error model columns (C: tmcs_dem_columns): a list of
+    (detectors, observables) per distinct non-empty single-fault signature,
+    in the library's canonical order, with each column's probability and
+    merged fault count."""
+    nc, ne = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    h = ctypes.c_void_p(handle)
+    _check(lib().tmcs_dem_columns(h, ctypes.byref(nc), ctypes.byref(ne), None, None, None, None))
+    off = np.zeros(nc.value + 1, dtype=np.uint64)
+    ent = np.zeros(max(ne.value, 1), dtype=np.uint32)
+    p = np.zeros(max(nc.value, 1), dtype=np.float64)
+    nf = np.zeros(max(nc.value, 1), dtype=np.uint64)
+    _check(lib().tmcs_dem_columns(h, ctypes.byref(nc), ctypes.byref(ne), off.ctypes.data, ent.ctypes.data,
+                                  p.ctypes.data, nf.ctypes.data))
+    cols = []
+    for c in range(nc.value):
+        v = ent[int(off[c]):int(off[c + 1])]
+        cols.append(([int(x) for x in v if x < 0x80000000], [int(x) & 0x7FFFFFFF for x in v if x >= 0x80000000]))
+    return cols, p[: nc.value], nf[: nc.value]
 
 
 def tmcs_check_device() -> None:
@@ -325,7 +319,7 @@ def tmcs_sample_measurements(handle: int, first_chunk: int, shots: int, seed: in
                                           _dev_ptr(meas), _stream_ptr(stream)))
 
 
-KERNEL_NAMES = {3: "frame_kernel", 4: "frame_kernel_w", 5: "sig_kernel", 6: "sig_pipe_kernel"}
+KERNEL_NAMES = {3: "frame_kernel", 4: "frame_kernel_w", 5: "sig_kernel", 6: "sig_pipe_kernel", 7: "flow_kernel"}
 
 
 def tmcs_launch_shape(handle: int) -> Dict[str, object]:

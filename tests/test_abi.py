@@ -100,6 +100,12 @@ def test_sample_rejects_bad_arguments_before_device_work(tmcs):
         assert L.tmcs_sample(h, 64, 1, None, 0x2000, None) == 1
         assert L.tmcs_sample(h, 64, 1, 0x1000, None, None) == 1
         assert L.tmcs_sample_range(h, (1 << 32) - 1, 128, 1, 0x1000, 0x2000, None) == 1
+        # first chunks near 2^64 must not wrap the range check around
+        for fc in ((1 << 64) - 1, (1 << 64) - 2, 1 << 32):
+            assert L.tmcs_sample_range(h, fc, 128, 1, 0x1000, 0x2000, None) == 1
+            assert L.tmcs_sample_noalloc(h, fc, 128, 1, 0x1000, 0x2000, None) == 1
+            assert L.tmcs_sample_measurements(h, fc, 128, 1, 0x1000, None) == 1
+            assert "2^32" in tmcs.tmcs_last_error()
         assert L.tmcs_sample(None, 64, 1, 0x1000, 0x2000, None) == 1
         assert L.tmcs_batch_sample(None, 3, None) == 1
     finally:
@@ -319,5 +325,62 @@ def test_signature_program_refuses_spans_beyond_the_ring(tmcs, monkeypatch):
     h = tmcs.tmcs_circuit_build(circ)
     try:
         assert tmcs.tmcs_circuit_stats(h)["sig_ok"] == 1
+    finally:
+        tmcs.tmcs_circuit_free(h)
+
+
+@pytest.mark.parametrize("case", _sig_cases(), ids=lambda c: c[0])
+def test_dem_columns_equal_oracle(tmcs, case):
+    """tmcs_dem_columns (the parity-check-matrix columns of Methods
+    "Decoding") equals the oracle's single-fault DEM merged by signature:
+    the same columns, each with the oracle's odd-parity probability and fault
+    count, in ascending order of their entry lists."""
+    from oracle import dem
+    _, circ = case
+    want = dem.column_probabilities(circ)
+    h = tmcs.tmcs_circuit_build(circ)
+    try:
+        cols, p, nf = tmcs.tmcs_dem_columns(h)
+    finally:
+        tmcs.tmcs_circuit_free(h)
+    keys = [(sum(1 << j for j in d), sum(1 << j for j in o)) for d, o in cols]
+    assert len(set(keys)) == len(keys) and set(keys) == set(want)
+    for k, pc, n in zip(keys, p, nf):
+        assert n == want[k][1]
+        assert abs(pc - want[k][0]) <= 1e-12 + 1e-9 * want[k][0]
+    entries = [d + [0x80000000 | o for o in ob] for d, ob in cols]
+    assert entries == sorted(entries)
+
+
+@pytest.mark.parametrize("key", ["sc3", "sc5", "sc7", "sc9", "sc11"])
+def test_dem_columns_reproduce_table_iii(tmcs, key):
+    """Distinct single-fault signatures of the 4/3-round surface-code
+    circuits equal the "cols" of Table III (non-local CNOT and teleportation),
+    computed by the library's C call."""
+    from conftest import golden_rows
+    t3 = {r[0]: [int(v) for v in r[1:]] for r in golden_rows("table_iii_counts.txt")}
+    code = C.code_by_name(key)
+    for fn, idx in ((C.nonlocal_cnot_circuit, 4), (C.teleport_circuit, 9)):
+        h = tmcs.tmcs_circuit_build(fn(code, 4, 3))
+        try:
+            cols, _, _ = tmcs.tmcs_dem_columns(h)
+            assert len(cols) == t3[key][idx]
+        finally:
+            tmcs.tmcs_circuit_free(h)
+
+
+def test_dem_columns_buffer_contract(tmcs):
+    """Sizes first, then arrays; too-small capacities return TMCS_E_BUFFER."""
+    import ctypes
+    h = tmcs.tmcs_circuit_build(C.WORKLOADS["nl_sc3"].circuit())
+    L = tmcs.lib()
+    try:
+        nc, ne = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        assert L.tmcs_dem_columns(h, ctypes.byref(nc), ctypes.byref(ne), None, None, None, None) == 0
+        assert nc.value > 0 and ne.value >= nc.value
+        off = np.zeros(nc.value + 1, dtype=np.uint64)
+        small = ctypes.c_uint64(nc.value - 1)
+        assert L.tmcs_dem_columns(h, ctypes.byref(small), ctypes.byref(ne), off.ctypes.data, None, None, None) == 6
+        assert L.tmcs_dem_columns(None, ctypes.byref(nc), ctypes.byref(ne), None, None, None, None) == 1
     finally:
         tmcs.tmcs_circuit_free(h)

@@ -79,13 +79,23 @@ def test_signatures_random_circuits(trial):
 
 @pytest.mark.parametrize("key", ["sc3", "sc5", "sc7", "sc9", "sc11"])
 def test_table_iii_columns_on_gpu(key):
-    """Distinct single-fault signatures of the 4/3-round circuits equal the
-    'cols' of Table III (non-local CNOT and teleportation)."""
+    """Distinct single-fault signatures found by fault injection on the GPU
+    (one fault per lane, tmcs_fault_signatures) are exactly the columns of
+    tmcs_dem_columns, and their number is Table III's "cols" for the
+    4/3-round circuits (non-local CNOT and teleportation)."""
     code = C.code_by_name(key)
     for fn, idx in ((C.nonlocal_cnot_circuit, 4), (C.teleport_circuit, 9)):
-        s = tmcs.Sampler(fn(code, 4, 3))
-        assert len(tmcs.dem_columns(s)) == T3[key][idx]
-        s.close()
+        circ = fn(code, 4, 3)
+        d, o = gpu_signatures(circ)
+        sigs = np.concatenate([d, o], axis=0).T
+        nonempty = sigs[sigs.any(axis=1)]
+        gpu_cols = {tuple(np.nonzero(r)[0]) for r in np.unique(nonempty, axis=0)}
+        h = tmcs.tmcs_circuit_build(circ)
+        cols, _, _ = tmcs.tmcs_dem_columns(h)
+        tmcs.tmcs_circuit_free(h)
+        lib_cols = {tuple(dd) + tuple(circ.n_det + ob for ob in oo) for dd, oo in cols}
+        assert gpu_cols == lib_cols
+        assert len(lib_cols) == T3[key][idx]
 
 
 @pytest.mark.parametrize("case", ["nl_sc5", "tp_bb18"])

@@ -1,0 +1,144 @@
+"""GPU parity of the decoupled event-signature kernel (walker and applier
+warps joined by a shared-memory event arena) against the CPU oracle.
+
+The kernel changes only the execution order of the event-signature sampler
+(Methods "Simulation": detector flips are XORs of the sampled events' output
+lists), so every launch shape must reproduce the oracle bit for bit: chunks
+per tile, applier warps, CTA size, ring schedule, several tiles per CTA, a
+ragged last chunk, a nonzero first chunk, and the path where an event does
+not fit its step's arena region (forced here with tiny capacities).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_05611_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2504_05611_gb300 import tmcs  # noqa: E402
+from circuit_gen import random_noisy_circuit  # noqa: E402
+
+
+def gpu_sample(circ, shots, seed, first_chunk=0):
+    s = tmcs.Sampler(circ)
+    det, obs = s.sample(shots, seed, first_chunk=first_chunk)
+    torch.cuda.synchronize()
+    out = det.cpu().numpy().view(np.uint64), obs.cpu().numpy().view(np.uint64)
+    s.close()
+    return out
+
+
+_ORACLE = {}
+
+
+def oracle_sample(circ, key, shots, seed, first_chunk):
+    k = (key, shots, seed, first_chunk)
+    if k not in _ORACLE:
+        _ORACLE[k] = oracle.sample(circ, shots, seed, first_chunk=first_chunk, threads=8)
+    return _ORACLE[k]
+
+
+def assert_flow_parity(monkeypatch, circ, key, shots, seed, first_chunk=0, **env):
+    monkeypatch.setenv("TMCS_KERNEL", "7")
+    for k, v in env.items():
+        monkeypatch.setenv(k, str(v))
+    gd, go = gpu_sample(circ, shots, seed, first_chunk)
+    od, oo = oracle_sample(circ, key, shots, seed, first_chunk)
+    assert gd.shape == od.shape and go.shape == oo.shape
+    bad = np.argwhere(gd != od)
+    assert bad.size == 0, f"{len(bad)} detector words differ, first at {bad[:3].tolist()}"
+    assert np.array_equal(go, oo)
+    tmcs.tmcs_check_device()
+    return gd, go
+
+
+def nl11():
+    return C.nonlocal_cnot_circuit(C.code_by_name("sc11"), 11, 11, C.NoiseModel(0.003, 0.02))
+
+
+# (schedule, chunks per tile, applier warps, CTA size): the ring of K x window
+# words must fit shared memory next to the arena, so larger windows (schedule
+# 0: 4096 detectors, 1: 2048, 2: 1024) take fewer chunks per tile
+FLOW_SHAPES = [(0, 1, 8, 1024), (0, 2, 4, 1024), (0, 4, 8, 1024), (0, 4, 1, 1024), (0, 2, 2, 512), (0, 1, 1, 256),
+               (1, 8, 4, 1024), (1, 4, 8, 1024), (1, 8, 8, 1024), (1, 2, 1, 256), (2, 16, 8, 1024), (2, 8, 4, 1024),
+               (2, 4, 2, 512), (2, 1, 8, 1024), (2, 16, 2, 256)]
+
+
+@pytest.mark.parametrize("sched,tile_k,appliers,threads", FLOW_SHAPES)
+def test_flow_shapes_are_bit_exact(monkeypatch, sched, tile_k, appliers, threads):
+    """Every ring schedule (4096, 2048, 1024 detectors) x chunks per tile x
+    applier warps x CTA size, ragged tail, nonzero first chunk."""
+    circ = nl11()
+    gd, go = assert_flow_parity(monkeypatch, circ, "nl11", 64 * 19 + 45, 29, first_chunk=3,
+                                TMCS_SIG_SCHED=sched, TMCS_TILE_K=tile_k, TMCS_FLOW_APPLIERS=appliers,
+                                TMCS_THREADS=threads)
+    assert gd.any() and go.any()
+
+
+@pytest.mark.parametrize("tile_k,shots", [(1, 64 * 1000 + 37), (2, 64 * 1000 + 37), (2, 64 * 1000),
+                                          (4, 64 * 2002 - 5), (8, 64 * 2002 - 5)])
+def test_flow_many_tiles_per_cta(monkeypatch, tile_k, shots):
+    """Several tiles per CTA: walkers run into the next tile's steps while
+    the appliers finish this one's. Odd and even column counts take the
+    scalar and the 16-byte output stores."""
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc5"), 6, 6, C.NoiseModel(0.01, 0.05))
+    gd, go = assert_flow_parity(monkeypatch, circ, "nl5", shots, 41, first_chunk=11, TMCS_TILE_K=tile_k)
+    assert gd.any() and go.any()
+
+
+@pytest.mark.parametrize("cap", [1, 3, 17, 200])
+@pytest.mark.parametrize("tile_k", [2, 8])
+def test_flow_region_overflow_is_exact(monkeypatch, cap, tile_k):
+    """Events beyond their step's arena region are held by their lane and
+    XORed into the ring once that step is being applied: with capacities of
+    a few events nearly every event takes that path, and the output is still
+    the oracle's."""
+    circ = nl11()
+    assert_flow_parity(monkeypatch, circ, "nl11", 64 * 19 + 45, 29, first_chunk=3, TMCS_TILE_K=tile_k,
+                       TMCS_SIG_SCHED=1 if tile_k == 8 else 0, TMCS_TEST_FLOW_CAP=cap)
+
+
+@pytest.mark.parametrize("arena", [1024, 2048])
+def test_flow_small_arena(monkeypatch, arena):
+    """An arena smaller than a step's expected events: steps are gated on
+    the appliers and regions are clamped to the arena, so events overflow."""
+    circ = nl11()
+    assert_flow_parity(monkeypatch, circ, "nl11", 64 * 19 + 45, 29, first_chunk=3, TMCS_TILE_K=8,
+                       TMCS_SIG_SCHED=1, TMCS_FLOW_ARENA=arena)
+
+
+@pytest.mark.parametrize("kind", ["nl", "teleport", "memory"])
+@pytest.mark.parametrize("code", ["sc3", "sc5", "bb18"])
+def test_flow_protocols_high_noise(monkeypatch, kind, code):
+    cc = C.code_by_name(code)
+    nz = C.NoiseModel(p=0.02, p_ebit=0.05)
+    circ = {"nl": C.nonlocal_cnot_circuit(cc, 2, 2, nz), "teleport": C.teleport_circuit(cc, 2, 2, nz),
+            "memory": C.memory_circuit(cc, 3, nz)}[kind]
+    assert_flow_parity(monkeypatch, circ, f"{kind}-{code}", 64 * 37 + 5, 7)
+
+
+@pytest.mark.parametrize("trial", range(8))
+def test_flow_random_circuits(monkeypatch, trial):
+    """Random Clifford circuits with every noise kind (PAULI_CHANNEL_1
+    included), feedback and observables."""
+    rng = np.random.default_rng(1900 + trial)
+    circ = random_noisy_circuit(rng, int(rng.integers(2, 9)), int(rng.integers(4, 40)))
+    assert_flow_parity(monkeypatch, circ, f"rand{trial}", 64 * 9 + int(rng.integers(1, 64)),
+                       int(rng.integers(1, 2 ** 62)), TMCS_TILE_K=int(rng.choice([1, 2, 4, 8])))
+
+
+def test_flow_ebit_decoherence(monkeypatch):
+    """Methods "Decoherence": aged ebits carry PAULI_CHANNEL_1 noise."""
+    w = C.WORKLOADS["nl_sc11_deco"]
+    assert_flow_parity(monkeypatch, w.circuit(), "deco", 64 * 23 + 9, w.seed, first_chunk=5, TMCS_TILE_K=4)
+
+
+def test_flow_teleport_bb144(monkeypatch):
+    """BB[[144,12,12]] teleportation, 12 observables, reduced shots."""
+    w = C.WORKLOADS["tp_bb144"]
+    assert_flow_parity(monkeypatch, w.circuit(), "tp144", 64 * 40 + 3, w.seed, TMCS_TILE_K=4)
