@@ -148,14 +148,22 @@ __device__ __forceinline__ void flow_put_word(const FlowArgs &A, uint64_t *ring,
 }
 
 // Walker warps. Every lane holds at most one stream; streams are handed out
-// in CTA order (tile, step, item, chunk). Per iteration a walking lane runs
-// one Philox call (two draws) and reserves arena entries for its events
-// together with the lanes of its warp whose streams belong to the same
-// step (one shared atomic per step and warp).
+// in CTA order (tile, step, item, chunk). An iteration is a window of
+// kFlowWindow Philox calls (two draws each) of every walking lane's stream,
+// with the window's events kept in registers; then the warp reserves arena
+// entries for all of them at once, together with the lanes whose streams
+// belong to the same step (one shared atomic per step and warp), reports the
+// streams that ended and refills those lanes. Streams longer than a window
+// continue in the next one. The per-iteration work of the warp (refill,
+// reservation, completion) is thus shared by up to 2 kFlowWindow draws per
+// lane.
+constexpr int kFlowWindow = 3;
+
 template <int K, bool SMT>
 __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, FlowCtl &C, uint32_t nt,
                                           uint32_t nv_last, const uint32_t *tabs) {
     constexpr uint32_t LK = FlowLog<K>::v;
+    constexpr int NE = 2 * kFlowWindow;  // events a lane can draw per window
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t n_steps = A.n_steps, amask = A.arena - 1u;
@@ -163,23 +171,26 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
     const uint64_t total = uint64_t(nt) * per_tile;
     const uint64_t c_tile = S.soff[n_steps];
     bool have = false, live = false, ended = false, exhausted = false;
-    uint32_t npend = 0, pend0 = 0, pend1 = 0;
     uint32_t tcur = 0xFFFFFFFFu, qcur = 0;
     uint64_t tbase = 0;
     // the lane's stream: step Q, its region (capacity, low word of its
     // unwrapped arena position, gate), Philox stream words, call counter,
-    // first event slot, kind, Pauli counts, gap table offset, position and
-    // length in trials
+    // first event slot, kind, Pauli counts, gap table offset, chunk tag,
+    // position and length in trials
     uint32_t Q = 0, cap = 0, uq = 0;
     long long gate = 0;
     PhiloxStream ps{0u, 0u, 0u};
     uint32_t call = 0, ubase = 0, kind = 0, npauli = 1, kp = 1, toff = 0, t1 = 0, t2 = 0, ktag = 0;
     int pos = -1, n_trials = 0;
     float inv = 0.f;
-    uint32_t t_wait = 0;
+    // the window's events; ev[held .. ne) are events that did not fit their
+    // step's region and wait for it to be the step being applied
+    uint32_t ev[NE];
+    uint32_t ne = 0, held = 0;
+    uint32_t t_wait = 0, iter = 0;
     bool waiting = false;
     for (;;) {
-        if (__any_sync(0xFFFFFFFFu, ld_shared_volatile(&C.abort) != 0u)) return;
+        if ((iter++ & 7u) == 0u && __any_sync(0xFFFFFFFFu, ld_shared_volatile(&C.abort) != 0u)) return;
         if (!have && !exhausted) {
             const uint64_t g = grab_index64(&C.next);
             if (g >= total) {
@@ -233,71 +244,72 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
         }
         // events held back by a full region: once step Q is the one being
         // applied, XOR them into the ring directly
-        if (npend && ld_shared_volatile(&C.applied) == Q) {
+        if (held < ne && ld_shared_volatile(&C.applied) == Q) {
             __threadfence_block();
-            flow_put_word<K>(A, S.ring, pend0);
-            if (npend > 1) flow_put_word<K>(A, S.ring, pend1);
-            npend = 0;
+#pragma unroll
+            for (int j = 0; j < NE; j++)
+                if (uint32_t(j) >= held && uint32_t(j) < ne) flow_put_word<K>(A, S.ring, ev[j]);
+            held = ne;
         }
-        const bool walk = live && !ended && npend == 0;
+        const bool walk = live && !ended && held == ne;
         const uint32_t wm = __ballot_sync(0xFFFFFFFFu, walk);
         if (wm) {
-            uint32_t e0 = 0, e1 = 0;
-            bool v0 = false, v1 = false;
             if (walk) {
-                const uint4 w = philox_call(ps, call, A.key0, A.key1);
-                call++;
-                pos += 1 + gap_count_t<SMT>(tabs + toff, inv, w.x);
-                if (pos >= n_trials) {
-                    ended = true;
-                } else {
-                    const uint32_t pk = kind == N_PC1 ? (w.y < t1 ? 1u : w.y < t2 ? 3u : 2u) : 1u + __umulhi(w.y, npauli);
-                    e0 = ((ubase + uint32_t(pos >> 6) * kp + (pk - 1u)) << (6u + LK)) | ktag | uint32_t(pos & 63);
-                    v0 = true;
-                    pos += 1 + gap_count_t<SMT>(tabs + toff, inv, w.z);
-                    if (pos >= n_trials) {
-                        ended = true;
-                    } else {
-                        const uint32_t pk1 =
-                            kind == N_PC1 ? (w.w < t1 ? 1u : w.w < t2 ? 3u : 2u) : 1u + __umulhi(w.w, npauli);
-                        e1 = ((ubase + uint32_t(pos >> 6) * kp + (pk1 - 1u)) << (6u + LK)) | ktag | uint32_t(pos & 63);
-                        v1 = true;
+                ne = 0;
+                held = 0;
+#pragma unroll
+                for (int c = 0; c < kFlowWindow; c++) {
+                    if (!ended) {
+                        const uint4 w = philox_call(ps, call, A.key0, A.key1);
+                        call++;
+                        pos += 1 + gap_count_t<SMT>(tabs + toff, inv, w.x);
+                        if (pos >= n_trials) {
+                            ended = true;
+                        } else {
+                            const uint32_t pk =
+                                kind == N_PC1 ? (w.y < t1 ? 1u : w.y < t2 ? 3u : 2u) : 1u + __umulhi(w.y, npauli);
+                            ev[2 * c] = ((ubase + uint32_t(pos >> 6) * kp + (pk - 1u)) << (6u + LK)) | ktag |
+                                        uint32_t(pos & 63);
+                            ne = 2 * c + 1;
+                            pos += 1 + gap_count_t<SMT>(tabs + toff, inv, w.z);
+                            if (pos >= n_trials) {
+                                ended = true;
+                            } else {
+                                const uint32_t pk1 = kind == N_PC1 ? (w.w < t1 ? 1u : w.w < t2 ? 3u : 2u)
+                                                                   : 1u + __umulhi(w.w, npauli);
+                                ev[2 * c + 1] = ((ubase + uint32_t(pos >> 6) * kp + (pk1 - 1u)) << (6u + LK)) |
+                                                ktag | uint32_t(pos & 63);
+                                ne = 2 * c + 2;
+                            }
+                        }
                     }
                 }
             }
-            const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, v0);
-            const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, v1);
-            if (v0) {  // v1 implies v0
-                const uint32_t peers = __match_any_sync(b0, Q);
+            // reserve the window's events: lanes of the same step share one
+            // atomic; a lane's offset among them from bit ballots of its count
+            const bool res = walk && ne != 0;
+            const uint32_t em = __ballot_sync(0xFFFFFFFFu, res);
+            if (res) {
+                const uint32_t peers = __match_any_sync(em, Q);
+                const uint32_t b0 = __ballot_sync(em, ne & 1u) & peers;
+                const uint32_t b1 = __ballot_sync(em, ne & 2u) & peers;
+                const uint32_t b2 = __ballot_sync(em, ne & 4u) & peers;
                 const uint32_t leader = uint32_t(__ffs(peers)) - 1u;
-                const uint32_t n = uint32_t(__popc(b0 & peers) + __popc(b1 & peers));
-                uint32_t idx = uint32_t(__popc(b0 & peers & lt) + __popc(b1 & peers & lt));
+                const uint32_t n = uint32_t(__popc(b0) + 2 * __popc(b1) + 4 * __popc(b2));
+                const uint32_t off = uint32_t(__popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt));
                 uint32_t base = 0;
                 if (lane == leader) base = atomicAdd(&C.cnt[Q & (kFlowSlots - 1u)], n);
-                idx += __shfl_sync(peers, base, int(leader));
-                if (idx < cap) {
-                    S.arena[(uq + idx) & amask] = e0;
-                } else {
-                    pend0 = e0;
-                    npend = 1;
-                }
-                if (v1) {
-                    idx++;
-                    if (idx < cap) {
-                        S.arena[(uq + idx) & amask] = e1;
-                    } else if (npend) {
-                        pend1 = e1;
-                        npend = 2;
-                    } else {
-                        pend0 = e1;
-                        npend = 1;
-                    }
-                }
+                const uint32_t idx = __shfl_sync(peers, base, int(leader)) + off;
+                // entries past the region's capacity stay in ev[] (held)
+                held = idx >= cap ? 0u : min(ne, cap - idx);
+#pragma unroll
+                for (int j = 0; j < NE; j++)
+                    if (uint32_t(j) < held) S.arena[(uq + idx + uint32_t(j)) & amask] = ev[j];
             }
         }
         // a stream whose walk ended and whose events are all stored or
         // applied is reported to its step
-        const bool complete = have && ended && npend == 0;
+        const bool complete = have && ended && held == ne;
         const uint32_t cm = __ballot_sync(0xFFFFFFFFu, complete);
         if (complete) {
             __threadfence_block();  // its events precede the count
@@ -307,6 +319,8 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
             have = false;
             live = false;
             ended = false;
+            ne = 0;
+            held = 0;
         }
         if (wm | cm) {
             waiting = false;
@@ -314,6 +328,7 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
         }
         // nothing to walk: every lane is done, gated or holding events
         if (!__any_sync(0xFFFFFFFFu, have)) return;
+        if (__any_sync(0xFFFFFFFFu, ld_shared_volatile(&C.abort) != 0u)) return;
         if (!waiting) {
             t_wait = uint32_t(globaltimer_ns());
             waiting = true;
