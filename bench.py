@@ -158,6 +158,9 @@ def main():
     ap.add_argument("--requests", type=int, default=120, help="serve: number of requests")
     ap.add_argument("--batch-mix", default="config", choices=["config", "small"], help="batch64: job mix")
     ap.add_argument("--load", type=float, default=0.7, help="serve: offered load / solo capacity")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched (64-job mix) and served (Poisson requests) measurements that the "
+                         "default single-GPU run appends to its line")
     args = ap.parse_args()
 
     from paper_2504_05611_gb300 import circuits
@@ -328,6 +331,23 @@ def main():
                "launches_per_step": nslices,
                "d2h_copy_gbs": hd[0].numel() * 8 / (min(link_ms) * 1e-3) / 1e9}
 
+    # batched and served throughput on the same GPU, stated against the
+    # single-circuit kernel (1 GPU only; the outputs of the headline run are
+    # released first)
+    extras = {}
+    if world == 1 and not args.no_extras and not args.shots:
+        del det, obs
+        if args.e2e_steps > 0:
+            del dbuf, obuf, hd, ho
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        b = batch_measure(args, 3)
+        b["vs_single_circuit_shots_per_s"] = b["shots_per_s"] / shots_s
+        extras["batch"] = b
+        sv = serve_measure(args, args.requests, args.load)
+        sv["vs_single_circuit_shots_per_s"] = sv["shots_per_s"] / shots_s
+        extras["serve"] = sv
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -364,21 +384,20 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     sampler.close()
     if world > 1:
         dist.destroy_process_group()
 
 
-def batch_bench(args):
+def batch_measure(args, steps):
     """Batched launch over the seeded 64-job mix (uneven circuits and shot
-    counts) against the same jobs sampled one call each on the same stream."""
+    counts) against the same jobs sampled one call each on the same stream;
+    returns the batched, graph-replay and solo times and throughput."""
     import torch
-    from paper_2504_05611_gb300 import build as lib_build
     from paper_2504_05611_gb300 import circuits, tmcs
-    lib_build.build()
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     if args.batch_mix == "small":
         # many small jobs (SC d = 3..9, 1e4..1e5 shots): solo launches underfill the GPU
         rng = __import__("numpy").random.default_rng(3)
@@ -437,37 +456,54 @@ def batch_bench(args):
         with torch.cuda.graph(g, stream=stream):
             batched()
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(dev.index)
     clocks.start()
-    ms_batch = timed(batched, args.steps)
+    ms_batch = timed(batched, steps)
 
     def replay():
         with torch.cuda.stream(stream):
             g.replay()
 
-    ms_graph = timed(replay, args.steps)
+    ms_graph = timed(replay, steps)
     clk = clocks.stop()
-    ms_solo = timed(solo, max(1, args.steps // 2))
+    ms_solo = timed(solo, max(1, steps // 2))
     value = total_det_bits / (min(ms_batch, ms_graph) / 1e3)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": min(ms_batch, ms_graph), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "shots_per_s": total_shots / (min(ms_batch, ms_graph) / 1e3),
-        "config": {"workload": "batch64", "jobs": len(jobs), "distinct_circuits": len(cache),
-                   "total_shots": total_shots,
-                   "mix": "circuits.batch_mix(64, seed=1)" if args.batch_mix != "small" else
-                          "64 SC d=3..9 NL/teleport jobs, 1e4..1e5 shots (seed 3)"},
-        "batched_ms": ms_batch, "graph_replay_ms": ms_graph, "solo_calls_ms": ms_solo,
-        "batched_vs_solo": ms_solo / min(ms_batch, ms_graph), "clocks": clk,
-        # jobs of at least 16 chunks per SM run as their own tuned launch;
-        # the others share one persistent launch per size class (1 or 2)
-        "gpu_launches": n_large + (1 if n_large < len(jobs) else 0),
-        "gpu_launches_note": f"{n_large} GPU-filling jobs as single launches + the shared launches (1 per size class)",
-    }
-    print(json.dumps(line), flush=True)
+    del g
     for s in cache.values():
         s.close()
+    return {
+        "value": value, "shots_per_s": total_shots / (min(ms_batch, ms_graph) / 1e3), "total_shots": total_shots,
+        "jobs": len(jobs), "distinct_circuits": len(cache), "batched_ms": ms_batch, "graph_replay_ms": ms_graph,
+        "solo_calls_ms": ms_solo, "batched_vs_solo": ms_solo / min(ms_batch, ms_graph), "clocks": clk,
+        "gpu_launches": n_large + (1 if n_large < len(jobs) else 0), "n_large": n_large,
+        "mix": "circuits.batch_mix(64, seed=1)" if args.batch_mix != "small" else
+               "64 SC d=3..9 NL/teleport jobs, 1e4..1e5 shots (seed 3)",
+    }
+
+
+def batch_bench(args):
+    """--workload batch64: the batched measurement as its own JSON line."""
+    import torch
+    from paper_2504_05611_gb300 import build as lib_build
+    lib_build.build()
+    torch.cuda.set_device(0)
+    r = batch_measure(args, args.steps)
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": min(r["batched_ms"], r["graph_replay_ms"]), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "shots_per_s": r["shots_per_s"],
+        "config": {"workload": "batch64", "jobs": r["jobs"], "distinct_circuits": r["distinct_circuits"],
+                   "total_shots": r["total_shots"], "mix": r["mix"]},
+        "batched_ms": r["batched_ms"], "graph_replay_ms": r["graph_replay_ms"], "solo_calls_ms": r["solo_calls_ms"],
+        "batched_vs_solo": r["batched_vs_solo"], "clocks": r["clocks"],
+        # jobs of at least 16 chunks per SM run as their own tuned launch;
+        # the others share one persistent launch per size class (1 or 2)
+        "gpu_launches": r["gpu_launches"],
+        "gpu_launches_note": f"{r['n_large']} GPU-filling jobs as single launches + the shared launches "
+                             "(1 per size class)",
+    }
+    print(json.dumps(line), flush=True)
 
 
 def serve_requests(n, seed):
@@ -478,18 +514,15 @@ def serve_requests(n, seed):
     return circuits.batch_mix(n, seed=seed)
 
 
-def serve_bench(args):
+def serve_measure(args, n_requests, load):
     """Poisson arrivals into the continuous-batching server at a fixed
-    fraction of the measured solo capacity; reports throughput and latency."""
+    fraction of the measured solo capacity; returns throughput and latency."""
     import threading
     import numpy as np
     import torch
-    from paper_2504_05611_gb300 import build as lib_build
     from paper_2504_05611_gb300 import tmcs
-    lib_build.build()
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    reqs = serve_requests(args.requests, seed=7)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    reqs = serve_requests(n_requests, seed=7)
     cache, handles = {}, []
     for w in reqs:
         key = (w.code, w.op, w.rounds_before, w.p)
@@ -518,7 +551,6 @@ def serve_bench(args):
     solo_s = time.perf_counter() - t0
     del scratch
     torch.cuda.empty_cache()
-    load = args.load
     mean_gap = solo_s / len(reqs) / load
     rng = np.random.default_rng(11)
     gaps = rng.exponential(mean_gap, size=len(reqs))
@@ -536,7 +568,7 @@ def serve_bench(args):
             ids[i] = srv.submit(h, w.shots, w.seed)
         submitted.set()
 
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(dev.index)
     clocks.start()
     start = time.perf_counter()
     th = threading.Thread(target=client)
@@ -552,21 +584,35 @@ def serve_bench(args):
     clk = clocks.stop()
     st = srv.stats()
     srv.close()
-    value = det_bits / makespan
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
-        "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u64", "data": "synthetic", "shots_per_s": shots_total / makespan,
-        "config": {"workload": "serve", "requests": len(reqs), "offered_load": load,
-                   "arrivals": "Poisson", "family": "circuits.batch_mix(n, seed=7)", "n_streams": 4},
-        "latency_p50_s": st["latency_p50_s"], "latency_p99_s": st["latency_p99_s"],
-        "latency_mean_s": st["latency_mean_s"], "solo_capacity_s": solo_s,
-        "served_vs_solo_throughput": solo_s / makespan, "completed": st["completed"], "failed": st["failed"],
-        "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
     for h in cache.values():
         h.close()
+    return {"value": det_bits / makespan, "shots_per_s": shots_total / makespan, "makespan_s": makespan,
+            "requests": len(reqs), "offered_load": load, "latency_p50_s": st["latency_p50_s"],
+            "latency_p99_s": st["latency_p99_s"], "latency_mean_s": st["latency_mean_s"],
+            "solo_capacity_s": solo_s, "solo_shots_per_s": shots_total / solo_s,
+            "served_vs_solo_throughput": solo_s / makespan, "completed": st["completed"], "failed": st["failed"],
+            "clocks": clk}
+
+
+def serve_bench(args):
+    """--workload serve: the serving measurement as its own JSON line."""
+    import torch
+    from paper_2504_05611_gb300 import build as lib_build
+    lib_build.build()
+    torch.cuda.set_device(0)
+    r = serve_measure(args, args.requests, args.load)
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": r["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic", "shots_per_s": r["shots_per_s"],
+        "config": {"workload": "serve", "requests": r["requests"], "offered_load": r["offered_load"],
+                   "arrivals": "Poisson", "family": "circuits.batch_mix(n, seed=7)", "n_streams": 4},
+        "latency_p50_s": r["latency_p50_s"], "latency_p99_s": r["latency_p99_s"],
+        "latency_mean_s": r["latency_mean_s"], "solo_capacity_s": r["solo_capacity_s"],
+        "served_vs_solo_throughput": r["served_vs_solo_throughput"], "completed": r["completed"],
+        "failed": r["failed"], "clocks": r["clocks"],
+    }
+    print(json.dumps(line), flush=True)
 
 
 def peaks_bench(args):

@@ -118,6 +118,33 @@ __device__ __forceinline__ int gap_count_t(const uint32_t *__restrict__ T, float
     return g;
 }
 
+// gap_count_t with a cheaper estimate and an early exit: est = log2(w | 1)
+// * inv_log2 + c32 (c32 = -32 inv_log2, so est ~ log(w 2^-32) / log(1-p));
+// two table reads show whether the estimate g is the count (w < T[g] and
+// w >= T[g+1], T + i holding T[i+1]); only lanes where it is not walk to the
+// exact count. Same result as gap_count_t for every w.
+template <bool SMT>
+__device__ __forceinline__ int gap_count_est(const uint32_t *__restrict__ T, float inv_log2, float c32, uint32_t w) {
+    auto ld = [&](int i) -> uint32_t {
+        if constexpr (SMT) return T[i];
+        else return __ldg(T + i);
+    };
+    const float est = fmaf(__log2f(__uint2float_rn(w | 1u)), inv_log2, c32);
+    int g = min(max(__float2int_rz(est), 0), int(kGapLen));
+    const uint32_t a = ld(max(g, 1) - 1), b = ld(min(g, int(kGapLen) - 1));
+    const bool ge = g == 0 || w < a;              // count >= g
+    const bool gt = g < int(kGapLen) && w < b;    // count >= g + 1
+    if (ge && !gt) return g;
+    if (gt) {
+        g++;
+        while (g < int(kGapLen) && w < ld(g)) g++;
+    } else {
+        g--;
+        while (g > 0 && w >= ld(g - 1)) g--;
+    }
+    return g;
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -126,6 +153,44 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 
 __device__ __forceinline__ uint32_t ld_shared_volatile(const uint32_t *p) {
     return *reinterpret_cast<const volatile uint32_t *>(p);
+}
+
+// Shared-memory accesses with acquire / release ordering at CTA scope (the
+// walker/applier hand-offs of the decoupled kernel): cheaper than a full
+// fence next to a relaxed access.
+__device__ __forceinline__ uint32_t shared_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t ld_acquire_shared(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(shared_addr(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_shared64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.cta.shared::cta.u64 %0, [%1];" : "=l"(v) : "r"(shared_addr(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_shared(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(shared_addr(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_shared64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.cta.shared::cta.u64 [%0], %1;" ::"r"(shared_addr(p)), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add_shared(uint32_t *p, uint32_t v) {
+    asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(shared_addr(p)), "r"(v) : "memory");
+}
+
+// Warp-aggregated shared counter: the calling lane's index among all lanes
+// that call together (one atomic per warp).
+__device__ __forceinline__ uint32_t grab_index(uint32_t *ctr) {
+    const uint32_t mask = __activemask();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t leader = uint32_t(__ffs(mask)) - 1u;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(ctr, uint32_t(__popc(mask)));
+    base = __shfl_sync(mask, base, int(leader));
+    return base + uint32_t(__popc(mask & ((1u << lane) - 1u)));
 }
 
 // 64-bit warp-aggregated counter: the calling lane's index among all lanes

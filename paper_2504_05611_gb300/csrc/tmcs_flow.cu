@@ -42,14 +42,18 @@
 namespace tmcs {
 
 constexpr uint32_t kFlowSlots = 64;       // steps in flight (done / count slots)
-constexpr uint32_t kFlowApplyBatch = 4;   // events an applier lane loads at once
+// events an applier lane loads at once (build-time tuning value)
+#ifndef TMCS_FLOW_APPLY_BATCH
+#define TMCS_FLOW_APPLY_BATCH 4
+#endif
+constexpr uint32_t kFlowApplyBatch = TMCS_FLOW_APPLY_BATCH;
 constexpr uint32_t kFlowMinArena = 1024;  // smallest useful arena (entries)
 constexpr uint32_t kFlowMaxArena = 65536;
 
 struct FlowArgs {
     const NoiseDesc *noise;
     const uint32_t *tables;
-    const uint4 *item_rec;      // op, segment, first event slot, kind | table << 3 | (units-1) << 16 | desc << 22
+    const uint4 *item_desc;     // walker descriptors, two uint4 per item (see SigSchedule::item_desc)
     const uint4 *steps;         // item_begin, item_end, flush_lo, flush_hi
     const float *step_events;   // expected events per chunk of each step
     const uint32_t *ev_ent;     // two words per event slot, then the overflow lists
@@ -61,14 +65,18 @@ struct FlowArgs {
     uint32_t key0, key1, first_chunk;
     uint32_t vec_out;           // det 16-byte aligned and n_cols even: 16-byte output stores
     uint64_t n_cols, last_mask, n_tiles;
+    uint64_t ld;                // words between output rows (the call's column count; a launch may cover a slice)
     uint64_t *det;
     uint64_t *obs;
     uint32_t *status;
 };
 
+// Arena positions are kept modulo 2^32: only differences (less than the
+// arena size plus one step's region) and positions modulo the arena size
+// (a power of two) are used.
 struct FlowCtl {
-    unsigned long long next;       // streams handed out (CTA sequence)
-    unsigned long long u_applied;  // arena position (unwrapped) of the first unapplied step
+    uint32_t next;                 // streams handed out (CTA sequence; a launch keeps it below 2^31)
+    uint32_t u_applied;            // arena position of the first unapplied step
     uint32_t applied;              // steps applied (CTA sequence)
     uint32_t abort;                // a bounded wait expired
     uint32_t app_stop;             // appliers leave (written by applier thread 0 before a barrier)
@@ -149,40 +157,36 @@ __device__ __forceinline__ void flow_put_word(const FlowArgs &A, uint64_t *ring,
 
 // Walker warps. Every lane holds at most one stream; streams are handed out
 // in CTA order (tile, step, item, chunk). An iteration is a window of
-// kFlowWindow Philox calls (two draws each) of every walking lane's stream,
+// W Philox calls (two draws each) of every walking lane's stream,
 // with the window's events kept in registers; then the warp reserves arena
 // entries for all of them at once, together with the lanes whose streams
 // belong to the same step (one shared atomic per step and warp), reports the
 // streams that ended and refills those lanes. Streams longer than a window
 // continue in the next one. The per-iteration work of the warp (refill,
-// reservation, completion) is thus shared by up to 2 kFlowWindow draws per
-// lane.
-constexpr int kFlowWindow = 3;
-
-template <int K, bool SMT>
+// reservation, completion) is thus shared by up to 2 W draws per lane.
+template <int K, int W, bool SMT>
 __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, FlowCtl &C, uint32_t nt,
                                           uint32_t nv_last, const uint32_t *tabs) {
     constexpr uint32_t LK = FlowLog<K>::v;
-    constexpr int NE = 2 * kFlowWindow;  // events a lane can draw per window
+    constexpr int NE = 2 * W;  // events a lane can draw per window
+    static_assert(NE < 16, "event counts per window are reserved with four count-bit ballots at most");
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t n_steps = A.n_steps, amask = A.arena - 1u;
-    const uint64_t per_tile = uint64_t(A.n_items) << LK;
-    const uint64_t total = uint64_t(nt) * per_tile;
-    const uint64_t c_tile = S.soff[n_steps];
+    const uint32_t per_tile = A.n_items << LK;
+    const uint32_t total = nt * per_tile;
+    const uint32_t c_tile = S.soff[n_steps];
     bool have = false, live = false, ended = false, exhausted = false;
-    uint32_t tcur = 0xFFFFFFFFu, qcur = 0;
-    uint64_t tbase = 0;
+    uint32_t tcur = 0xFFFFFFFFu, tbase = 0;
     // the lane's stream: step Q, its region (capacity, low word of its
     // unwrapped arena position, gate), Philox stream words, call counter,
     // first event slot, kind, Pauli counts, gap table offset, chunk tag,
     // position and length in trials
-    uint32_t Q = 0, cap = 0, uq = 0;
-    long long gate = 0;
+    uint32_t Q = 0, cap = 0, uq = 0, gate = 0;
     PhiloxStream ps{0u, 0u, 0u};
     uint32_t call = 0, ubase = 0, kind = 0, npauli = 1, kp = 1, toff = 0, t1 = 0, t2 = 0, ktag = 0;
     int pos = -1, n_trials = 0;
-    float inv = 0.f;
+    float inv = 0.f, c32 = 0.f;
     // the window's events; ev[held .. ne) are events that did not fit their
     // step's region and wait for it to be the step being applied
     uint32_t ev[NE];
@@ -192,40 +196,44 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
     for (;;) {
         if ((iter++ & 7u) == 0u && __any_sync(0xFFFFFFFFu, ld_shared_volatile(&C.abort) != 0u)) return;
         if (!have && !exhausted) {
-            const uint64_t g = grab_index64(&C.next);
+            const uint32_t g = grab_index(&C.next);
             if (g >= total) {
                 exhausted = true;
             } else {
                 if (tcur == 0xFFFFFFFFu || g - tbase >= per_tile) {
-                    tcur = uint32_t(g / per_tile);
-                    tbase = uint64_t(tcur) * per_tile;
-                    qcur = 0;
+                    tcur = g / per_tile;
+                    tbase = tcur * per_tile;
                 }
-                const uint32_t sl = uint32_t(g - tbase);
+                const uint32_t sl = g - tbase;
                 const uint32_t it = sl >> LK, k = sl & uint32_t(K - 1);
-                while (it >= S.send[qcur]) qcur++;
-                Q = tcur * n_steps + qcur;
-                const uint64_t U = uint64_t(tcur) * c_tile + S.soff[qcur];
-                cap = S.scap[qcur];
-                gate = (long long)(U + cap) - (long long)A.arena;
-                uq = uint32_t(U);
-                const uint4 rec = __ldg(A.item_rec + it);
-                kind = rec.w & 7u;
-                npauli = npauli_of(kind);
-                kp = sig_paulis(kind);
-                toff = ((rec.w >> 3) & 0x1FFFu) * kTableWords;
-                inv = __uint_as_float(tabs[toff + kGapLen]);
+                const uint4 d0 = __ldg(A.item_desc + 2 * it), d1 = __ldg(A.item_desc + 2 * it + 1);
+                const uint32_t q = d1.x >> 17;
+                Q = tcur * n_steps + q;
+                const uint32_t U = tcur * c_tile + S.soff[q];  // modulo 2^32
+                cap = S.scap[q];
+                gate = U + cap - A.arena;
+                uq = U;
+                kind = d1.x & 7u;
+                npauli = (d1.x >> 3) & 15u;
+                kp = (d1.x >> 7) & 15u;
+                toff = (d1.y & 0x1FFFu) * kTableWords;
+                inv = __uint_as_float(d1.z);
+                c32 = __uint_as_float(d1.w);
                 if (kind == N_PC1) {
-                    t1 = __ldg(&A.noise[rec.w >> 22].t1);
-                    t2 = __ldg(&A.noise[rec.w >> 22].t2);
+                    t1 = __ldg(&A.noise[d1.y >> 13].t1);
+                    t2 = __ldg(&A.noise[d1.y >> 13].t2);
                 }
                 const uint32_t nv = tcur == nt - 1u ? nv_last : uint32_t(K);
-                const uint64_t col = (uint64_t(blockIdx.x) + uint64_t(tcur) * gridDim.x) * uint64_t(K) + k;
-                ps = philox_stream(A.first_chunk + uint32_t(col), rec.x, rec.y, A.key0, A.key1);
-                ubase = rec.z;
+                const uint32_t chunk = A.first_chunk + (blockIdx.x + tcur * gridDim.x) * uint32_t(K) + k;
+                // Philox round 1 of this stream from the descriptor's product
+                // of the op index (counter words: call, chunk, op, segment)
+                ps.a0 = d0.x ^ chunk ^ A.key0;
+                ps.a1 = d0.y;
+                ps.a3 = d0.z ^ A.key1;
+                ubase = d0.w;
                 ktag = k << 6;
                 // chunks past the end of the call (ragged last tile): no trials
-                n_trials = k < nv ? 64 * int(((rec.w >> 16) & 63u) + 1u) : 0;
+                n_trials = k < nv ? 64 * int(((d1.x >> 11) & 63u) + 1u) : 0;
                 call = 0;
                 pos = -1;
                 have = true;
@@ -236,16 +244,16 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
         // the stream may start once its step's arena region is free and the
         // step is within the slots in flight
         if (have && !live) {
-            const long long ua = (long long)ld_shared_volatile64(&C.u_applied);
-            if (ua >= gate && Q - ld_shared_volatile(&C.applied) < kFlowSlots) {
-                __threadfence_block();  // the appliers' reads of the region precede our writes
-                live = true;
-            }
+            // acquire: the appliers' last reads of the region and their
+            // reset of the step's counters precede our writes. The region
+            // is free once u_applied has reached the gate (signed
+            // difference: positions are modulo 2^32).
+            const uint32_t ua = ld_acquire_shared(&C.u_applied);
+            if (int32_t(ua - gate) >= 0 && Q - ld_acquire_shared(&C.applied) < kFlowSlots) live = true;
         }
         // events held back by a full region: once step Q is the one being
         // applied, XOR them into the ring directly
-        if (held < ne && ld_shared_volatile(&C.applied) == Q) {
-            __threadfence_block();
+        if (held < ne && ld_acquire_shared(&C.applied) == Q) {
 #pragma unroll
             for (int j = 0; j < NE; j++)
                 if (uint32_t(j) >= held && uint32_t(j) < ne) flow_put_word<K>(A, S.ring, ev[j]);
@@ -257,32 +265,32 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
             if (walk) {
                 ne = 0;
                 held = 0;
+                // the window's W Philox calls and 2W gap counts do not depend
+                // on one another: straight-line code, so their latencies
+                // overlap; draws after the stream's last one are computed
+                // and discarded (the warp runs them for its other lanes)
+                uint32_t wp[NE];
+                int gp[NE];
 #pragma unroll
-                for (int c = 0; c < kFlowWindow; c++) {
-                    if (!ended) {
-                        const uint4 w = philox_call(ps, call, A.key0, A.key1);
-                        call++;
-                        pos += 1 + gap_count_t<SMT>(tabs + toff, inv, w.x);
-                        if (pos >= n_trials) {
-                            ended = true;
-                        } else {
-                            const uint32_t pk =
-                                kind == N_PC1 ? (w.y < t1 ? 1u : w.y < t2 ? 3u : 2u) : 1u + __umulhi(w.y, npauli);
-                            ev[2 * c] = ((ubase + uint32_t(pos >> 6) * kp + (pk - 1u)) << (6u + LK)) | ktag |
-                                        uint32_t(pos & 63);
-                            ne = 2 * c + 1;
-                            pos += 1 + gap_count_t<SMT>(tabs + toff, inv, w.z);
-                            if (pos >= n_trials) {
-                                ended = true;
-                            } else {
-                                const uint32_t pk1 = kind == N_PC1 ? (w.w < t1 ? 1u : w.w < t2 ? 3u : 2u)
-                                                                   : 1u + __umulhi(w.w, npauli);
-                                ev[2 * c + 1] = ((ubase + uint32_t(pos >> 6) * kp + (pk1 - 1u)) << (6u + LK)) |
-                                                ktag | uint32_t(pos & 63);
-                                ne = 2 * c + 2;
-                            }
-                        }
-                    }
+                for (int c = 0; c < W; c++) {
+                    const uint4 w = philox_call(ps, call + uint32_t(c), A.key0, A.key1);
+                    gp[2 * c] = gap_count_est<SMT>(tabs + toff, inv, c32, w.x);
+                    gp[2 * c + 1] = gap_count_est<SMT>(tabs + toff, inv, c32, w.z);
+                    wp[2 * c] = w.y;
+                    wp[2 * c + 1] = w.w;
+                }
+                call += uint32_t(W);
+                // positions in draw order: every draw before the one that
+                // passes the end of the segment is an event
+#pragma unroll
+                for (int d = 0; d < NE; d++) {
+                    pos += 1 + gp[d];
+                    const bool is_ev = !ended && pos < n_trials;
+                    ended = ended || !is_ev;
+                    const uint32_t pk = kind == N_PC1 ? (wp[d] < t1 ? 1u : wp[d] < t2 ? 3u : 2u)
+                                                      : 1u + __umulhi(wp[d], npauli);
+                    ev[d] = ((ubase + uint32_t(pos >> 6) * kp + (pk - 1u)) << (6u + LK)) | ktag | uint32_t(pos & 63);
+                    ne = is_ev ? uint32_t(d + 1) : ne;
                 }
             }
             // reserve the window's events: lanes of the same step share one
@@ -291,12 +299,17 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
             const uint32_t em = __ballot_sync(0xFFFFFFFFu, res);
             if (res) {
                 const uint32_t peers = __match_any_sync(em, Q);
-                const uint32_t b0 = __ballot_sync(em, ne & 1u) & peers;
-                const uint32_t b1 = __ballot_sync(em, ne & 2u) & peers;
-                const uint32_t b2 = __ballot_sync(em, ne & 4u) & peers;
+                // counts reach NE (6 or 8 for windows of 3 or 4 calls): one
+                // ballot per bit of the count
+                constexpr int NB = NE >= 8 ? 4 : 3;
+                uint32_t n = 0, off = 0;
+#pragma unroll
+                for (int bit = 0; bit < NB; bit++) {
+                    const uint32_t bm = __ballot_sync(em, (ne >> bit) & 1u) & peers;
+                    n += uint32_t(__popc(bm)) << bit;
+                    off += uint32_t(__popc(bm & lt)) << bit;
+                }
                 const uint32_t leader = uint32_t(__ffs(peers)) - 1u;
-                const uint32_t n = uint32_t(__popc(b0) + 2 * __popc(b1) + 4 * __popc(b2));
-                const uint32_t off = uint32_t(__popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt));
                 uint32_t base = 0;
                 if (lane == leader) base = atomicAdd(&C.cnt[Q & (kFlowSlots - 1u)], n);
                 const uint32_t idx = __shfl_sync(peers, base, int(leader)) + off;
@@ -312,10 +325,12 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
         const bool complete = have && ended && held == ne;
         const uint32_t cm = __ballot_sync(0xFFFFFFFFu, complete);
         if (complete) {
-            __threadfence_block();  // its events precede the count
+            // the streams' events (stored or applied by these lanes) precede
+            // the count: warp barrier, then a release add by the leader
             const uint32_t peers = __match_any_sync(cm, Q);
             const uint32_t leader = uint32_t(__ffs(peers)) - 1u;
-            if (lane == leader) atomicAdd(&C.done[Q & (kFlowSlots - 1u)], uint32_t(__popc(peers)));
+            __syncwarp(peers);
+            if (lane == leader) red_release_add_shared(&C.done[Q & (kFlowSlots - 1u)], uint32_t(__popc(peers)));
             have = false;
             live = false;
             ended = false;
@@ -357,7 +372,7 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
     const uint32_t amask = A.arena - 1u, mask = A.window_mask;
     const uint32_t obs_row = A.window_mask + 1u;
     const uint2 *ev2 = reinterpret_cast<const uint2 *>(A.ev_ent);
-    uint64_t U = 0;
+    uint32_t U = 0;  // arena position of step Q, modulo 2^32
     for (uint32_t T = 0; T < nt; T++) {
         const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(T) * gridDim.x;
         const uint64_t col0 = tile * uint64_t(K);
@@ -394,7 +409,7 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
             if (C.app_stop) return;
             __threadfence_block();  // the walkers' events precede the reads below
             const uint32_t n = min(ld_shared_volatile(&C.cnt[slot]), S.scap[q]);
-            const uint32_t u0 = uint32_t(U);
+            const uint32_t u0 = U;
             for (uint32_t e = at; e < n; e += nthr * kFlowApplyBatch) {
                 uint32_t wv[kFlowApplyBatch];
                 uint2 v[kFlowApplyBatch];
@@ -427,7 +442,7 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
                         if (col == A.n_cols - 1) v.x &= A.last_mask;
                         if (col + 1 == A.n_cols - 1) v.y &= A.last_mask;
                         unsigned long long *out =
-                            reinterpret_cast<unsigned long long *>(A.det + uint64_t(d) * A.n_cols + col);
+                            reinterpret_cast<unsigned long long *>(A.det + uint64_t(d) * A.ld + col);
                         if (k + 1 < nv) __stcs(reinterpret_cast<ulonglong2 *>(out), v);
                         else __stcs(out, v.x);
                     }
@@ -442,7 +457,7 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
                     if (k >= nv) continue;
                     const uint64_t col = col0 + k;
                     if (col == A.n_cols - 1) v &= A.last_mask;
-                    __stcs(reinterpret_cast<unsigned long long *>(A.det + uint64_t(d) * A.n_cols + col), v);
+                    __stcs(reinterpret_cast<unsigned long long *>(A.det + uint64_t(d) * A.ld + col), v);
                 }
             }
             if (q == A.n_steps - 1u) {
@@ -454,7 +469,7 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
                     if (k >= nv) continue;
                     const uint64_t col = col0 + k;
                     if (col == A.n_cols - 1) v &= A.last_mask;
-                    A.obs[uint64_t(o) * A.n_cols + col] = v;
+                    A.obs[uint64_t(o) * A.ld + col] = v;
                 }
             }
             flow_bar(nthr);
@@ -462,23 +477,25 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
             if (at == 0) {
                 C.done[slot] = 0u;
                 C.cnt[slot] = 0u;
-                __threadfence_block();
-                *reinterpret_cast<volatile unsigned long long *>(&C.u_applied) = U;
-                *reinterpret_cast<volatile uint32_t *>(&C.applied) = Q + 1u;
+                // release: every applier's reads and writes of this step
+                // (ordered before by the barrier) and the counter resets
+                // precede the hand-off
+                st_release_shared(&C.u_applied, U);
+                st_release_shared(&C.applied, Q + 1u);
             }
         }
     }
 }
 
-template <int K>
+template <int K, int W>
 __global__ void __launch_bounds__(1024, 1) flow_kernel(const FlowArgs A) {
     extern __shared__ __align__(128) uint64_t smem[];
     __shared__ FlowCtl C;
     if (uint64_t(blockIdx.x) >= A.n_tiles) return;
     const FlowSmem S = flow_layout(smem, A, K);
     const uint32_t tid = threadIdx.x, T_ = blockDim.x;
-    const uint32_t W = A.window_mask + 1u;
-    for (uint32_t i = tid; i < (W + A.n_obs) * uint32_t(K); i += T_) S.ring[i] = 0ull;
+    const uint32_t rows = A.window_mask + 1u;
+    for (uint32_t i = tid; i < (rows + A.n_obs) * uint32_t(K); i += T_) S.ring[i] = 0ull;
     for (uint32_t i = tid; i < A.smem_tables * kTableWords; i += T_) S.stab[i] = __ldg(A.tables + i);
     // region capacities: mean + 6 sigma + 64 of the step's events over K
     // chunks (Poisson-like counts), at most the arena; steps without items
@@ -496,8 +513,8 @@ __global__ void __launch_bounds__(1024, 1) flow_kernel(const FlowArgs A) {
         C.cnt[tid] = 0u;
     }
     if (tid == 0) {
-        C.next = 0ull;
-        C.u_applied = 0ull;
+        C.next = 0u;
+        C.u_applied = 0u;
         C.applied = 0u;
         C.abort = 0u;
         C.app_stop = 0u;
@@ -527,8 +544,8 @@ __global__ void __launch_bounds__(1024, 1) flow_kernel(const FlowArgs A) {
     const uint32_t nv_last = rem < uint64_t(K) ? uint32_t(rem) : uint32_t(K);
     __syncthreads();
     if ((tid >> 5) >= A.walkers) flow_apply<K>(A, S, C, nt, nv_last);
-    else if (A.smem_tables) flow_walk<K, true>(A, S, C, nt, nv_last, S.stab);
-    else flow_walk<K, false>(A, S, C, nt, nv_last, A.tables);
+    else if (A.smem_tables) flow_walk<K, W, true>(A, S, C, nt, nv_last, S.stab);
+    else flow_walk<K, W, false>(A, S, C, nt, nv_last, A.tables);
 }
 
 // ------------------------------------------------------------------- host
@@ -565,6 +582,8 @@ bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int applie
     s.K = K;
     s.threads = threads;
     s.appliers = appliers;
+    const int wforce = env_int_flow("TMCS_FLOW_WINDOW", 3);  // tuning knob: Philox calls per walker window
+    s.window = (wforce >= 2 && wforce <= 4) ? wforce : 3;
     // gap tables in shared memory when that still leaves an arena of 8192
     // entries, else read through L1
     s.smem_tables = arena_for(fixed + tabs) >= 8192u;
@@ -579,21 +598,25 @@ bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int applie
     return true;
 }
 
-template <int K>
+template <int K, int W>
 static cudaError_t flow_go(const FlowArgs &a, const FlowShape &s, int sms, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(flow_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem));
+    cudaError_t e = cudaFuncSetAttribute(flow_kernel<K, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(flow_kernel<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(flow_kernel<K, W>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              int(cudaSharedmemCarveoutMaxShared));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flow_kernel<K>, s.threads, s.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flow_kernel<K, W>, s.threads, s.smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(a.n_tiles, uint64_t(sms) * uint64_t(per_sm)));
-    // steps are counted per CTA in 32 bits
-    if ((a.n_tiles / grid + 1) * uint64_t(a.n_steps) >= (uint64_t(1) << 31)) return cudaErrorInvalidValue;
-    flow_kernel<K><<<unsigned(grid), s.threads, s.smem, st>>>(a);
+    // streams and steps are counted per CTA in 32 bits (flow_launch slices
+    // calls so that this holds)
+    const uint64_t tiles_per_cta = (a.n_tiles + grid - 1) / grid;
+    if (tiles_per_cta * uint64_t(a.n_steps) >= (uint64_t(1) << 31) ||
+        tiles_per_cta * (uint64_t(a.n_items) * uint64_t(K)) >= (uint64_t(1) << 31))
+        return cudaErrorInvalidValue;
+    flow_kernel<K, W><<<unsigned(grid), s.threads, s.smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -605,7 +628,7 @@ cudaError_t flow_launch(const SigProgram &G, uint32_t n_obs, const DeviceSig *ds
     FlowArgs a{};
     a.noise = ds->noise;
     a.tables = ds->tables;
-    a.item_rec = reinterpret_cast<const uint4 *>(ds->items[s.sched]);
+    a.item_desc = reinterpret_cast<const uint4 *>(ds->item_desc[s.sched]);
     a.steps = reinterpret_cast<const uint4 *>(ds->steps[s.sched]);
     a.step_events = ds->step_events[s.sched];
     a.ev_ent = ds->ev_ent;
@@ -619,21 +642,63 @@ cudaError_t flow_launch(const SigProgram &G, uint32_t n_obs, const DeviceSig *ds
     a.walkers = uint32_t(s.threads / 32 - s.appliers);
     a.key0 = call.key0;
     a.key1 = call.key1;
-    a.first_chunk = call.first_chunk;
-    a.vec_out = (reinterpret_cast<uintptr_t>(call.det) % 16 == 0 && call.n_cols % 2 == 0) ? 1u : 0u;
-    a.n_cols = call.n_cols;
-    a.last_mask = call.last_mask;
-    a.n_tiles = (call.n_cols + uint64_t(s.K) - 1) / uint64_t(s.K);
-    a.det = call.det;
-    a.obs = call.obs;
-    a.status = call.status;
-    switch (s.K) {
-    case 16: return flow_go<16>(a, s, sms, st);
-    case 8: return flow_go<8>(a, s, sms, st);
-    case 4: return flow_go<4>(a, s, sms, st);
-    case 2: return flow_go<2>(a, s, sms, st);
-    default: return flow_go<1>(a, s, sms, st);
+    a.ld = call.n_cols;
+    // A CTA counts its streams and its steps in 32 bits: a call with more
+    // tiles per CTA than that allows runs as several launches over column
+    // slices (each a multiple of the tile size, in column order).
+    const uint64_t per_tile_streams = uint64_t(a.n_items) * uint64_t(s.K);
+    const uint64_t per_tile_steps = a.n_steps;
+    const uint64_t lim = (uint64_t(1) << 31) - 1;
+    const uint64_t max_tiles_per_cta =
+        std::max<uint64_t>(1, std::min(lim / std::max<uint64_t>(per_tile_streams, 1), lim / per_tile_steps) - 1);
+    uint64_t slice_cols = max_tiles_per_cta * uint64_t(sms) * uint64_t(s.K);
+    // testing knob: slices of this many tiles (so the sliced path runs at
+    // sizes the tests can check)
+    const int tslice = env_int_flow("TMCS_TEST_FLOW_SLICE_TILES", 0);
+    if (tslice > 0) slice_cols = std::min<uint64_t>(slice_cols, uint64_t(tslice) * uint64_t(s.K));
+    for (uint64_t c0 = 0; c0 < call.n_cols; c0 += slice_cols) {
+        const uint64_t n = std::min(slice_cols, call.n_cols - c0);
+        a.first_chunk = call.first_chunk + uint32_t(c0);
+        a.n_cols = n;
+        a.last_mask = c0 + n == call.n_cols ? call.last_mask : ~uint64_t(0);
+        a.n_tiles = (n + uint64_t(s.K) - 1) / uint64_t(s.K);
+        a.det = call.det + c0;
+        a.obs = call.obs ? call.obs + c0 : nullptr;
+        a.vec_out = (reinterpret_cast<uintptr_t>(a.det) % 16 == 0 && a.ld % 2 == 0) ? 1u : 0u;
+        a.status = call.status;
+        cudaError_t e;
+        switch (s.window) {
+        case 2:
+            switch (s.K) {
+            case 16: e = flow_go<16, 2>(a, s, sms, st); break;
+            case 8: e = flow_go<8, 2>(a, s, sms, st); break;
+            case 4: e = flow_go<4, 2>(a, s, sms, st); break;
+            case 2: e = flow_go<2, 2>(a, s, sms, st); break;
+            default: e = flow_go<1, 2>(a, s, sms, st); break;
+            }
+            break;
+        case 4:
+            switch (s.K) {
+            case 16: e = flow_go<16, 4>(a, s, sms, st); break;
+            case 8: e = flow_go<8, 4>(a, s, sms, st); break;
+            case 4: e = flow_go<4, 4>(a, s, sms, st); break;
+            case 2: e = flow_go<2, 4>(a, s, sms, st); break;
+            default: e = flow_go<1, 4>(a, s, sms, st); break;
+            }
+            break;
+        default:
+            switch (s.K) {
+            case 16: e = flow_go<16, 3>(a, s, sms, st); break;
+            case 8: e = flow_go<8, 3>(a, s, sms, st); break;
+            case 4: e = flow_go<4, 3>(a, s, sms, st); break;
+            case 2: e = flow_go<2, 3>(a, s, sms, st); break;
+            default: e = flow_go<1, 3>(a, s, sms, st); break;
+            }
+            break;
+        }
+        if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
 }
 
 }  // namespace tmcs

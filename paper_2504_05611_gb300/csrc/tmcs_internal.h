@@ -128,6 +128,7 @@ struct DeviceSig {
     const uint32_t *items[kSigMaxSchedules] = {};  // item records of each schedule
     const SigStep *steps[kSigMaxSchedules] = {};
     const float *step_events[kSigMaxSchedules] = {};
+    const uint32_t *item_desc[kSigMaxSchedules] = {};
     const uint32_t *ev_ent = nullptr;
 };
 
@@ -143,6 +144,7 @@ struct FlowShape {
     int K = 4;                // chunks per tile
     int threads = 1024;
     int appliers = 8;         // applier warps (the other warps walk)
+    int window = 3;           // Philox calls per walker window (2..4)
     uint32_t arena = 0;       // event arena entries (power of two)
     bool smem_tables = false; // gap tables staged in shared memory
     size_t smem = 0;          // dynamic shared memory
@@ -203,6 +205,12 @@ struct SigSchedule {
     // Expected events per 64-shot chunk of each step (sum over its items of
     // 64 x units x p); the decoupled kernel sizes its event regions by it.
     std::vector<float> step_events;
+    // Walker descriptors of the decoupled kernel, 8 words per item (no
+    // dependence on the seed): hi and lo of 0xCD9E8D57 x op index (Philox
+    // round 1), segment, first event slot, kind | npauli << 3 | paulis << 7
+    // | (units - 1) << 11 | step << 17, table | descriptor << 13, float bits
+    // of 1/log2(1-p) and of -32/log2(1-p) (the gap estimate).
+    std::vector<uint32_t> item_desc;
 };
 
 struct SigProgram {

@@ -595,17 +595,6 @@ __device__ __forceinline__ void sig_apply_events(const SigArgs &A, const uint64_
     }
 }
 
-// Warp-aggregated shared counter: the calling lane's index among all lanes
-// that call together (one atomic per warp).
-__device__ __forceinline__ uint32_t grab_index(uint32_t *ctr) {
-    const uint32_t mask = __activemask();
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t leader = uint32_t(__ffs(mask)) - 1u;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(ctr, uint32_t(__popc(mask)));
-    base = __shfl_sync(mask, base, int(leader));
-    return base + uint32_t(__popc(mask & ((1u << lane) - 1u)));
-}
 
 // Applies the n events of a warp's queue slice, converged: lane l takes
 // events l, l + 32, ... N at a time. Called by all 32 lanes.
@@ -1709,12 +1698,14 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
     const size_t b_noise = align256(G.noise.size() * sizeof(NoiseDesc));
     const size_t b_tables = align256(G.tables.size() * 4);
     const size_t n_sched = G.sched.size();
-    size_t b_items[kSigMaxSchedules] = {}, b_steps[kSigMaxSchedules] = {}, b_sev[kSigMaxSchedules] = {}, b_sched = 0;
+    size_t b_items[kSigMaxSchedules] = {}, b_steps[kSigMaxSchedules] = {}, b_sev[kSigMaxSchedules] = {},
+           b_desc[kSigMaxSchedules] = {}, b_sched = 0;
     for (size_t k = 0; k < n_sched; k++) {
         b_items[k] = align256(G.sched[k].item_rec.size() * 4);
         b_steps[k] = align256(G.sched[k].steps.size() * sizeof(SigStep));
         b_sev[k] = align256(G.sched[k].step_events.size() * sizeof(float));
-        b_sched += b_items[k] + b_steps[k] + b_sev[k];
+        b_desc[k] = align256(G.sched[k].item_desc.size() * 4);
+        b_sched += b_items[k] + b_steps[k] + b_sev[k] + b_desc[k];
     }
     const size_t b_ent = align256(G.ev_ent.size() * 4);
     const size_t total = std::max<size_t>(b_noise + b_tables + b_sched + b_ent, 256);
@@ -1730,12 +1721,14 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
     for (size_t i = 0; i < dn.size(); i++) dn[i].tgt_off = G.ev_base[i];
     const size_t o_noise = put(dn.data(), dn.size() * sizeof(NoiseDesc), b_noise);
     const size_t o_tables = put(G.tables.data(), G.tables.size() * 4, b_tables);
-    size_t o_items[kSigMaxSchedules] = {}, o_steps[kSigMaxSchedules] = {}, o_sev[kSigMaxSchedules] = {};
+    size_t o_items[kSigMaxSchedules] = {}, o_steps[kSigMaxSchedules] = {}, o_sev[kSigMaxSchedules] = {},
+           o_desc[kSigMaxSchedules] = {};
     for (size_t k = 0; k < n_sched; k++) {
         const SigSchedule &S = G.sched[k];
         o_items[k] = put(S.item_rec.data(), S.item_rec.size() * 4, b_items[k]);
         o_steps[k] = put(S.steps.data(), S.steps.size() * sizeof(SigStep), b_steps[k]);
         o_sev[k] = put(S.step_events.data(), S.step_events.size() * sizeof(float), b_sev[k]);
+        o_desc[k] = put(S.item_desc.data(), S.item_desc.size() * 4, b_desc[k]);
     }
     const size_t o_ent = put(G.ev_ent.data(), G.ev_ent.size() * 4, b_ent);
     void *base = nullptr;
@@ -1760,6 +1753,7 @@ static int device_sig(const tmcs_circuit *c, const DeviceSig **out) {
         ds.items[k] = reinterpret_cast<const uint32_t *>(b + o_items[k]);
         ds.steps[k] = reinterpret_cast<const SigStep *>(b + o_steps[k]);
         ds.step_events[k] = reinterpret_cast<const float *>(b + o_sev[k]);
+        ds.item_desc[k] = reinterpret_cast<const uint32_t *>(b + o_desc[k]);
     }
     ds.ev_ent = reinterpret_cast<const uint32_t *>(b + o_ent);
     auto ins = c->dev_sig.emplace(dev, ds);

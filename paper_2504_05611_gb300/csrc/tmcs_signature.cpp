@@ -148,6 +148,7 @@ static std::string validate_signature_program(const SigProgram &G, uint64_t D, u
         if (W < 256 || (W & (W - 1)) || S.lag > uint32_t(kSigMaxLag) || (S.lag && W > 16384)) return "schedule shape";
         if (S.item_rec.size() != 4 * n_items || S.steps.empty()) return "schedule size";
         if (S.step_events.size() != S.steps.size()) return "step event counts";
+        if (S.item_desc.size() != 8 * n_items || S.steps.size() > (1u << 15)) return "walker descriptors size";
         std::vector<uint64_t> lo(n_items), hi(n_items);
         for (size_t k = 0; k < n_items; k++) {
             const uint32_t di = S.items[2 * k], sg = S.items[2 * k + 1];
@@ -158,6 +159,17 @@ static std::string validate_signature_program(const SigProgram &G, uint64_t D, u
             if (r[0] != nd.op_index || r[1] != sg || r[2] != G.ev_base[di] + sg * kSegUnits * sig_paulis(nd.kind) ||
                 r[3] != (nd.kind | (nd.table << 3) | ((units - 1) << 16) | (di << 22)))
                 return "item record";
+            // walker descriptor: the indices the decoupled kernel forms from it
+            const uint32_t *wd = &S.item_desc[8 * k];
+            const uint64_t m = uint64_t(0xCD9E8D57u) * nd.op_index;
+            const uint32_t step = wd[4] >> 17;
+            if (wd[0] != uint32_t(m >> 32) || wd[1] != uint32_t(m) || wd[2] != sg || wd[3] != r[2] ||
+                (wd[4] & 7u) != nd.kind || ((wd[4] >> 3) & 15u) != (nd.kind == 3u ? 15u : nd.kind == 2u ? 3u : 1u) ||
+                ((wd[4] >> 7) & 15u) != sig_paulis(nd.kind) || ((wd[4] >> 11) & 63u) != units - 1 ||
+                step >= S.steps.size() || k < S.steps[step].item_begin || k >= S.steps[step].item_end ||
+                (wd[5] & 0x1FFFu) != nd.table || (wd[5] >> 13) != di ||
+                wd[6] != G.tables[size_t(nd.table) * kTableWords + kGapLen])
+                return "walker descriptor";
             lo[k] = seg_lo[seg0[di] + sg];
             hi[k] = seg_hi[seg0[di] + sg];
         }
@@ -577,6 +589,27 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
             for (uint32_t k = st.item_begin; k < st.item_end; k++) ev += 64.0 * cost(perm[k]);
             S.step_events.push_back(float(ev));
         }
+        // walker descriptors of the decoupled kernel (see SigSchedule)
+        for (uint32_t t = 0; t < S.steps.size(); t++)
+            for (uint32_t k = S.steps[t].item_begin; k < S.steps[t].item_end; k++) {
+                const uint32_t di = S.items[2 * k], sg = S.items[2 * k + 1];
+                const NoiseDesc &nd = G.noise[di];
+                const uint32_t units = std::min(kSegUnits, nd.n_units - sg * kSegUnits);
+                const uint64_t m = uint64_t(0xCD9E8D57u) * nd.op_index;
+                const uint32_t npauli = nd.kind == 3u ? 15u : nd.kind == 2u ? 3u : 1u;
+                uint32_t inv_bits = G.tables[size_t(nd.table) * kTableWords + kGapLen];
+                float inv = 0.f, c32 = 0.f;
+                std::memcpy(&inv, &inv_bits, 4);
+                c32 = -32.0f * inv;
+                uint32_t c32_bits = 0;
+                std::memcpy(&c32_bits, &c32, 4);
+                const uint32_t w[8] = {uint32_t(m >> 32), uint32_t(m), sg,
+                                       G.ev_base[di] + sg * kSegUnits * sig_paulis(nd.kind),
+                                       nd.kind | (npauli << 3) | (sig_paulis(nd.kind) << 7) | ((units - 1) << 11) |
+                                           (t << 17),
+                                       nd.table | (di << 13), inv_bits, c32_bits};
+                S.item_desc.insert(S.item_desc.end(), w, w + 8);
+            }
         // device item records (the walk reads one 16-byte record per stream)
         for (size_t k = 0; k < n_items; k++) {
             const uint32_t di = S.items[2 * k], sg = S.items[2 * k + 1];

@@ -142,3 +142,26 @@ def test_flow_teleport_bb144(monkeypatch):
     """BB[[144,12,12]] teleportation, 12 observables, reduced shots."""
     w = C.WORKLOADS["tp_bb144"]
     assert_flow_parity(monkeypatch, w.circuit(), "tp144", 64 * 40 + 3, w.seed, TMCS_TILE_K=4)
+
+
+@pytest.mark.parametrize("window", [2, 3, 4])
+@pytest.mark.parametrize("tile_k,cap", [(8, 0), (2, 5)])
+def test_flow_walker_windows(monkeypatch, window, tile_k, cap):
+    """Walker windows of 2 to 4 Philox calls per iteration (streams longer
+    than a window continue in the next), with and without region overflow."""
+    circ = nl11()
+    env = dict(TMCS_TILE_K=tile_k, TMCS_SIG_SCHED=1 if tile_k == 8 else 0, TMCS_FLOW_WINDOW=window)
+    if cap:
+        env["TMCS_TEST_FLOW_CAP"] = cap
+    assert_flow_parity(monkeypatch, circ, "nl11", 64 * 19 + 45, 29, first_chunk=3, **env)
+
+
+@pytest.mark.parametrize("slice_tiles,tile_k", [(1, 2), (7, 4), (150, 2)])
+def test_flow_sliced_launches(monkeypatch, slice_tiles, tile_k):
+    """A call too large for one launch's 32-bit stream counters runs as
+    several launches over column slices; forced small slices here (ragged
+    tail in the last slice, odd slice starts, nonzero first chunk)."""
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc5"), 6, 6, C.NoiseModel(0.01, 0.05))
+    gd, go = assert_flow_parity(monkeypatch, circ, "nl5", 64 * 1000 + 37, 41, first_chunk=11, TMCS_TILE_K=tile_k,
+                                TMCS_TEST_FLOW_SLICE_TILES=slice_tiles)
+    assert gd.any() and go.any()
