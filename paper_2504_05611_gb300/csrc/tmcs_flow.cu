@@ -66,6 +66,7 @@ struct FlowArgs {
     uint32_t vec_out;           // det 16-byte aligned and n_cols even: 16-byte output stores
     uint64_t n_cols, last_mask, n_tiles;
     uint64_t ld;                // words between output rows (the call's column count; a launch may cover a slice)
+    uint32_t *garena;           // arena in global memory (a slice of `arena` entries per CTA), or null
     uint64_t *det;
     uint64_t *obs;
     uint32_t *status;
@@ -164,7 +165,7 @@ __device__ __forceinline__ void flow_put_word(const FlowArgs &A, uint64_t *ring,
 // streams that ended and refills those lanes. Streams longer than a window
 // continue in the next one. The per-iteration work of the warp (refill,
 // reservation, completion) is thus shared by up to 2 W draws per lane.
-template <int K, int W, bool SMT>
+template <int K, int W, bool SMT, bool GA>
 __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, FlowCtl &C, uint32_t nt,
                                           uint32_t nv_last, const uint32_t *tabs) {
     constexpr uint32_t LK = FlowLog<K>::v;
@@ -173,6 +174,9 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t n_steps = A.n_steps, amask = A.arena - 1u;
+    // the arena: shared memory, or this CTA's slice of a global buffer
+    // (L2-resident; entries written and read past L1)
+    uint32_t *const arena = GA ? A.garena + size_t(blockIdx.x) * A.arena : S.arena;
     const uint32_t per_tile = A.n_items << LK;
     const uint32_t total = nt * per_tile;
     const uint32_t c_tile = S.soff[n_steps];
@@ -317,7 +321,10 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
                 held = idx >= cap ? 0u : min(ne, cap - idx);
 #pragma unroll
                 for (int j = 0; j < NE; j++)
-                    if (uint32_t(j) < held) S.arena[(uq + idx + uint32_t(j)) & amask] = ev[j];
+                    if (uint32_t(j) < held) {
+                        if constexpr (GA) __stcg(arena + ((uq + idx + uint32_t(j)) & amask), ev[j]);
+                        else arena[(uq + idx + uint32_t(j)) & amask] = ev[j];
+                    }
             }
         }
         // a stream whose walk ended and whose events are all stored or
@@ -363,7 +370,7 @@ __device__ __forceinline__ void flow_bar(uint32_t nthreads) {
 }
 
 // Applier warps: steps in CTA order.
-template <int K>
+template <int K, bool GA>
 __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S, FlowCtl &C, uint32_t nt,
                                            uint32_t nv_last) {
     constexpr uint32_t LK = FlowLog<K>::v;
@@ -372,6 +379,7 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
     const uint32_t amask = A.arena - 1u, mask = A.window_mask;
     const uint32_t obs_row = A.window_mask + 1u;
     const uint2 *ev2 = reinterpret_cast<const uint2 *>(A.ev_ent);
+    const uint32_t *const arena = GA ? A.garena + size_t(blockIdx.x) * A.arena : S.arena;
     uint32_t U = 0;  // arena position of step Q, modulo 2^32
     for (uint32_t T = 0; T < nt; T++) {
         const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(T) * gridDim.x;
@@ -416,7 +424,8 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
 #pragma unroll
                 for (uint32_t j = 0; j < kFlowApplyBatch; j++) {
                     const uint32_t i = e + j * nthr;
-                    wv[j] = i < n ? S.arena[(u0 + i) & amask] : 0u;
+                    if constexpr (GA) wv[j] = i < n ? __ldcg(arena + ((u0 + i) & amask)) : 0u;
+                    else wv[j] = i < n ? arena[(u0 + i) & amask] : 0u;
                 }
 #pragma unroll
                 for (uint32_t j = 0; j < kFlowApplyBatch; j++)
@@ -487,8 +496,13 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
     }
 }
 
-template <int K, int W>
-__global__ void __launch_bounds__(1024, 1) flow_kernel(const FlowArgs A) {
+// CTA size the kernel is compiled for (its register budget follows from it)
+#ifndef TMCS_FLOW_MAX_THREADS
+#define TMCS_FLOW_MAX_THREADS 1024
+#endif
+
+template <int K, int W, bool GA>
+__global__ void __launch_bounds__(TMCS_FLOW_MAX_THREADS, 1) flow_kernel(const FlowArgs A) {
     extern __shared__ __align__(128) uint64_t smem[];
     __shared__ FlowCtl C;
     if (uint64_t(blockIdx.x) >= A.n_tiles) return;
@@ -543,9 +557,9 @@ __global__ void __launch_bounds__(1024, 1) flow_kernel(const FlowArgs A) {
     const uint64_t rem = A.n_cols - last * K;
     const uint32_t nv_last = rem < uint64_t(K) ? uint32_t(rem) : uint32_t(K);
     __syncthreads();
-    if ((tid >> 5) >= A.walkers) flow_apply<K>(A, S, C, nt, nv_last);
-    else if (A.smem_tables) flow_walk<K, W, true>(A, S, C, nt, nv_last, S.stab);
-    else flow_walk<K, W, false>(A, S, C, nt, nv_last, A.tables);
+    if ((tid >> 5) >= A.walkers) flow_apply<K, GA>(A, S, C, nt, nv_last);
+    else if (A.smem_tables) flow_walk<K, W, true, GA>(A, S, C, nt, nv_last, S.stab);
+    else flow_walk<K, W, false, GA>(A, S, C, nt, nv_last, A.tables);
 }
 
 // ------------------------------------------------------------------- host
@@ -560,14 +574,16 @@ static size_t flow_fixed_bytes(const SigProgram &G, int sched, uint32_t n_obs, i
     return flow_ring_bytes(S.window, n_obs, K) + flow_step_bytes(uint32_t(S.steps.size()));
 }
 
-bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int appliers, size_t budget, FlowShape *out) {
+bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int appliers, size_t budget, FlowShape *out,
+                bool global_arena) {
     const SigProgram &G = c->sig;
     if (!G.ok || sched < 0 || size_t(sched) >= G.sched.size()) return false;
     const SigSchedule &S = G.sched[sched];
     if (S.lag || S.steps.empty() || S.steps.size() > kFlowMaxSteps || S.step_events.size() != S.steps.size())
         return false;
     if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16) return false;
-    if (threads < 64 || threads > 1024 || threads % 32 || appliers < 1 || appliers >= threads / 32) return false;
+    if (threads < 64 || threads > TMCS_FLOW_MAX_THREADS || threads % 32 || appliers < 1 || appliers >= threads / 32)
+        return false;
     // event words: slot << (6 + log2 K) | chunk << 6 | lane must fit 32 bits
     if (uint64_t(G.n_event_slots) * 64u * uint64_t(K) > (uint64_t(1) << 32)) return false;
     const size_t fixed = flow_fixed_bytes(G, sched, uint32_t(c->n_obs), K);
@@ -582,6 +598,21 @@ bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int applie
     s.K = K;
     s.threads = threads;
     s.appliers = appliers;
+    // global arena: tables stay in shared memory, the arena is an L2-resident
+    // slice per CTA of the library's scratch buffer
+    if (global_arena) {
+        if (fixed + tabs > budget) return false;
+        const int gforce = env_int_flow("TMCS_FLOW_GARENA", 0);  // tuning knob: global arena entries per CTA
+        s.arena = (gforce >= int(kFlowMinArena) && !(gforce & (gforce - 1))) ? uint32_t(gforce) : 65536u;
+        s.smem_tables = true;
+        s.smem = fixed + tabs;
+        s.garena_ctas = 0;  // set by the caller (resident CTAs)
+        const int wforce = env_int_flow("TMCS_FLOW_WINDOW", 3);
+        s.window = (wforce >= 2 && wforce <= 4) ? wforce : 3;
+        s.global_arena = true;
+        *out = s;
+        return true;
+    }
     const int wforce = env_int_flow("TMCS_FLOW_WINDOW", 3);  // tuning knob: Philox calls per walker window
     s.window = (wforce >= 2 && wforce <= 4) ? wforce : 3;
     // gap tables in shared memory when that still leaves an arena of 8192
@@ -598,26 +629,44 @@ bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int applie
     return true;
 }
 
-template <int K, int W>
+template <int K, int W, bool GA>
 static cudaError_t flow_go(const FlowArgs &a, const FlowShape &s, int sms, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(flow_kernel<K, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem));
+    auto kern = flow_kernel<K, W, GA>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(flow_kernel<K, W>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             int(cudaSharedmemCarveoutMaxShared));
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, int(cudaSharedmemCarveoutMaxShared));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flow_kernel<K, W>, s.threads, s.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.threads, s.smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(a.n_tiles, uint64_t(sms) * uint64_t(per_sm)));
+    uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(a.n_tiles, uint64_t(sms) * uint64_t(per_sm)));
+    // a global arena holds one slice per CTA
+    if (GA) grid = std::min<uint64_t>(grid, s.garena_ctas);
     // streams and steps are counted per CTA in 32 bits (flow_launch slices
     // calls so that this holds)
     const uint64_t tiles_per_cta = (a.n_tiles + grid - 1) / grid;
     if (tiles_per_cta * uint64_t(a.n_steps) >= (uint64_t(1) << 31) ||
         tiles_per_cta * (uint64_t(a.n_items) * uint64_t(K)) >= (uint64_t(1) << 31))
         return cudaErrorInvalidValue;
-    flow_kernel<K, W><<<unsigned(grid), s.threads, s.smem, st>>>(a);
+    kern<<<unsigned(grid), s.threads, s.smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int W, bool GA>
+static cudaError_t flow_go_kg(const FlowArgs &a, const FlowShape &s, int sms, cudaStream_t st) {
+    switch (s.K) {
+    case 16: return flow_go<16, W, GA>(a, s, sms, st);
+    case 8: return flow_go<8, W, GA>(a, s, sms, st);
+    case 4: return flow_go<4, W, GA>(a, s, sms, st);
+    case 2: return flow_go<2, W, GA>(a, s, sms, st);
+    default: return flow_go<1, W, GA>(a, s, sms, st);
+    }
+}
+
+template <int W>
+static cudaError_t flow_go_k(const FlowArgs &a, const FlowShape &s, int sms, cudaStream_t st) {
+    return a.garena ? flow_go_kg<W, true>(a, s, sms, st) : flow_go_kg<W, false>(a, s, sms, st);
 }
 
 cudaError_t flow_launch(const SigProgram &G, uint32_t n_obs, const DeviceSig *ds, const FlowShape &s,
@@ -643,6 +692,10 @@ cudaError_t flow_launch(const SigProgram &G, uint32_t n_obs, const DeviceSig *ds
     a.key0 = call.key0;
     a.key1 = call.key1;
     a.ld = call.n_cols;
+    if (s.garena_ctas) {
+        if (!call.scratch || call.scratch_bytes < size_t(s.garena_ctas) * s.arena * 4) return cudaErrorInvalidValue;
+        a.garena = call.scratch;
+    }
     // A CTA counts its streams and its steps in 32 bits: a call with more
     // tiles per CTA than that allows runs as several launches over column
     // slices (each a multiple of the tile size, in column order).
@@ -668,33 +721,9 @@ cudaError_t flow_launch(const SigProgram &G, uint32_t n_obs, const DeviceSig *ds
         a.status = call.status;
         cudaError_t e;
         switch (s.window) {
-        case 2:
-            switch (s.K) {
-            case 16: e = flow_go<16, 2>(a, s, sms, st); break;
-            case 8: e = flow_go<8, 2>(a, s, sms, st); break;
-            case 4: e = flow_go<4, 2>(a, s, sms, st); break;
-            case 2: e = flow_go<2, 2>(a, s, sms, st); break;
-            default: e = flow_go<1, 2>(a, s, sms, st); break;
-            }
-            break;
-        case 4:
-            switch (s.K) {
-            case 16: e = flow_go<16, 4>(a, s, sms, st); break;
-            case 8: e = flow_go<8, 4>(a, s, sms, st); break;
-            case 4: e = flow_go<4, 4>(a, s, sms, st); break;
-            case 2: e = flow_go<2, 4>(a, s, sms, st); break;
-            default: e = flow_go<1, 4>(a, s, sms, st); break;
-            }
-            break;
-        default:
-            switch (s.K) {
-            case 16: e = flow_go<16, 3>(a, s, sms, st); break;
-            case 8: e = flow_go<8, 3>(a, s, sms, st); break;
-            case 4: e = flow_go<4, 3>(a, s, sms, st); break;
-            case 2: e = flow_go<2, 3>(a, s, sms, st); break;
-            default: e = flow_go<1, 3>(a, s, sms, st); break;
-            }
-            break;
+        case 2: e = flow_go_k<2>(a, s, sms, st); break;
+        case 4: e = flow_go_k<4>(a, s, sms, st); break;
+        default: e = flow_go_k<3>(a, s, sms, st); break;
         }
         if (e != cudaSuccess) return e;
     }

@@ -148,6 +148,8 @@ struct FlowShape {
     uint32_t arena = 0;       // event arena entries (power of two)
     bool smem_tables = false; // gap tables staged in shared memory
     size_t smem = 0;          // dynamic shared memory
+    bool global_arena = false;  // arena in a global scratch buffer (one slice of `arena` entries per CTA)
+    uint32_t garena_ctas = 0;   // CTAs the scratch buffer has slices for (global arena)
 };
 
 struct FlowCall {
@@ -155,6 +157,8 @@ struct FlowCall {
     uint64_t n_cols = 0, last_mask = 0;
     uint64_t *det = nullptr, *obs = nullptr;
     uint32_t *status = nullptr;
+    uint32_t *scratch = nullptr;  // global arena slices (FlowShape::global_arena)
+    size_t scratch_bytes = 0;
 };
 
 // Per-device scratch of the library: a status word that kernels set when a
@@ -309,7 +313,8 @@ void free_device_programs(tmcs_circuit *c);
 // Decoupled event-signature kernel (tmcs_flow.cu). flow_shape fills *out for
 // the given schedule, chunks per tile, CTA size and applier warps if that
 // shape fits `budget` bytes of dynamic shared memory.
-bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int appliers, size_t budget, FlowShape *out);
+bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int appliers, size_t budget, FlowShape *out,
+                bool global_arena = false);
 #ifdef __CUDACC__
 cudaError_t flow_launch(const SigProgram &G, uint32_t n_obs, const DeviceSig *ds, const FlowShape &s,
                         const FlowCall &call, int sms, cudaStream_t st);

@@ -1907,15 +1907,18 @@ static LaunchShape make_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const 
 // tile, `appliers` of its warps apply steps, the others walk. mode = 0 when
 // the shape does not fit.
 static LaunchShape make_shape_flow(const tmcs_circuit *c, uint64_t n_cols, const DeviceLimits &lim, int sched, int K,
-                                   int threads, int appliers) {
+                                   int threads, int appliers, bool global_arena = false) {
     LaunchShape s;
     s.mode = 0;
-    if (!flow_shape(c, sched, K, threads, appliers, lim.smem_optin - 1024, &s.flow)) return s;
+    if (!flow_shape(c, sched, K, threads, appliers, lim.smem_optin - 1024, &s.flow, global_arena)) return s;
+    // a global arena has one slice per resident CTA (at most two per SM)
+    if (global_arena) s.flow.garena_ctas = uint32_t(2 * lim.sms);
     s.mode = 7;
     s.sched = sched;
     s.K = K;
     s.threads = threads;
     s.warps = appliers;
+    s.group = global_arena ? 1 : 0;
     s.sms = lim.sms;
     s.smem = s.flow.smem;
     s.smem_tables = s.flow.smem_tables;
@@ -2014,6 +2017,33 @@ static cudaError_t launch_pipe(const SigArgs &a, const LaunchShape &s, cudaStrea
     return cudaGetLastError();
 }
 
+// ---- per-device scratch of the decoupled kernel's global arena (grow-only;
+// library-owned, allocated by the first call that needs it, which must not
+// be under stream capture)
+static std::mutex g_flow_scratch_mu;
+static std::map<int, std::pair<uint32_t *, size_t>> g_flow_scratch;
+
+static cudaError_t flow_scratch(size_t bytes, uint32_t **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_flow_scratch_mu);
+    auto &slot = g_flow_scratch[dev];
+    if (slot.second < bytes) {
+        if (slot.first) {
+            // in-flight kernels may still use the old buffer
+            if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+            cudaFree(slot.first);
+            slot = {nullptr, 0};
+        }
+        void *p = nullptr;
+        if ((e = cudaMalloc(&p, bytes)) != cudaSuccess) return e;
+        slot = {static_cast<uint32_t *>(p), bytes};
+    }
+    *out = slot.first;
+    return cudaSuccess;
+}
+
 static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream_t st,
                           const DeviceSig *ds = nullptr, const SigProgram *G = nullptr, uint32_t n_obs = 0) {
     if (s.mode == 7) {
@@ -2027,6 +2057,11 @@ static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream
         call.det = a0.det;
         call.obs = a0.obs;
         call.status = a0.status;
+        if (s.flow.global_arena) {
+            call.scratch_bytes = size_t(s.flow.garena_ctas) * s.flow.arena * 4;
+            const cudaError_t e = flow_scratch(call.scratch_bytes, &call.scratch);
+            if (e != cudaSuccess) return e;
+        }
         return flow_launch(*G, n_obs, ds, s.flow, call, s.sms, st);
     }
     if (s.mode == 5 || s.mode == 6) {
@@ -2139,10 +2174,17 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
     if (ds)
         for (int sched = 0; sched < int(c->sig.sched.size()); sched++) {
             if (c->sig.sched[sched].lag) continue;
-            for (int K = 1; K <= 8; K *= 2)
-                for (int app : {4, 8}) {
+            for (int K = 1; K <= 16; K *= 2)
+                for (int app : {8, 12}) {
                     const LaunchShape cs = make_shape_flow(c, n_cols, lim, sched, K, 1024, app);
+                    // the arena goes to global memory only where shared
+                    // memory leaves it small (its reads then cost an L2 trip)
+                    const bool small = cs.mode != 7 || cs.flow.arena < 16384u;
                     if (cs.mode == 7) cands.push_back(cs);
+                    if (small) {
+                        const LaunchShape cg = make_shape_flow(c, n_cols, lim, sched, K, 1024, app, true);
+                        if (cg.mode == 7) cands.push_back(cg);
+                    }
                 }
         }
     // With a signature program the frame kernels are compared through their
@@ -2230,7 +2272,8 @@ static LaunchShape choose_shape_sig(const tmcs_circuit *c, uint64_t n_cols, cons
         while (K > 1 && (K & (K - 1))) K--;
         const int tforce = env_int("TMCS_THREADS", 0);
         const int threads = (tforce >= 64 && tforce <= 1024 && tforce % 32 == 0) ? tforce : 1024;
-        return make_shape_flow(c, n_cols, lim, sched, K, threads, env_int("TMCS_FLOW_APPLIERS", 8));
+        return make_shape_flow(c, n_cols, lim, sched, K, threads, env_int("TMCS_FLOW_APPLIERS", 8),
+                               env_int("TMCS_FLOW_GLOBAL_ARENA", 0) > 0);
     }
     // tuning/testing knobs: TMCS_SIG_SCHED = schedule index among the barrier
     // schedules (0 = largest ring window), or among the pipelined ones with
@@ -2314,8 +2357,8 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
         if ((mdp.tuned_mode == 5 || mdp.tuned_mode == 6) && ds)
             s = make_shape_sig(c, n_cols, lim, mdp.tuned_K, mdp.tuned_threads, mdp.tuned_sched);
         if (mdp.tuned_mode == 7 && ds) {
-            const LaunchShape f =
-                make_shape_flow(c, n_cols, lim, mdp.tuned_sched, mdp.tuned_K, mdp.tuned_threads, mdp.tuned_warps);
+            const LaunchShape f = make_shape_flow(c, n_cols, lim, mdp.tuned_sched, mdp.tuned_K, mdp.tuned_threads,
+                                                  mdp.tuned_warps, mdp.tuned_group == 1);
             if (f.mode == 7) s = f;
         }
     }

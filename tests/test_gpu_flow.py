@@ -165,3 +165,24 @@ def test_flow_sliced_launches(monkeypatch, slice_tiles, tile_k):
     gd, go = assert_flow_parity(monkeypatch, circ, "nl5", 64 * 1000 + 37, 41, first_chunk=11, TMCS_TILE_K=tile_k,
                                 TMCS_TEST_FLOW_SLICE_TILES=slice_tiles)
     assert gd.any() and go.any()
+
+
+@pytest.mark.parametrize("sched,tile_k,appliers,garena,cap", [(1, 8, 12, 0, 0), (2, 16, 8, 0, 0), (0, 4, 8, 1024, 0),
+                                                               (1, 8, 8, 0, 3), (0, 2, 4, 2048, 0)])
+def test_flow_global_arena(monkeypatch, sched, tile_k, appliers, garena, cap):
+    """The event arena in a global scratch buffer (one L2-resident slice per
+    CTA) instead of shared memory: same bits, also with a small arena
+    (steps gated on the appliers) and with forced region overflow."""
+    env = dict(TMCS_SIG_SCHED=sched, TMCS_TILE_K=tile_k, TMCS_FLOW_APPLIERS=appliers, TMCS_FLOW_GLOBAL_ARENA=1)
+    if garena:
+        env["TMCS_FLOW_GARENA"] = garena
+    if cap:
+        env["TMCS_TEST_FLOW_CAP"] = cap
+    gd, go = assert_flow_parity(monkeypatch, nl11(), "nl11", 64 * 19 + 45, 29, first_chunk=3, **env)
+    assert gd.any() and go.any()
+
+
+def test_flow_global_arena_many_tiles(monkeypatch):
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc5"), 6, 6, C.NoiseModel(0.01, 0.05))
+    assert_flow_parity(monkeypatch, circ, "nl5", 64 * 2002 - 5, 41, first_chunk=11, TMCS_TILE_K=8,
+                       TMCS_FLOW_GLOBAL_ARENA=1, TMCS_FLOW_GARENA=4096)
