@@ -258,7 +258,7 @@ def main():
     shape = tmcs.tmcs_launch_shape(sampler.handle)
     kernel = shape["kernel"] or "autotuner not run (call below its size threshold)"
     traffic = None
-    sha = _kernel_sha()
+    sha = _kernel_sha(kernel)
     for fn in sorted(os.listdir(os.path.join(ROOT, "profiles"))):
         if not fn.endswith("_traffic.json"):
             continue
@@ -657,14 +657,18 @@ def _strip_comments(src: str) -> str:
     return re.sub(r"\s+", "", "".join(out))
 
 
-def _kernel_sha():
-    """Hash of the sampler's device and host sources, comments and
+def _kernel_sha(kernel=None):
+    """Hash of the sources that define a kernel (its device code, the device
+    primitives it uses and the program layout it reads), comments and
     whitespace excluded: a committed traffic figure stays attached to the
     kernel build it was measured on."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("tmcs_sample.cu", "tmcs_flow.cu", "tmcs_device.cuh", "tmcs_internal.h", "tmcs_host.cpp",
-              "tmcs_signature.cpp"):
+    if kernel and kernel.startswith("flow_kernel"):
+        files = ("tmcs_flow.cu", "tmcs_device.cuh", "tmcs_internal.h", "tmcs_signature.cpp")
+    else:
+        files = ("tmcs_sample.cu", "tmcs_device.cuh", "tmcs_internal.h", "tmcs_host.cpp", "tmcs_signature.cpp")
+    for f in files:
         with open(os.path.join(ROOT, "paper_2504_05611_gb300", "csrc", f)) as fh:
             h.update(_strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]

@@ -360,13 +360,24 @@ int tmcs_check_device(void);
  * The launch shape the autotuner chose for this circuit on the current
  * device (for reports): *mode = 0 if it has not run yet (first large call),
  * 3 = CTA-wide frame kernel, 4 = warp-group frame kernel, 5 = event-signature
- * kernel, 6 = pipelined event-signature kernel; *chunks = 64-shot chunks per
- * CTA (modes 3, 5, 6) or per warp group (mode 4); *threads = CTA size;
- * *ring_window = detector ring of the chosen event-signature schedule
- * (modes 5, 6; 0 otherwise). Any pointer may be NULL.
+ * kernel, 6 = pipelined event-signature kernel, 7 = decoupled
+ * event-signature kernel; *chunks = 64-shot chunks per CTA (modes 3, 5, 6,
+ * 7) or per warp group (mode 4); *threads = CTA size; *ring_window =
+ * detector ring of the chosen event-signature schedule (modes 5, 6, 7; 0
+ * otherwise). Any pointer may be NULL.
  * Errors: TMCS_E_INVALID (NULL circuit), TMCS_E_CUDA (no current device).
  */
 int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *threads, int *ring_window);
+
+/*
+ * The decoupled kernel's part of the chosen shape (mode 7; zeros otherwise):
+ * applier warps, Philox calls per walker window, whether the event arena is
+ * in global memory, and the arena's entries (per CTA). Together with
+ * tmcs_launch_shape this fixes the launch (for reports and for forcing the
+ * same shape with the tuning knobs). Any pointer may be NULL.
+ * Errors: as tmcs_launch_shape.
+ */
+int tmcs_launch_flow_shape(const tmcs_circuit *c, int *appliers, int *window, int *global_arena, int *arena_entries);
 
 /*
  * Measured non-HBM ceilings of the current device, for roofline reports (the

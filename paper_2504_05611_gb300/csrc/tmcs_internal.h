@@ -100,6 +100,19 @@ struct SigStep;
 constexpr int kSigMaxSchedules = 9;  // schedules an event-signature program carries
 constexpr int kSigMaxLag = 4;        // steps in flight in a pipelined schedule
 
+struct FlowShape {
+    int sched = 0;            // barrier schedule of the signature program
+    int K = 4;                // chunks per tile
+    int threads = 1024;
+    int appliers = 8;         // applier warps (the other warps walk)
+    int window = 3;           // Philox calls per walker window (2..4)
+    uint32_t arena = 0;       // event arena entries (power of two)
+    bool smem_tables = false; // gap tables staged in shared memory
+    size_t smem = 0;          // dynamic shared memory
+    bool global_arena = false;  // arena in a global scratch buffer (one slice of `arena` entries per CTA)
+    uint32_t garena_ctas = 0;   // CTAs the scratch buffer has slices for (global arena)
+};
+
 // One device copy of a program.
 struct DeviceProgram {
     int device = -1;
@@ -116,6 +129,7 @@ struct DeviceProgram {
     int tuned_group = 0;
     int tuned_threads = 0;
     int tuned_sched = 0;    // event-signature schedule the autotuner chose
+    FlowShape tuned_flow;   // mode 7: the decoupled kernel's shape
 };
 
 // One device copy of an event-signature program.
@@ -139,18 +153,7 @@ struct DeviceSig {
 // schedules (lag 0) of at most kFlowMaxSteps steps.
 constexpr uint32_t kFlowMaxSteps = 1024;
 
-struct FlowShape {
-    int sched = 0;            // barrier schedule of the signature program
-    int K = 4;                // chunks per tile
-    int threads = 1024;
-    int appliers = 8;         // applier warps (the other warps walk)
-    int window = 3;           // Philox calls per walker window (2..4)
-    uint32_t arena = 0;       // event arena entries (power of two)
-    bool smem_tables = false; // gap tables staged in shared memory
-    size_t smem = 0;          // dynamic shared memory
-    bool global_arena = false;  // arena in a global scratch buffer (one slice of `arena` entries per CTA)
-    uint32_t garena_ctas = 0;   // CTAs the scratch buffer has slices for (global arena)
-};
+
 
 struct FlowCall {
     uint32_t key0 = 0, key1 = 0, first_chunk = 0;

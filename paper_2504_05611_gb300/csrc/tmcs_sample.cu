@@ -2017,18 +2017,19 @@ static cudaError_t launch_pipe(const SigArgs &a, const LaunchShape &s, cudaStrea
     return cudaGetLastError();
 }
 
-// ---- per-device scratch of the decoupled kernel's global arena (grow-only;
-// library-owned, allocated by the first call that needs it, which must not
-// be under stream capture)
+// ---- scratch of the decoupled kernel's global arena: one grow-only buffer
+// per (device, stream), so launches on different streams never share arena
+// slices (library-owned; allocated by the first call on that stream that
+// needs it, which must not be under stream capture)
 static std::mutex g_flow_scratch_mu;
-static std::map<int, std::pair<uint32_t *, size_t>> g_flow_scratch;
+static std::map<std::pair<int, cudaStream_t>, std::pair<uint32_t *, size_t>> g_flow_scratch;
 
-static cudaError_t flow_scratch(size_t bytes, uint32_t **out) {
+static cudaError_t flow_scratch(cudaStream_t st, size_t bytes, uint32_t **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_flow_scratch_mu);
-    auto &slot = g_flow_scratch[dev];
+    auto &slot = g_flow_scratch[{dev, st}];
     if (slot.second < bytes) {
         if (slot.first) {
             // in-flight kernels may still use the old buffer
@@ -2059,7 +2060,7 @@ static cudaError_t launch(const KernelArgs &a0, const LaunchShape &s, cudaStream
         call.status = a0.status;
         if (s.flow.global_arena) {
             call.scratch_bytes = size_t(s.flow.garena_ctas) * s.flow.arena * 4;
-            const cudaError_t e = flow_scratch(call.scratch_bytes, &call.scratch);
+            const cudaError_t e = flow_scratch(st, call.scratch_bytes, &call.scratch);
             if (e != cudaSuccess) return e;
         }
         return flow_launch(*G, n_obs, ds, s.flow, call, s.sms, st);
@@ -2176,15 +2177,10 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
             if (c->sig.sched[sched].lag) continue;
             for (int K = 1; K <= 16; K *= 2)
                 for (int app : {8, 12}) {
+                    // shared-memory arena (the global-memory arena, a tuning
+                    // knob, measured no faster: its reads cost an L2 trip)
                     const LaunchShape cs = make_shape_flow(c, n_cols, lim, sched, K, 1024, app);
-                    // the arena goes to global memory only where shared
-                    // memory leaves it small (its reads then cost an L2 trip)
-                    const bool small = cs.mode != 7 || cs.flow.arena < 16384u;
                     if (cs.mode == 7) cands.push_back(cs);
-                    if (small) {
-                        const LaunchShape cg = make_shape_flow(c, n_cols, lim, sched, K, 1024, app, true);
-                        if (cg.mode == 7) cands.push_back(cg);
-                    }
                 }
         }
     // With a signature program the frame kernels are compared through their
@@ -2253,6 +2249,7 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
     mdp.tuned_group = chosen.group;
     mdp.tuned_threads = chosen.threads;
     mdp.tuned_sched = chosen.sched;
+    mdp.tuned_flow = chosen.mode == 7 ? chosen.flow : FlowShape();
     return TMCS_OK;
 }
 
@@ -2976,6 +2973,22 @@ int tmcs_launch_shape(const tmcs_circuit *c, int *mode, int *chunks, int *thread
                            ? int(c->sig.sched[k].window)
                            : 0;
     }
+    return TMCS_OK;
+}
+
+int tmcs_launch_flow_shape(const tmcs_circuit *c, int *appliers, int *window, int *global_arena, int *arena_entries) {
+    if (!c) return fail(TMCS_E_INVALID, "circuit is NULL");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(c->mu);
+    auto it = c->dev.find(dev);
+    const bool flow = it != c->dev.end() && it->second.tuned_mode == 7;
+    const FlowShape f = flow ? it->second.tuned_flow : FlowShape();
+    if (appliers) *appliers = flow ? f.appliers : 0;
+    if (window) *window = flow ? f.window : 0;
+    if (global_arena) *global_arena = flow && f.global_arena ? 1 : 0;
+    if (arena_entries) *arena_entries = flow ? int(f.arena) : 0;
     return TMCS_OK;
 }
 

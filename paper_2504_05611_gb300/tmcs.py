@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
         L.tmcs_fault_outputs.argtypes = [P, U64, P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
         L.tmcs_dem_columns.argtypes = [P, ctypes.POINTER(U64), ctypes.POINTER(U64), P, P, P, P]
         L.tmcs_launch_shape.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
+        L.tmcs_launch_flow_shape.argtypes = [P] + [ctypes.POINTER(I)] * 4
         L.tmcs_measure_peaks.argtypes = [P]
         L.tmcs_server_open.argtypes = [P, ctypes.POINTER(P)]
         L.tmcs_server_submit.argtypes = [P, P, U64, U64, ctypes.POINTER(ctypes.c_uint64)]
@@ -116,7 +117,7 @@ def lib() -> ctypes.CDLL:
                   "tmcs_server_submit", "tmcs_server_poll", "tmcs_server_fetch", "tmcs_server_release",
                   "tmcs_server_get_stats", "tmcs_server_close", "tmcs_fault_count", "tmcs_fault_signatures",
                   "tmcs_sample_measurements", "tmcs_fault_outputs", "tmcs_launch_shape", "tmcs_measure_peaks",
-                  "tmcs_dem_columns"):
+                  "tmcs_dem_columns", "tmcs_launch_flow_shape"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -329,11 +330,18 @@ def tmcs_launch_shape(handle: int) -> Dict[str, object]:
     m, k, t, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().tmcs_launch_shape(ctypes.c_void_p(handle), ctypes.byref(m), ctypes.byref(k), ctypes.byref(t),
                                    ctypes.byref(w)))
+    ap, win, ga, ae = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().tmcs_launch_flow_shape(ctypes.c_void_p(handle), ctypes.byref(ap), ctypes.byref(win),
+                                        ctypes.byref(ga), ctypes.byref(ae)))
     name = KERNEL_NAMES.get(m.value)
     label = None
     if name:
-        label = f"{name}<{k.value}> ({t.value} threads" + (f", ring {w.value})" if w.value else ")")
-    return {"mode": m.value, "chunks": k.value, "threads": t.value, "ring_window": w.value, "kernel": label}
+        extra = f", ring {w.value}" if w.value else ""
+        if m.value == 7:
+            extra += f", {ap.value} applier warps, window {win.value}" + (", global arena" if ga.value else "")
+        label = f"{name}<{k.value}> ({t.value} threads{extra})"
+    return {"mode": m.value, "chunks": k.value, "threads": t.value, "ring_window": w.value, "kernel": label,
+            "appliers": ap.value, "window": win.value, "global_arena": ga.value, "arena_entries": ae.value}
 
 
 class _Peaks(ctypes.Structure):
