@@ -176,12 +176,22 @@ int tmcs_reference_sample(const tmcs_circuit *c, uint8_t *meas_bits);
  * shared-memory arena, applier warps apply whole steps), TMCS_TILE_K,
  * TMCS_THREADS, TMCS_SIG_SCHED (signature schedule index), TMCS_FLOW_APPLIERS
  * and TMCS_FLOW_ARENA (kernel 7: applier warps, arena entries),
+ * TMCS_FLOW_WINDOW (kernel 7: Philox calls per walker pass, 2 to 4),
+ * TMCS_FLOW_GLOBAL_ARENA=1 and TMCS_FLOW_GARENA (kernel 7: the arena in a
+ * per-stream global scratch buffer, its entries per CTA), TMCS_FLOW_TMA
+ * and TMCS_FLOW_TMA_ROWS (kernel 7 with 8 or more chunks per tile, or any
+ * even number with TMCS_FLOW_TMA=1, writes finished detector rows as 2D
+ * tensor stores, boxes of that many rows (default 64) by the tile's chunks,
+ * when detector_bits is 16-byte aligned and ceil(shots/64) is even;
+ * TMCS_FLOW_TMA=0 never; other outputs take plain stores),
  * TMCS_SIG_WINDOW (read by tmcs_circuit_build), TMCS_AUTOTUNE=0.
  * Testing: TMCS_TEST_STALL_FLUSH=1 makes the pipelined kernel's flusher wait
  * for a stream count that never arrives, so its bounded wait (2 s) expires,
  * every warp leaves and tmcs_check_device reports TMCS_E_TIMEOUT.
  * TMCS_TEST_FLOW_CAP=n gives every step of kernel 7 an arena region of n
- * events, so most events take its overflow path (same bits).
+ * events, so most events take its overflow path (same bits);
+ * TMCS_TEST_FLOW_SLICE_TILES=n splits a kernel-7 call into launches of n
+ * tiles (the path huge calls take to keep 32-bit stream counters).
  * Errors: TMCS_E_INVALID (NULL circuit/buffer, shots == 0), TMCS_E_CUDA,
  * TMCS_E_OOM (program upload).
  */

@@ -29,6 +29,7 @@
 // window of detectors, while the arena keeps several steps of walking in
 // flight. All waits are bounded (kWaitNs); on expiry the kernel sets bit 0
 // of the status word and every warp leaves.
+#include <cuda.h>  // CUtensorMap (encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,6 +52,7 @@ constexpr uint32_t kFlowMinArena = 1024;  // smallest useful arena (entries)
 constexpr uint32_t kFlowMaxArena = 65536;
 
 struct FlowArgs {
+    CUtensorMap tmap;           // det as a [n_det][ld] uint64 tensor (tensor-store flush), when tma_rows > 0
     const NoiseDesc *noise;
     const uint32_t *tables;
     const uint4 *item_desc;     // walker descriptors, two uint4 per item (see SigSchedule::item_desc)
@@ -67,6 +69,8 @@ struct FlowArgs {
     uint64_t n_cols, last_mask, n_tiles;
     uint64_t ld;                // words between output rows (the call's column count; a launch may cover a slice)
     uint32_t *garena;           // arena in global memory (a slice of `arena` entries per CTA), or null
+    uint32_t tma_rows;          // detector rows per tensor-store box of the flush (0: plain stores)
+    uint64_t col_base;          // column of this launch's column 0 in the tensor map (sliced launches)
     uint64_t *det;
     uint64_t *obs;
     uint32_t *status;
@@ -369,6 +373,109 @@ __device__ __forceinline__ void flow_bar(uint32_t nthreads) {
     asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(shared_addr(src))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Flush of detectors [z, w) with tensor stores: the rows of each ring
+// segment (at most two: the ring wraps) go out as boxes of tma_rows rows x K
+// chunk words issued by the first applier warp, starting at a ring row whose
+// address is 128-byte aligned; the few rows before that point and after the
+// last whole box are written with plain stores. Every row is cleared: the
+// boxes' rows once the tensor stores have read them. The last column of the
+// call (in the call's last tile) gets its pad bits masked in the ring first.
+// Every applier has fenced its ring writes for the async proxy before the
+// barrier that precedes this call. Ends with the boxes' rows cleared; the
+// caller's barrier follows.
+// Rows [d0, d1) of one contiguous stretch of the ring: plain head rows
+// [d0, dh) up to the first 128-byte aligned ring row, whole boxes [dh, db),
+// plain tail rows [db, d1).
+struct FlushSeg {
+    uint32_t d0, dh, db, d1;
+};
+
+template <int K>
+__device__ __forceinline__ FlushSeg flush_seg(uint32_t d, uint32_t e, uint32_t mask, uint32_t R) {
+    constexpr uint32_t AL = K >= 16 ? 1u : 16u / uint32_t(K);  // ring rows per 128 bytes
+    FlushSeg g;
+    g.d0 = d;
+    g.d1 = e;
+    g.dh = min(e, d + (AL - (d & mask) % AL) % AL);
+    g.db = g.dh + (e - g.dh) / R * R;
+    return g;
+}
+
+template <int K>
+__device__ __forceinline__ void flush_plain_rows(const FlowArgs &A, const FlowSmem &S, const FlushSeg &g,
+                                                 uint64_t col0, uint32_t nv, uint32_t at, uint32_t nthr) {
+    const uint32_t nh = g.dh - g.d0, nt = g.d1 - g.db;
+    for (uint32_t i = at; i < (nh + nt) * uint32_t(K); i += nthr) {
+        const uint32_t row = i / uint32_t(K), k = i % uint32_t(K);
+        const uint32_t d = row < nh ? g.d0 + row : g.db + (row - nh);
+        uint64_t *r = S.ring + size_t(d & A.window_mask) * K + k;
+        const uint64_t v = *r;
+        *r = 0ull;
+        if (k < nv) __stcs(reinterpret_cast<unsigned long long *>(A.det + uint64_t(d) * A.ld + col0 + k), v);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void flush_clear_boxes(const FlowArgs &A, const FlowSmem &S, const FlushSeg &g,
+                                                  uint32_t at, uint32_t nthr) {
+    ulonglong2 *base = reinterpret_cast<ulonglong2 *>(S.ring + size_t(g.dh & A.window_mask) * K);
+    const uint32_t nw = (g.db - g.dh) * uint32_t(K) / 2u;
+    for (uint32_t i = at; i < nw; i += nthr) base[i] = make_ulonglong2(0ull, 0ull);
+}
+
+// Flush of detectors [z, w) (w - z at most the ring's rows) with tensor
+// stores: the rows of each stretch of the ring (at most two: the ring wraps)
+// go out as boxes of tma_rows rows x K chunk words issued by the first
+// applier warp, each starting at a 128-byte aligned ring row; the few rows
+// before the first aligned row and after the last whole box are written with
+// plain stores. Every row is cleared: the boxes' rows once the tensor stores
+// have read them. The call's last column (in the call's last tile) gets its
+// pad bits masked in the ring first. Every applier has fenced its ring
+// writes for the async proxy before the barrier that precedes this call.
+// Ends with the boxes' rows cleared; the caller's barrier follows.
+template <int K>
+__device__ __forceinline__ void flow_flush_tma(const FlowArgs &A, const FlowSmem &S, uint32_t z, uint32_t w,
+                                               uint64_t col0, uint32_t nv, uint32_t at, uint32_t nthr) {
+    const uint32_t mask = A.window_mask, R = A.tma_rows;
+    if (col0 + uint64_t(K) > A.n_cols - 1) {  // this tile holds the call's last column
+        const uint32_t kl = uint32_t(A.n_cols - 1 - col0);
+        for (uint32_t i = at; i < w - z; i += nthr) S.ring[size_t((z + i) & mask) * K + kl] &= A.last_mask;
+        fence_proxy_async_shared();
+        flow_bar(nthr);
+    }
+    const uint32_t split = min(w, z + (mask + 1u - (z & mask)));  // first row past the ring's end
+    const FlushSeg g0 = flush_seg<K>(z, split, mask, R), g1 = flush_seg<K>(split, w, mask, R);
+    const uint32_t n0 = (g0.db - g0.dh) / R, nbox = n0 + (g1.db - g1.dh) / R;
+    const bool issuer = at < 32u;
+    if (issuer) {
+        const int x = int(A.col_base + col0);
+        for (uint32_t b = at; b < nbox; b += 32u) {
+            const uint32_t d = b < n0 ? g0.dh + b * R : g1.dh + (b - n0) * R;
+            tma_store_2d(&A.tmap, x, int(d), S.ring + size_t(d & mask) * K);
+        }
+        tma_commit();
+    }
+    flush_plain_rows<K>(A, S, g0, col0, nv, at, nthr);
+    flush_plain_rows<K>(A, S, g1, col0, nv, at, nthr);
+    if (issuer) tma_wait_read();
+    flow_bar(nthr);
+    flush_clear_boxes<K>(A, S, g0, at, nthr);
+    flush_clear_boxes<K>(A, S, g1, at, nthr);
+}
+
 // Applier warps: steps in CTA order.
 template <int K, bool GA>
 __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S, FlowCtl &C, uint32_t nt,
@@ -380,6 +487,11 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
     const uint32_t obs_row = A.window_mask + 1u;
     const uint2 *ev2 = reinterpret_cast<const uint2 *>(A.ev_ent);
     const uint32_t *const arena = GA ? A.garena + size_t(blockIdx.x) * A.arena : S.arena;
+    // tensor-store flush: needs the ring 128-byte aligned in shared memory
+    // and boxes of a whole number of 128-byte ring stretches (each box then
+    // starts aligned)
+    const bool tma = (K % 2 == 0) && A.tma_rows != 0 && (A.tma_rows * uint32_t(K)) % 16u == 0 &&
+                     (shared_addr(S.ring) & 127u) == 0;
     uint32_t U = 0;  // arena position of step Q, modulo 2^32
     for (uint32_t T = 0; T < nt; T++) {
         const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(T) * gridDim.x;
@@ -414,7 +526,10 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
                 C.app_stop = stop;
             }
             flow_bar(nthr);
-            if (C.app_stop) return;
+            if (C.app_stop) {
+                if (tma && at < 32u) tma_wait_all();
+                return;
+            }
             __threadfence_block();  // the walkers' events precede the reads below
             const uint32_t n = min(ld_shared_volatile(&C.cnt[slot]), S.scap[q]);
             const uint32_t u0 = U;
@@ -433,12 +548,16 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
 #pragma unroll
                 for (uint32_t j = 0; j < kFlowApplyBatch; j++) flow_put<K>(A, S.ring, wv[j], v[j]);
             }
+            if (tma) fence_proxy_async_shared();  // ring writes before the tensor stores read them
             flow_bar(nthr);
             // detectors [flush_lo, flush_hi) are final: write and clear them
             const uint32_t nd = st.w - st.z;
             bool vec_done = false;
             if constexpr (K % 2 == 0) {
-                if (A.vec_out) {
+                if (tma) {
+                    vec_done = true;
+                    flow_flush_tma<K>(A, S, st.z, st.w, col0, nv, at, nthr);
+                } else if (A.vec_out) {
                     vec_done = true;
                     constexpr uint32_t H = uint32_t(K) / 2u;
                     for (uint32_t i = at; i < nd * H; i += nthr) {
@@ -494,6 +613,7 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
             }
         }
     }
+    if (tma && at < 32u) tma_wait_all();  // the tensor stores have written the outputs
 }
 
 // CTA size the kernel is compiled for (its register budget follows from it)
@@ -502,7 +622,7 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
 #endif
 
 template <int K, int W, bool GA>
-__global__ void __launch_bounds__(TMCS_FLOW_MAX_THREADS, 1) flow_kernel(const FlowArgs A) {
+__global__ void __launch_bounds__(TMCS_FLOW_MAX_THREADS, 1) flow_kernel(const __grid_constant__ FlowArgs A) {
     extern __shared__ __align__(128) uint64_t smem[];
     __shared__ FlowCtl C;
     if (uint64_t(blockIdx.x) >= A.n_tiles) return;
@@ -629,6 +749,46 @@ bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int applie
     return true;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null if unavailable
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// Tensor map of the call's detector words for the tensor-store flush: a
+// [n_det][ld] uint64 tensor, boxes of K chunk words x rows detectors. Needs
+// K >= 2 (16-byte box rows), a 16-byte aligned buffer, an even row stride
+// and coordinates below 2^31; returns false otherwise.
+static bool encode_det_map(CUtensorMap *map, uint64_t *det, uint64_t n_det, uint64_t ld, int K, uint32_t rows) {
+    if (K < 2 || !det || reinterpret_cast<uintptr_t>(det) % 16 || ld % 2 || ld >= (uint64_t(1) << 31) ||
+        n_det == 0 || n_det >= (uint64_t(1) << 31) || rows == 0 || rows > 256)
+        return false;
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dim[2] = {ld, n_det};
+    const cuuint64_t stride[1] = {ld * 8};
+    const cuuint32_t box[2] = {cuuint32_t(K), rows};
+    const cuuint32_t estride[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, det, dim, stride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 template <int K, int W, bool GA>
 static cudaError_t flow_go(const FlowArgs &a, const FlowShape &s, int sms, cudaStream_t st) {
     auto kern = flow_kernel<K, W, GA>;
@@ -692,6 +852,16 @@ cudaError_t flow_launch(const SigProgram &G, uint32_t n_obs, const DeviceSig *ds
     a.key0 = call.key0;
     a.key1 = call.key1;
     a.ld = call.n_cols;
+    // tensor-store flush: by default for tiles of 8 or more chunks (rows of
+    // 64 bytes or more; narrower boxes measured slower than plain stores);
+    // TMCS_FLOW_TMA=1 for any even tile, 0 never; TMCS_FLOW_TMA_ROWS sets
+    // the rows per box (default 64, rounded up to whole 128-byte stretches
+    // of the ring)
+    const uint32_t al = s.K >= 16 ? 1u : 16u / uint32_t(std::max(s.K, 1));
+    const uint32_t trows = (uint32_t(std::max(env_int_flow("TMCS_FLOW_TMA_ROWS", 64), 1)) + al - 1) / al * al;
+    const int tma = env_int_flow("TMCS_FLOW_TMA", -1);
+    if ((tma > 0 || (tma < 0 && s.K >= 8)) && encode_det_map(&a.tmap, call.det, G.n_det, call.n_cols, s.K, trows))
+        a.tma_rows = trows;
     if (s.garena_ctas) {
         if (!call.scratch || call.scratch_bytes < size_t(s.garena_ctas) * s.arena * 4) return cudaErrorInvalidValue;
         a.garena = call.scratch;
@@ -716,6 +886,7 @@ cudaError_t flow_launch(const SigProgram &G, uint32_t n_obs, const DeviceSig *ds
         a.last_mask = c0 + n == call.n_cols ? call.last_mask : ~uint64_t(0);
         a.n_tiles = (n + uint64_t(s.K) - 1) / uint64_t(s.K);
         a.det = call.det + c0;
+        a.col_base = c0;
         a.obs = call.obs ? call.obs + c0 : nullptr;
         a.vec_out = (reinterpret_cast<uintptr_t>(a.det) % 16 == 0 && a.ld % 2 == 0) ? 1u : 0u;
         a.status = call.status;

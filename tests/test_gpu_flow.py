@@ -186,3 +186,50 @@ def test_flow_global_arena_many_tiles(monkeypatch):
     circ = C.nonlocal_cnot_circuit(C.code_by_name("sc5"), 6, 6, C.NoiseModel(0.01, 0.05))
     assert_flow_parity(monkeypatch, circ, "nl5", 64 * 2002 - 5, 41, first_chunk=11, TMCS_TILE_K=8,
                        TMCS_FLOW_GLOBAL_ARENA=1, TMCS_FLOW_GARENA=4096)
+
+
+@pytest.mark.parametrize("sched,tile_k,rows,appliers", [(1, 8, 16, 12), (1, 8, 2, 8), (0, 2, 8, 8), (0, 4, 4, 1),
+                                                        (2, 16, 1, 8), (2, 16, 64, 2), (0, 4, 256, 8), (1, 8, 0, 12)])
+def test_flow_tensor_store_flush(monkeypatch, sched, tile_k, rows, appliers):
+    """Detector rows leave the ring as 2D tensor stores (boxes of rows x K
+    chunk words, head and tail rows around the aligned boxes by plain
+    stores): same bits for any box height, with the ring wrapping under the
+    boxes, several tiles per CTA and the last tile partly outside the output
+    (its columns past the call's end are clipped). rows = 0 turns the tensor
+    stores off."""
+    env = dict(TMCS_SIG_SCHED=sched, TMCS_TILE_K=tile_k, TMCS_FLOW_APPLIERS=appliers)
+    env["TMCS_FLOW_TMA"] = 1 if rows else 0
+    if rows:
+        env["TMCS_FLOW_TMA_ROWS"] = rows
+    # 20 columns: the last tile of K = 8 or 16 holds 4 columns
+    gd, go = assert_flow_parity(monkeypatch, nl11(), "nl11", 64 * 19 + 45, 29, first_chunk=3, **env)
+    assert gd.any() and go.any()
+    circ = C.nonlocal_cnot_circuit(C.code_by_name("sc5"), 6, 6, C.NoiseModel(0.01, 0.05))
+    assert_flow_parity(monkeypatch, circ, "nl5", 64 * 2002 - 5, 41, first_chunk=11, **env)
+
+
+@pytest.mark.parametrize("offset_words", [1, 2])
+def test_flow_flush_unaligned_outputs(monkeypatch, offset_words):
+    """An output buffer that does not start on a 16-byte boundary (one word
+    in) cannot be a tensor map: the flush falls back to plain stores; two
+    words in (16-byte aligned) it uses the tensor stores."""
+    monkeypatch.setenv("TMCS_KERNEL", "7")
+    monkeypatch.setenv("TMCS_TILE_K", "4")
+    monkeypatch.setenv("TMCS_FLOW_TMA", "1")
+    circ = nl11()
+    shots, seed, first = 64 * 19 + 45, 29, 3
+    s = tmcs.Sampler(circ)
+    try:
+        n_det, n_obs, cols = s.info["n_det"], s.info["n_obs"], (shots + 63) // 64
+        flat = torch.full((n_det * cols + offset_words,), -1, dtype=torch.int64, device="cuda")
+        det = flat[offset_words:].view(n_det, cols)
+        obs = torch.empty((max(n_obs, 1), cols), dtype=torch.int64, device="cuda")
+        s.sample(shots, seed, first_chunk=first, out=(det, obs))
+        torch.cuda.synchronize()
+        tmcs.tmcs_check_device()
+        od, oo = oracle_sample(circ, "nl11", shots, seed, first)
+        assert np.array_equal(det.cpu().numpy().view(np.uint64), od)
+        assert np.array_equal(obs[:n_obs].cpu().numpy().view(np.uint64), oo)
+        assert int(flat[:offset_words].eq(-1).sum()) == offset_words  # nothing written before the buffer
+    finally:
+        s.close()
