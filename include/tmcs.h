@@ -472,6 +472,21 @@ const char *tmcs_last_error(void);
  */
 int tmcs_debug_gap_table(double p, uint32_t *table);
 
+/*
+ * Gap counts G = #{g in 1..4096 : w < T[g]} of the table above for n words,
+ * computed on the current device by the routines the sampling kernels use:
+ * method 0 as the decoupled kernel's walkers count (one table read guided by
+ * a float estimate when |1/log2(1-p)| < 32768, else method 1), 1 the
+ * two-read count with neighbour walks, 2 the log estimate with neighbour
+ * loops (kernels 3 to 6 count as method 0 does where one read is allowed,
+ * else by method 2). words and counts are device pointers to n uint32
+ * and n int32. Blocks until done (on `stream`). Exported so tests can check
+ * every route against the definition, words at the table's boundaries
+ * included. Errors: TMCS_E_INVALID (NULL pointer, p outside (0, 1], bad
+ * method), TMCS_E_CUDA.
+ */
+int tmcs_debug_gap_counts(double p, const uint32_t *words, uint64_t n, int32_t *counts, int method, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

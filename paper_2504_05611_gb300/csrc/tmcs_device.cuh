@@ -145,6 +145,40 @@ __device__ __forceinline__ int gap_count_est(const uint32_t *__restrict__ T, flo
     return g;
 }
 
+// Gap count with a single table read, for tables with |inv_log2| below
+// kNearInv (p above about 2.1e-5). The count is floor(x) clamped to
+// [0, kGapLen] for the real x = (log2(w + 1) - 32) / log2(1 - p), since
+// w < floor(2^32 (1-p)^g) holds exactly when g <= x; the host's rounding of
+// the table moves that boundary only where x lies within 1e-9 of an integer.
+// est = fma(log2f(w + 1), inv_log2, c32) with c32 = -32 inv_log2 (exact in
+// float) differs from x by at most
+//   |inv| (|log2 error| + 32 * 2^-24) + |x| 2^-24
+// where the log2 error is at most 2^-17 + 2^-22.6 (CUDA documents __log2f to
+// 2 ulp of a result below 32, or 2^-22.6 absolute on [0.5, 2]; w + 1 is
+// formed with two float roundings): below 0.32 + 2.5e-4 for |inv| < 32768.
+// So with m = rint(est) the count is m or m - 1, and one comparison with
+// T[m] decides (clamping m to [1, kGapLen] keeps the answer right at both
+// ends). Same result as gap_count_t for every w of such a table.
+constexpr float kNearInv = 32768.0f;
+
+template <bool SMT>
+__device__ __forceinline__ int gap_count_near(const uint32_t *__restrict__ T, float inv_log2, float c32, uint32_t w) {
+    const float est = fmaf(__log2f(__uint2float_rn(w) + 1.0f), inv_log2, c32);
+    const int m = min(max(__float2int_rn(est), 1), int(kGapLen));
+    uint32_t t;
+    if constexpr (SMT) t = T[m - 1];
+    else t = __ldg(T + (m - 1));
+    return w < t ? m : m - 1;
+}
+
+// The count by one table read where the table allows it, else by the log
+// estimate with neighbour loops (per lane: lanes of one warp may differ).
+template <bool SMT>
+__device__ __forceinline__ int gap_count_fast(const uint32_t *__restrict__ T, float inv_log2, uint32_t w) {
+    if (fabsf(inv_log2) < kNearInv) return gap_count_near<SMT>(T, inv_log2, -32.0f * inv_log2, w);
+    return gap_count_t<SMT>(T, inv_log2, w);
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

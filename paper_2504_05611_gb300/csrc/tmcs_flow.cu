@@ -279,13 +279,26 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
                 // and discarded (the warp runs them for its other lanes)
                 uint32_t wp[NE];
                 int gp[NE];
+                // one table read per gap when every walking lane's p allows
+                // it (warp-uniform choice), else the two-read count
+                if (__all_sync(wm, fabsf(inv) < kNearInv)) {
 #pragma unroll
-                for (int c = 0; c < W; c++) {
-                    const uint4 w = philox_call(ps, call + uint32_t(c), A.key0, A.key1);
-                    gp[2 * c] = gap_count_est<SMT>(tabs + toff, inv, c32, w.x);
-                    gp[2 * c + 1] = gap_count_est<SMT>(tabs + toff, inv, c32, w.z);
-                    wp[2 * c] = w.y;
-                    wp[2 * c + 1] = w.w;
+                    for (int c = 0; c < W; c++) {
+                        const uint4 w = philox_call(ps, call + uint32_t(c), A.key0, A.key1);
+                        gp[2 * c] = gap_count_near<SMT>(tabs + toff, inv, c32, w.x);
+                        gp[2 * c + 1] = gap_count_near<SMT>(tabs + toff, inv, c32, w.z);
+                        wp[2 * c] = w.y;
+                        wp[2 * c + 1] = w.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < W; c++) {
+                        const uint4 w = philox_call(ps, call + uint32_t(c), A.key0, A.key1);
+                        gp[2 * c] = gap_count_est<SMT>(tabs + toff, inv, c32, w.x);
+                        gp[2 * c + 1] = gap_count_est<SMT>(tabs + toff, inv, c32, w.z);
+                        wp[2 * c] = w.y;
+                        wp[2 * c + 1] = w.w;
+                    }
                 }
                 call += uint32_t(W);
                 // positions in draw order: every draw before the one that

@@ -167,7 +167,7 @@ __device__ __forceinline__ void walk_segment(const NoiseDesc &nd, const uint32_t
         const uint32_t wg = (d & 1u) ? w.z : w.x;
         const uint32_t wp = (d & 1u) ? w.w : w.y;
         const int prev = pos;
-        pos += 1 + gap_count(T, inv, wg);
+        pos += 1 + gap_count_fast<false>(T, inv, wg);
         if (pos >= n_trials) break;
         const uint32_t pk = pauli_index(nd, npauli, wp);
         if (buf) {
@@ -550,7 +550,7 @@ __device__ __forceinline__ void walk_stream(const NoiseDesc &nd, const uint32_t 
         if ((d & 1u) == 0) w = philox4x32_10(d >> 1, chunk, nd.op_index, s, key0, key1);
         const uint32_t wg = (d & 1u) ? w.z : w.x;
         const uint32_t wp = (d & 1u) ? w.w : w.y;
-        pos += 1 + gap_count(T, inv, wg);
+        pos += 1 + gap_count_fast<false>(T, inv, wg);
         if (pos >= n_trials) break;
         sink(pos, pauli_index(nd, npauli, wp));
     }
@@ -683,7 +683,7 @@ __device__ __forceinline__ uint32_t sig_walk(const SigArgs &A, const uint4 st, u
             uint64_t q = 0;
             if (have) {
                 const uint32_t wg = h ? w.z : w.x, wp = h ? w.w : w.y;
-                pos += 1 + gap_count_t<SMT>(Tt, inv, wg);
+                pos += 1 + gap_count_fast<SMT>(Tt, inv, wg);
                 if (pos >= n_trials) {
                     have = false;
                 } else {
@@ -1006,7 +1006,7 @@ __device__ __forceinline__ void pipe_walk(const SigArgs &A, const PipeSmem &S, P
             uint64_t q = 0;
             if (have) {
                 const uint32_t wg = h ? w.z : w.x, wp = h ? w.w : w.y;
-                pos += 1 + gap_count_t<SMT>(tabs + toff, inv, wg);
+                pos += 1 + gap_count_fast<SMT>(tabs + toff, inv, wg);
                 if (pos >= n_trials) {
                     have = false;
                     fin = true;
@@ -1618,6 +1618,23 @@ static size_t kernel_smem_bytes(uint32_t n_slots, uint32_t max_window_segs, int 
     b += size_t(max_window_segs) * K * sizeof(EvUnit);
     b += 2 * 8 + 16;
     return b;
+}
+
+// Gap counts of words w by the device routines the kernels use (method 0:
+// the decoupled kernel's walkers, one table read when |inv_log2| <
+// kNearInv, else the two-read count; 1: the two-read count; 2: the log
+// estimate with neighbour loops, which kernels 3 to 6 use where the one
+// read is not allowed); table in global memory.
+__global__ void gap_counts_kernel(const uint32_t *__restrict__ T, float inv, float c32, const uint32_t *__restrict__ w,
+                                  uint64_t n, int method, int32_t *__restrict__ out) {
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
+        const uint32_t x = w[i];
+        int g;
+        if (method == 0 && fabsf(inv) < kNearInv) g = gap_count_near<false>(T, inv, c32, x);
+        else if (method <= 1) g = gap_count_est<false>(T, inv, c32, x);
+        else g = gap_count(T, inv, x);
+        out[i] = g;
+    }
 }
 
 // ------------------------------------------------------------- host code
@@ -2934,6 +2951,30 @@ int tmcs_fault_signatures(const tmcs_circuit *c, uint64_t first_fault, uint64_t 
     if (n_faults == 0 || first_fault + n_faults > c->prog.n_faults)
         return fail(TMCS_E_INVALID, "fault range outside [0, tmcs_fault_count)");
     return sample_range(c, 0, n_faults, 0, detector_bits, observable_bits, stream, true, first_fault);
+}
+
+int tmcs_debug_gap_counts(double p, const uint32_t *words, uint64_t n, int32_t *counts, int method, void *stream) {
+    if (!words || !counts) return fail(TMCS_E_INVALID, "null words or counts");
+    if (method < 0 || method > 2) return fail(TMCS_E_INVALID, "method must be 0, 1 or 2");
+    std::vector<uint32_t> tables;
+    std::vector<double> table_p;
+    uint32_t id = 0;
+    if (int rc = table_for_p(tables, table_p, p, &id)) return rc;
+    float inv = 0.f;
+    std::memcpy(&inv, &tables[kGapLen], 4);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t *T = nullptr;
+    cudaError_t e = cudaMalloc(&T, tables.size() * 4);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (gap table)");
+    e = cudaMemcpyAsync(T, tables.data(), tables.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n) {
+        const uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 4096);
+        gap_counts_kernel<<<unsigned(blocks), 256, 0, st>>>(T, inv, -32.0f * inv, words, n, method, counts);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(T);
+    return e == cudaSuccess ? TMCS_OK : cuda_fail(e, "gap counts");
 }
 
 int tmcs_check_device(void) {

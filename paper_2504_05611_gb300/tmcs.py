@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
         L.tmcs_sample_range.argtypes = [P, U64, U64, U64, P, P, P]
         L.tmcs_batch_sample.argtypes = [P, ctypes.c_size_t, P]
         L.tmcs_debug_gap_table.argtypes = [ctypes.c_double, P]
+        L.tmcs_debug_gap_counts.argtypes = [ctypes.c_double, P, U64, P, I, P]
         L.tmcs_sample_noalloc.argtypes = [P, U64, U64, U64, P, P, P]
         L.tmcs_check_device.argtypes = []
         L.tmcs_fault_count.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
@@ -117,7 +118,7 @@ def lib() -> ctypes.CDLL:
                   "tmcs_server_submit", "tmcs_server_poll", "tmcs_server_fetch", "tmcs_server_release",
                   "tmcs_server_get_stats", "tmcs_server_close", "tmcs_fault_count", "tmcs_fault_signatures",
                   "tmcs_sample_measurements", "tmcs_fault_outputs", "tmcs_launch_shape", "tmcs_measure_peaks",
-                  "tmcs_dem_columns", "tmcs_launch_flow_shape"):
+                  "tmcs_dem_columns", "tmcs_launch_flow_shape", "tmcs_debug_gap_counts"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -246,6 +247,21 @@ def tmcs_debug_gap_table(p: float) -> np.ndarray:
     t = np.zeros(4096, dtype=np.uint32)
     _check(lib().tmcs_debug_gap_table(float(p), t.ctypes.data))
     return t
+
+
+def tmcs_debug_gap_counts(p: float, words, method: int = 0, stream=None):
+    """Gap counts of `words` (a CUDA uint32 tensor, or int32 viewed as such)
+    for probability p by the device routine `method` (0 the decoupled
+    kernel's walkers, 1 the two-read count, 2 kernels 3-6); returns an int32
+    CUDA tensor."""
+    import torch
+    if not (isinstance(words, torch.Tensor) and words.is_cuda and words.is_contiguous() and
+            words.element_size() == 4):
+        raise ValueError("words must be a contiguous 4-byte CUDA tensor")
+    counts = torch.empty(words.shape, dtype=torch.int32, device=words.device)
+    _check(lib().tmcs_debug_gap_counts(float(p), words.data_ptr(), words.numel(), counts.data_ptr(), int(method),
+                                       _stream_ptr(stream)))
+    return counts
 
 
 def _dev_ptr(buf) -> Optional[int]:
