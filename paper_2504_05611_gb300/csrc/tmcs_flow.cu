@@ -36,6 +36,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "tmcs_device.cuh"
 #include "tmcs_internal.h"
@@ -192,7 +193,12 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
     // position and length in trials
     uint32_t Q = 0, cap = 0, uq = 0, gate = 0;
     PhiloxStream ps{0u, 0u, 0u};
-    uint32_t call = 0, ubase = 0, kind = 0, npauli = 1, kp = 1, toff = 0, t1 = 0, t2 = 0, ktag = 0;
+    // event words: slot << S | chunk << 6 | lane (S = 6 + log2 K) with slot =
+    // ubase + (pos >> 6) kp + (Pauli index - 1), formed as
+    // evb + (pos >> 6) kpm + pos + (Pauli index - 1) 2^S, where evb = ubase 2^S
+    // + chunk 2^6 and kpm = kp 2^S - 64 (all modulo 2^32)
+    constexpr uint32_t S_EV = 6u + LK;
+    uint32_t call = 0, evb = 0, kind = 0, npauli = 1, kpm = 0, toff = 0, t1 = 0, t2 = 0;
     int pos = -1, n_trials = 0;
     float inv = 0.f, c32 = 0.f;
     // the window's events; ev[held .. ne) are events that did not fit their
@@ -223,7 +229,7 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
                 uq = U;
                 kind = d1.x & 7u;
                 npauli = (d1.x >> 3) & 15u;
-                kp = (d1.x >> 7) & 15u;
+                kpm = (((d1.x >> 7) & 15u) << S_EV) - 64u;
                 toff = (d1.y & 0x1FFFu) * kTableWords;
                 inv = __uint_as_float(d1.z);
                 c32 = __uint_as_float(d1.w);
@@ -238,8 +244,7 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
                 ps.a0 = d0.x ^ chunk ^ A.key0;
                 ps.a1 = d0.y;
                 ps.a3 = d0.z ^ A.key1;
-                ubase = d0.w;
-                ktag = k << 6;
+                evb = (d0.w << S_EV) | (k << 6);
                 // chunks past the end of the call (ragged last tile): no trials
                 n_trials = k < nv ? 64 * int(((d1.x >> 11) & 63u) + 1u) : 0;
                 call = 0;
@@ -301,18 +306,33 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
                     }
                 }
                 call += uint32_t(W);
-                // positions in draw order: every draw before the one that
-                // passes the end of the segment is an event
+                // positions in draw order (increasing): every draw before the
+                // one that passes the end of the segment is an event
+                int pd[NE];
 #pragma unroll
                 for (int d = 0; d < NE; d++) {
                     pos += 1 + gp[d];
-                    const bool is_ev = !ended && pos < n_trials;
-                    ended = ended || !is_ev;
-                    const uint32_t pk = kind == N_PC1 ? (wp[d] < t1 ? 1u : wp[d] < t2 ? 3u : 2u)
-                                                      : 1u + __umulhi(wp[d], npauli);
-                    ev[d] = ((ubase + uint32_t(pos >> 6) * kp + (pk - 1u)) << (6u + LK)) | ktag | uint32_t(pos & 63);
-                    ne = is_ev ? uint32_t(d + 1) : ne;
+                    pd[d] = pos;
                 }
+                ne = 0;
+#pragma unroll
+                for (int d = 0; d < NE; d++) ne = pd[d] < n_trials ? uint32_t(d + 1) : ne;
+                ended = pos >= n_trials;
+                // Pauli index - 1: PAULI_CHANNEL_1 thresholds, else uniform
+                // (the thresholds are only looked at in warps that have a
+                // PAULI_CHANNEL_1 lane)
+                auto words = [&](auto pc1) {
+#pragma unroll
+                    for (int d = 0; d < NE; d++) {
+                        uint32_t k1 = __umulhi(wp[d], npauli);
+                        if constexpr (decltype(pc1)::value)
+                            if (kind == N_PC1) k1 = wp[d] < t1 ? 0u : wp[d] < t2 ? 2u : 1u;
+                        const uint32_t pu = uint32_t(pd[d]);
+                        ev[d] = (pu >> 6) * kpm + (evb + pu) + (k1 << S_EV);
+                    }
+                };
+                if (__any_sync(wm, kind == N_PC1)) words(std::true_type{});
+                else words(std::false_type{});
             }
             // reserve the window's events: lanes of the same step share one
             // atomic; a lane's offset among them from bit ballots of its count
@@ -336,12 +356,25 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
                 const uint32_t idx = __shfl_sync(peers, base, int(leader)) + off;
                 // entries past the region's capacity stay in ev[] (held)
                 held = idx >= cap ? 0u : min(ne, cap - idx);
+                // the entries are contiguous unless they wrap past the
+                // arena's end
+                const uint32_t a0 = (uq + idx) & amask;
+                if (a0 + uint32_t(NE) <= A.arena) {
+                    uint32_t *const at = arena + a0;
 #pragma unroll
-                for (int j = 0; j < NE; j++)
-                    if (uint32_t(j) < held) {
-                        if constexpr (GA) __stcg(arena + ((uq + idx + uint32_t(j)) & amask), ev[j]);
-                        else arena[(uq + idx + uint32_t(j)) & amask] = ev[j];
-                    }
+                    for (int j = 0; j < NE; j++)
+                        if (uint32_t(j) < held) {
+                            if constexpr (GA) __stcg(at + j, ev[j]);
+                            else at[j] = ev[j];
+                        }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NE; j++)
+                        if (uint32_t(j) < held) {
+                            if constexpr (GA) __stcg(arena + ((a0 + uint32_t(j)) & amask), ev[j]);
+                            else arena[(a0 + uint32_t(j)) & amask] = ev[j];
+                        }
+                }
             }
         }
         // a stream whose walk ended and whose events are all stored or
@@ -702,13 +735,21 @@ static int env_int_flow(const char *name, int dflt) {
     return (v && *v) ? std::atoi(v) : dflt;
 }
 
+// Philox calls per walker window: TMCS_FLOW_WINDOW (2 to 4) when set, else
+// the requested one (2 to 4), else 3
+static int flow_window(int window) {
+    const int wforce = env_int_flow("TMCS_FLOW_WINDOW", 0);
+    if (wforce >= 2 && wforce <= 4) return wforce;
+    return (window >= 2 && window <= 4) ? window : 3;
+}
+
 static size_t flow_fixed_bytes(const SigProgram &G, int sched, uint32_t n_obs, int K) {
     const SigSchedule &S = G.sched[sched];
     return flow_ring_bytes(S.window, n_obs, K) + flow_step_bytes(uint32_t(S.steps.size()));
 }
 
 bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int appliers, size_t budget, FlowShape *out,
-                bool global_arena) {
+                bool global_arena, int window) {
     const SigProgram &G = c->sig;
     if (!G.ok || sched < 0 || size_t(sched) >= G.sched.size()) return false;
     const SigSchedule &S = G.sched[sched];
@@ -740,14 +781,12 @@ bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int applie
         s.smem_tables = true;
         s.smem = fixed + tabs;
         s.garena_ctas = 0;  // set by the caller (resident CTAs)
-        const int wforce = env_int_flow("TMCS_FLOW_WINDOW", 3);
-        s.window = (wforce >= 2 && wforce <= 4) ? wforce : 3;
+        s.window = flow_window(window);
         s.global_arena = true;
         *out = s;
         return true;
     }
-    const int wforce = env_int_flow("TMCS_FLOW_WINDOW", 3);  // tuning knob: Philox calls per walker window
-    s.window = (wforce >= 2 && wforce <= 4) ? wforce : 3;
+    s.window = flow_window(window);
     // gap tables in shared memory when that still leaves an arena of 8192
     // entries, else read through L1
     s.smem_tables = arena_for(fixed + tabs) >= 8192u;

@@ -314,10 +314,11 @@ int table_for_p(std::vector<uint32_t> &tables, std::vector<double> &table_p, dou
 void free_device_programs(tmcs_circuit *c);
 
 // Decoupled event-signature kernel (tmcs_flow.cu). flow_shape fills *out for
-// the given schedule, chunks per tile, CTA size and applier warps if that
-// shape fits `budget` bytes of dynamic shared memory.
+// the given schedule, chunks per tile, CTA size, applier warps and walker
+// window (Philox calls per pass, 2 to 4; 0: 3; TMCS_FLOW_WINDOW overrides)
+// if that shape fits `budget` bytes of dynamic shared memory.
 bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int appliers, size_t budget, FlowShape *out,
-                bool global_arena = false);
+                bool global_arena = false, int window = 0);
 #ifdef __CUDACC__
 cudaError_t flow_launch(const SigProgram &G, uint32_t n_obs, const DeviceSig *ds, const FlowShape &s,
                         const FlowCall &call, int sms, cudaStream_t st);

@@ -1924,10 +1924,10 @@ static LaunchShape make_shape_sig(const tmcs_circuit *c, uint64_t n_cols, const 
 // tile, `appliers` of its warps apply steps, the others walk. mode = 0 when
 // the shape does not fit.
 static LaunchShape make_shape_flow(const tmcs_circuit *c, uint64_t n_cols, const DeviceLimits &lim, int sched, int K,
-                                   int threads, int appliers, bool global_arena = false) {
+                                   int threads, int appliers, bool global_arena = false, int window = 0) {
     LaunchShape s;
     s.mode = 0;
-    if (!flow_shape(c, sched, K, threads, appliers, lim.smem_optin - 1024, &s.flow, global_arena)) return s;
+    if (!flow_shape(c, sched, K, threads, appliers, lim.smem_optin - 1024, &s.flow, global_arena, window)) return s;
     // a global arena has one slice per resident CTA (at most two per SM)
     if (global_arena) s.flow.garena_ctas = uint32_t(2 * lim.sms);
     s.mode = 7;
@@ -2188,17 +2188,19 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
                 }
             }
     // decoupled kernel: every barrier schedule x chunks per tile x applier
-    // warps, 1024 threads
+    // warps x walker window (3 or 4 Philox calls), 1024 threads
     if (ds)
         for (int sched = 0; sched < int(c->sig.sched.size()); sched++) {
             if (c->sig.sched[sched].lag) continue;
             for (int K = 1; K <= 16; K *= 2)
-                for (int app : {8, 12}) {
-                    // shared-memory arena (the global-memory arena, a tuning
-                    // knob, measured no faster: its reads cost an L2 trip)
-                    const LaunchShape cs = make_shape_flow(c, n_cols, lim, sched, K, 1024, app);
-                    if (cs.mode == 7) cands.push_back(cs);
-                }
+                for (int app : {8, 12})
+                    for (int win : {3, 4}) {
+                        // shared-memory arena (the global-memory arena, a
+                        // tuning knob, measured no faster: its reads cost an
+                        // L2 trip)
+                        const LaunchShape cs = make_shape_flow(c, n_cols, lim, sched, K, 1024, app, false, win);
+                        if (cs.mode == 7 && (win == 3 || cs.flow.window == 4)) cands.push_back(cs);
+                    }
         }
     // With a signature program the frame kernels are compared through their
     // heuristic shape only (they lost to kernel 4 on every measured
@@ -2372,7 +2374,7 @@ static int sample_range(const tmcs_circuit *c, uint64_t first_chunk, uint64_t sh
             s = make_shape_sig(c, n_cols, lim, mdp.tuned_K, mdp.tuned_threads, mdp.tuned_sched);
         if (mdp.tuned_mode == 7 && ds) {
             const LaunchShape f = make_shape_flow(c, n_cols, lim, mdp.tuned_sched, mdp.tuned_K, mdp.tuned_threads,
-                                                  mdp.tuned_warps, mdp.tuned_group == 1);
+                                                  mdp.tuned_warps, mdp.tuned_group == 1, mdp.tuned_flow.window);
             if (f.mode == 7) s = f;
         }
     }
