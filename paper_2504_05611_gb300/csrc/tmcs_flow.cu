@@ -596,6 +596,11 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
             }
             if (tma) fence_proxy_async_shared();  // ring writes before the tensor stores read them
             flow_bar(nthr);
+            // every applier has read the step's arena entries (barrier): the
+            // region is free for the walkers of later steps while the
+            // appliers flush (release: those reads precede the hand-off)
+            U += S.scap[q];
+            if (at == 0) st_release_shared(&C.u_applied, U);
             // detectors [flush_lo, flush_hi) are final: write and clear them
             const uint32_t nd = st.w - st.z;
             bool vec_done = false;
@@ -647,14 +652,12 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
                 }
             }
             flow_bar(nthr);
-            U += S.scap[q];
             if (at == 0) {
                 C.done[slot] = 0u;
                 C.cnt[slot] = 0u;
-                // release: every applier's reads and writes of this step
-                // (ordered before by the barrier) and the counter resets
-                // precede the hand-off
-                st_release_shared(&C.u_applied, U);
+                // release: every applier's ring writes of this step (ordered
+                // before by the barrier) and the counter resets precede the
+                // hand-off of the ring window and the step's slots
                 st_release_shared(&C.applied, Q + 1u);
             }
         }
