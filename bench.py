@@ -273,7 +273,7 @@ def main():
     # (resident) and the seed.
     e2e = None
     if args.e2e_steps > 0:
-        slice_cols = max(1, min(cols, (1 << 30) // max(8 * (info["n_det"] + info["n_obs"]), 1)))
+        slice_cols = max(1, min(cols, (1 << 28) // max(8 * (info["n_det"] + info["n_obs"]), 1)))
         nslices = (cols + slice_cols - 1) // slice_cols
         dbuf = [torch.empty((info["n_det"], slice_cols), dtype=torch.int64, device=dev) for _ in range(2)]
         obuf = [torch.empty((max(info["n_obs"], 1), slice_cols), dtype=torch.int64, device=dev) for _ in range(2)]
