@@ -50,6 +50,9 @@ constexpr uint32_t kFlowSlots = 64;       // steps in flight (done / count slots
 #endif
 constexpr uint32_t kFlowApplyBatch = TMCS_FLOW_APPLY_BATCH;
 constexpr uint32_t kFlowMinArena = 1024;  // smallest useful arena (entries)
+// arena entry of an event that flips nothing (no event word takes this value:
+// flow_shape keeps event slots x 64 x K below 2^32)
+constexpr uint32_t kFlowDead = 0xFFFFFFFFu;
 constexpr uint32_t kFlowMaxArena = 65536;
 
 struct FlowArgs {
@@ -157,6 +160,7 @@ __device__ __forceinline__ void flow_put(const FlowArgs &A, uint64_t *ring, uint
 
 template <int K>
 __device__ __forceinline__ void flow_put_word(const FlowArgs &A, uint64_t *ring, uint32_t wv) {
+    if (wv == kFlowDead) return;
     const uint2 v = __ldg(reinterpret_cast<const uint2 *>(A.ev_ent) + (wv >> (6u + FlowLog<K>::v)));
     flow_put<K>(A, ring, wv, v);
 }
@@ -198,7 +202,7 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
     // evb + (pos >> 6) kpm + pos + (Pauli index - 1) 2^S, where evb = ubase 2^S
     // + chunk 2^6 and kpm = kp 2^S - 64 (all modulo 2^32)
     constexpr uint32_t S_EV = 6u + LK;
-    uint32_t call = 0, evb = 0, kind = 0, npauli = 1, kpm = 0, toff = 0, t1 = 0, t2 = 0;
+    uint32_t call = 0, evb = 0, kind = 0, npauli = 1, kpm = 0, toff = 0, t1 = 0, t2 = 0, live_k = 0;
     int pos = -1, n_trials = 0;
     float inv = 0.f, c32 = 0.f;
     // the window's events; ev[held .. ne) are events that did not fit their
@@ -232,7 +236,8 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
                 kpm = (((d1.x >> 7) & 15u) << S_EV) - 64u;
                 toff = (d1.y & 0x1FFFu) * kTableWords;
                 inv = __uint_as_float(d1.z);
-                c32 = __uint_as_float(d1.w);
+                c32 = -32.0f * inv;  // exact (a power-of-two scaling)
+                live_k = d1.w;
                 if (kind == N_PC1) {
                     t1 = __ldg(&A.noise[d1.y >> 13].t1);
                     t2 = __ldg(&A.noise[d1.y >> 13].t2);
@@ -320,7 +325,9 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
                 ended = pos >= n_trials;
                 // Pauli index - 1: PAULI_CHANNEL_1 thresholds, else uniform
                 // (the thresholds are only looked at in warps that have a
-                // PAULI_CHANNEL_1 lane)
+                // PAULI_CHANNEL_1 lane). An event whose Pauli index flips
+                // nothing in any unit of the segment becomes kFlowDead: it
+                // keeps its arena entry but costs the appliers no table read.
                 auto words = [&](auto pc1) {
 #pragma unroll
                     for (int d = 0; d < NE; d++) {
@@ -328,7 +335,8 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
                         if constexpr (decltype(pc1)::value)
                             if (kind == N_PC1) k1 = wp[d] < t1 ? 0u : wp[d] < t2 ? 2u : 1u;
                         const uint32_t pu = uint32_t(pd[d]);
-                        ev[d] = (pu >> 6) * kpm + (evb + pu) + (k1 << S_EV);
+                        const uint32_t wd = (pu >> 6) * kpm + (evb + pu) + (k1 << S_EV);
+                        ev[d] = (live_k >> k1) & 1u ? wd : kFlowDead;
                     }
                 };
                 if (__any_sync(wm, kind == N_PC1)) words(std::true_type{});
@@ -590,7 +598,8 @@ __device__ __forceinline__ void flow_apply(const FlowArgs &A, const FlowSmem &S,
                 }
 #pragma unroll
                 for (uint32_t j = 0; j < kFlowApplyBatch; j++)
-                    v[j] = e + j * nthr < n ? __ldg(ev2 + (wv[j] >> (6u + LK))) : make_uint2(kEvNone, kEvNone);
+                    v[j] = e + j * nthr < n && wv[j] != kFlowDead ? __ldg(ev2 + (wv[j] >> (6u + LK)))
+                                                                   : make_uint2(kEvNone, kEvNone);
 #pragma unroll
                 for (uint32_t j = 0; j < kFlowApplyBatch; j++) flow_put<K>(A, S.ring, wv[j], v[j]);
             }
@@ -762,7 +771,8 @@ bool flow_shape(const tmcs_circuit *c, int sched, int K, int threads, int applie
     if (threads < 64 || threads > TMCS_FLOW_MAX_THREADS || threads % 32 || appliers < 1 || appliers >= threads / 32)
         return false;
     // event words: slot << (6 + log2 K) | chunk << 6 | lane must fit 32 bits
-    if (uint64_t(G.n_event_slots) * 64u * uint64_t(K) > (uint64_t(1) << 32)) return false;
+    // and never equal kFlowDead
+    if (uint64_t(G.n_event_slots) * 64u * uint64_t(K) >= (uint64_t(1) << 32)) return false;
     const size_t fixed = flow_fixed_bytes(G, sched, uint32_t(c->n_obs), K);
     const size_t tabs = G.tables.size() * 4;
     auto arena_for = [&](size_t used) {

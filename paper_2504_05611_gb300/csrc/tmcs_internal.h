@@ -216,7 +216,8 @@ struct SigSchedule {
     // dependence on the seed): hi and lo of 0xCD9E8D57 x op index (Philox
     // round 1), segment, first event slot, kind | npauli << 3 | paulis << 7
     // | (units - 1) << 11 | step << 17, table | descriptor << 13, float bits
-    // of 1/log2(1-p) and of -32/log2(1-p) (the gap estimate).
+    // of 1/log2(1-p) (the gap estimate), and the mask of Pauli indices that
+    // flip an output in some unit of the segment (bit k - 1 for index k).
     std::vector<uint32_t> item_desc;
 };
 

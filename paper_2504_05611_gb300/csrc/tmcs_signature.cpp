@@ -79,6 +79,19 @@ struct Pass {
 
 }  // namespace
 
+// Pauli indices of a segment that can flip an output: bit k - 1 is set when
+// event (unit, Pauli index k) has a non-empty output list for some unit of
+// the segment (slots slot0 .. slot0 + units * paulis - 1, unit-major). The
+// decoupled kernel drops the other events of the segment's streams before
+// they reach its arena: they flip nothing, so the result is unchanged.
+static uint32_t live_paulis(const SigProgram &G, uint32_t slot0, uint32_t units, uint32_t paulis) {
+    uint32_t m = 0;
+    for (uint32_t u = 0; u < units; u++)
+        for (uint32_t k = 0; k < paulis; k++)
+            if (G.ev_ent[2 * (size_t(slot0) + size_t(u) * paulis + k)] != kEvNone) m |= 1u << k;
+    return m;
+}
+
 // Checks every invariant the signature kernels rely on, after each build:
 // the memory safety of each index they form from the program (event slots
 // and overflow lists, observable and detector ids, gap tables, item
@@ -168,7 +181,8 @@ static std::string validate_signature_program(const SigProgram &G, uint64_t D, u
                 ((wd[4] >> 7) & 15u) != sig_paulis(nd.kind) || ((wd[4] >> 11) & 63u) != units - 1 ||
                 step >= S.steps.size() || k < S.steps[step].item_begin || k >= S.steps[step].item_end ||
                 (wd[5] & 0x1FFFu) != nd.table || (wd[5] >> 13) != di ||
-                wd[6] != G.tables[size_t(nd.table) * kTableWords + kGapLen])
+                wd[6] != G.tables[size_t(nd.table) * kTableWords + kGapLen] ||
+                wd[7] != live_paulis(G, r[2], units, sig_paulis(nd.kind)))
                 return "walker descriptor";
             lo[k] = seg_lo[seg0[di] + sg];
             hi[k] = seg_hi[seg0[di] + sg];
@@ -598,16 +612,12 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
                 const uint64_t m = uint64_t(0xCD9E8D57u) * nd.op_index;
                 const uint32_t npauli = nd.kind == 3u ? 15u : nd.kind == 2u ? 3u : 1u;
                 uint32_t inv_bits = G.tables[size_t(nd.table) * kTableWords + kGapLen];
-                float inv = 0.f, c32 = 0.f;
-                std::memcpy(&inv, &inv_bits, 4);
-                c32 = -32.0f * inv;
-                uint32_t c32_bits = 0;
-                std::memcpy(&c32_bits, &c32, 4);
-                const uint32_t w[8] = {uint32_t(m >> 32), uint32_t(m), sg,
-                                       G.ev_base[di] + sg * kSegUnits * sig_paulis(nd.kind),
+                const uint32_t slot0 = G.ev_base[di] + sg * kSegUnits * sig_paulis(nd.kind);
+                const uint32_t w[8] = {uint32_t(m >> 32), uint32_t(m), sg, slot0,
                                        nd.kind | (npauli << 3) | (sig_paulis(nd.kind) << 7) | ((units - 1) << 11) |
                                            (t << 17),
-                                       nd.table | (di << 13), inv_bits, c32_bits};
+                                       nd.table | (di << 13), inv_bits,
+                                       live_paulis(G, slot0, units, sig_paulis(nd.kind))};
                 S.item_desc.insert(S.item_desc.end(), w, w + 8);
             }
         // device item records (the walk reads one 16-byte record per stream)
