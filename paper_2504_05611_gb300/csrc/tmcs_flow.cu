@@ -390,12 +390,10 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
         const bool complete = have && ended && held == ne;
         const uint32_t cm = __ballot_sync(0xFFFFFFFFu, complete);
         if (complete) {
-            // the streams' events (stored or applied by these lanes) precede
-            // the count: warp barrier, then a release add by the leader
-            const uint32_t peers = __match_any_sync(cm, Q);
-            const uint32_t leader = uint32_t(__ffs(peers)) - 1u;
-            __syncwarp(peers);
-            if (lane == leader) red_release_add_shared(&C.done[Q & (kFlowSlots - 1u)], uint32_t(__popc(peers)));
+            // the stream's events (stored or applied by this lane) precede
+            // the count: a release add per lane (cheaper than grouping the
+            // lanes of a step behind one add)
+            red_release_add_shared(&C.done[Q & (kFlowSlots - 1u)], 1u);
             have = false;
             live = false;
             ended = false;
