@@ -161,14 +161,24 @@ __device__ __forceinline__ int gap_count_est(const uint32_t *__restrict__ T, flo
 // ends). Same result as gap_count_t for every w of such a table.
 constexpr float kNearInv = 32768.0f;
 
+// gap_count_near on the table whose word T[g - 1] sits at tab[base1 + g]
+// (base1 = the table's first word index minus one, modulo 2^32), so a
+// caller walking many draws of one table forms the base once.
 template <bool SMT>
-__device__ __forceinline__ int gap_count_near(const uint32_t *__restrict__ T, float inv_log2, float c32, uint32_t w) {
+__device__ __forceinline__ int gap_count_near_at(const uint32_t *__restrict__ tab, uint32_t base1, float inv_log2,
+                                                 float c32, uint32_t w) {
     const float est = fmaf(__log2f(__uint2float_rn(w) + 1.0f), inv_log2, c32);
     const int m = min(max(__float2int_rn(est), 1), int(kGapLen));
+    const uint32_t i = base1 + uint32_t(m);
     uint32_t t;
-    if constexpr (SMT) t = T[m - 1];
-    else t = __ldg(T + (m - 1));
+    if constexpr (SMT) t = tab[i];
+    else t = __ldg(tab + i);
     return w < t ? m : m - 1;
+}
+
+template <bool SMT>
+__device__ __forceinline__ int gap_count_near(const uint32_t *__restrict__ T, float inv_log2, float c32, uint32_t w) {
+    return gap_count_near_at<SMT>(T, 0xFFFFFFFFu, inv_log2, c32, w);
 }
 
 // The count by one table read where the table allows it, else by the log

@@ -295,8 +295,8 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
 #pragma unroll
                     for (int c = 0; c < W; c++) {
                         const uint4 w = philox_call(ps, call + uint32_t(c), A.key0, A.key1);
-                        gp[2 * c] = gap_count_near<SMT>(tabs + toff, inv, c32, w.x);
-                        gp[2 * c + 1] = gap_count_near<SMT>(tabs + toff, inv, c32, w.z);
+                        gp[2 * c] = gap_count_near_at<SMT>(tabs, toff - 1u, inv, c32, w.x);
+                        gp[2 * c + 1] = gap_count_near_at<SMT>(tabs, toff - 1u, inv, c32, w.z);
                         wp[2 * c] = w.y;
                         wp[2 * c + 1] = w.w;
                     }
@@ -336,7 +336,7 @@ __device__ __forceinline__ void flow_walk(const FlowArgs &A, const FlowSmem &S, 
                             if (kind == N_PC1) k1 = wp[d] < t1 ? 0u : wp[d] < t2 ? 2u : 1u;
                         const uint32_t pu = uint32_t(pd[d]);
                         const uint32_t wd = (pu >> 6) * kpm + (evb + pu) + (k1 << S_EV);
-                        ev[d] = (live_k >> k1) & 1u ? wd : kFlowDead;
+                        ev[d] = wd | (((live_k >> k1) & 1u) - 1u);  // kFlowDead when not live
                     }
                 };
                 if (__any_sync(wm, kind == N_PC1)) words(std::true_type{});
