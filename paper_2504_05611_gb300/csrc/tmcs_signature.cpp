@@ -694,6 +694,14 @@ int build_signature_program(tmcs_circuit *c, uint32_t max_window) {
             G.sched[0].item_rec[2] += 1;  // first item's event slot
         } else if (what == "window" && !G.sched.empty()) {
             G.sched[0].window = 256;  // steps cut for a larger ring
+        } else if (what == "live" && !G.sched.empty()) {
+            // drop a Pauli index that flips something from one item's mask
+            std::vector<uint32_t> &wd = G.sched[0].item_desc;
+            for (size_t k = 7; k < wd.size(); k += 8)
+                if (wd[k]) {
+                    wd[k] &= wd[k] - 1u;
+                    break;
+                }
         }
     }
     const std::string bad = validate_signature_program(G, D, O);

@@ -270,12 +270,14 @@ def test_signature_single_schedule_at_the_floor(tmcs, monkeypatch):
 
 
 @pytest.mark.parametrize("mistake,reason", [("observable", "event entry"), ("record", "item record"),
-                                            ("window", "window")])
+                                            ("window", "window"), ("live", "walker descriptor")])
 def test_signature_validator_refuses_planted_mistakes(tmcs, monkeypatch, mistake, reason):
     """The host-side validator of the event-signature program refuses a
-    program with an out-of-range observable id, a wrong item record or a
-    ring too small for its steps; the circuit then has no signature program
-    (sampling runs on the frame kernels)."""
+    program with an out-of-range observable id, a wrong item record, a ring
+    too small for its steps, or a walker descriptor whose live-Pauli mask
+    leaves out a Pauli index that flips an output (the decoupled kernel would
+    drop those events); the circuit then has no signature program (sampling
+    runs on the frame kernels)."""
     circ = C.nonlocal_cnot_circuit(C.code_by_name("sc11"), 11, 11, C.NoiseModel(0.001, 0.01))
     h = tmcs.tmcs_circuit_build(circ)
     assert tmcs.tmcs_circuit_stats(h)["sig_ok"] == 1
