@@ -233,3 +233,36 @@ def test_flow_flush_unaligned_outputs(monkeypatch, offset_words):
         assert int(flat[:offset_words].eq(-1).sum()) == offset_words  # nothing written before the buffer
     finally:
         s.close()
+
+
+def _mostly_silent_circuit(n=150):
+    """Z-basis readout of n qubits after two-qubit depolarizing noise on
+    pairs, a Z-heavy PAULI_CHANNEL_1 and Z flips: only the X parts of the
+    noise flip a detector, so most Pauli indices of every noise op flip
+    nothing (the Z_ERROR op flips nothing at all and has no walked item)."""
+    c = C.Circuit()
+    q = list(range(n))
+    c.append("R", q)
+    c.append("DEPOLARIZE2", [t for i in range(0, n - 1, 2) for t in (i, i + 1)], p=0.04)
+    c.append("PAULI_CHANNEL_1", q, p=(0.005, 0.0, 0.1))
+    c.append("Z_ERROR", q, p=0.2)
+    c.append("CX", [t for i in range(0, n - 1, 2) for t in (i, i + 1)])
+    recs = c.append("M", q)
+    for r in recs:
+        c.append("DETECTOR", [int(r)])
+    c.append("OBSERVABLE", [int(recs[0]), int(recs[n - 1])], arg=0)
+    return c
+
+
+@pytest.mark.parametrize("tile_k,cap", [(8, None), (8, 2), (2, None), (1, 5)])
+def test_flow_events_that_flip_nothing(monkeypatch, tile_k, cap):
+    """Walkers mark events whose Pauli index flips nothing in their segment
+    (the segment's live-Pauli mask) so that the appliers skip them; on a
+    circuit where most drawn events are such, including the events a lane
+    holds back when its step's region is full, the output is the oracle's."""
+    circ = _mostly_silent_circuit()
+    env = {"TMCS_TILE_K": tile_k}
+    if cap is not None:
+        env["TMCS_TEST_FLOW_CAP"] = cap
+    gd, go = assert_flow_parity(monkeypatch, circ, "silent", 64 * 23 + 9, 77, first_chunk=5, **env)
+    assert gd.any() and go.any()
