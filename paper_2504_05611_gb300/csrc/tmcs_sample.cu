@@ -2188,12 +2188,14 @@ static int autotune(const tmcs_circuit *c, int device, KernelArgs a, const Devic
                 }
             }
     // decoupled kernel: every barrier schedule x chunks per tile x applier
-    // warps x walker window (3 or 4 Philox calls), 1024 threads
+    // warps x walker window (3 or 4 Philox calls), 1024 threads. Circuits
+    // whose events flip many outputs (BB codes: weight-6 checks, several
+    // observables) want more applier warps than the surface-code ones.
     if (ds)
         for (int sched = 0; sched < int(c->sig.sched.size()); sched++) {
             if (c->sig.sched[sched].lag) continue;
             for (int K = 1; K <= 16; K *= 2)
-                for (int app : {8, 12})
+                for (int app : {8, 12, 16, 20, 24})
                     for (int win : {3, 4}) {
                         // shared-memory arena (the global-memory arena, a
                         // tuning knob, measured no faster: its reads cost an

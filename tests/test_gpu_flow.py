@@ -66,7 +66,8 @@ def nl11():
 # 0: 4096 detectors, 1: 2048, 2: 1024) take fewer chunks per tile
 FLOW_SHAPES = [(0, 1, 8, 1024), (0, 2, 4, 1024), (0, 4, 8, 1024), (0, 4, 1, 1024), (0, 2, 2, 512), (0, 1, 1, 256),
                (1, 8, 4, 1024), (1, 4, 8, 1024), (1, 8, 8, 1024), (1, 2, 1, 256), (2, 16, 8, 1024), (2, 8, 4, 1024),
-               (2, 4, 2, 512), (2, 1, 8, 1024), (2, 16, 2, 256)]
+               (2, 4, 2, 512), (2, 1, 8, 1024), (2, 16, 2, 256), (1, 8, 16, 1024), (1, 8, 20, 1024),
+               (2, 8, 24, 1024), (2, 4, 20, 1024)]
 
 
 @pytest.mark.parametrize("sched,tile_k,appliers,threads", FLOW_SHAPES)
